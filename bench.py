@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the chi0 / E_c hot path on one GB300 (or N replicas).
+
+Metric: chi0 TFLOP/s (algorithmic Hermitian rank-k flops 4 NG (NG+1) K nw per
+q-point, summed over the step) and seconds per q-point with all frequencies,
+mixed precision against plain FP64 on the same GPU, and the E_c relative error
+of the mixed mode against the FP64 mode.
+
+Workload: the bulk-solid configuration (9 bohr cubic box, 40^3 grid, 2x2x2
+k-mesh, 8 q-points, 16 occupied + 1200 empty bands, 20 Ha orbitals, NG ~ 1200,
+16 frequencies, 3 PAW atoms x 13 projectors), seeded synthetic data.  One step
+is one E_c evaluation over all 8 q-points: wavefunctions to the grid, pair
+densities + PAW, rank-k update, FP64 log-det and quadrature.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With --gpus N > 1 it expects torchrun: every rank runs its own replica of the
+step (independent problems, no data-path collective) and rank 0 prints one
+JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "chi0 TFLOP/s and s per q (all iw), mixed vs FP64 on 1 GB300; E_c rel. error"
+WORKLOAD = "bulk 9 bohr box, 40^3 grid, 2x2x2 k, 8 q, 16 occ + 1200 empty bands, NG~1200, 16 iw, 3x13 PAW projectors"
+CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                "clocks_event_reasons.sw_power_cap")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rankk_flops(ngs, ks, nw):
+    return float(sum(4.0 * ng * (ng + 1) * k * nw for ng, k in zip(ngs, ks)))
+
+
+def make_workload():
+    from paper_1307_8052_gb300 import synthetic as syn
+    return syn.config1()
+
+
+def pairs_per_q(p):
+    out = []
+    for qp in p.qpoints:
+        k = 0
+        for ik, ikp in zip(qp.k_of, qp.kq_of):
+            k += int(np.sum(p.sets[ik].f > 0)) * int(np.sum(p.sets[ikp].f < 1))
+        out.append(k)
+    return out
+
+
+def cpu_sample(p, steps=1, warmup=0):
+    """Time the oracle on a bounded sample of the workload: chi0 of q-point 3 from
+    the first transition with 4 occupied x 100 empty bands (all G, all iw)."""
+    import oracle as o
+    from paper_1307_8052_gb300 import synthetic as syn
+    iq = 3
+    qp = p.qpoints[iq]
+    sets = []
+    for s in p.sets:
+        keep = np.r_[np.arange(12, 16), np.arange(16, 116)]
+        sets.append(syn.OrbitalSet(s.k_red, s.miller, s.C[keep], s.eps[keep], s.f[keep], s.P[keep]))
+    sub = syn.Problem(p.name, p.config, p.cell, p.grid, p.ecut_wf, p.ecut_chi, p.spin_factor, p.nk_bz, sets,
+                      [syn.QPoint(qp.q_red, qp.k_of[:1], qp.kq_of[:1], qp.G0[:1], 1.0)], p.nw, p.paw)
+    gm = o.g_sphere(p.cell, qp.q_red, p.ecut_chi)
+    Q = syn.paw_Q(p.paw, p.cell, qp.q_red, gm)
+    om, _ = o.frequency_grid(p.nw)
+    flops = rankk_flops([len(gm)], [4 * 100], p.nw)
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        o.chi0(sub, 0, om, Q)
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    t = float(np.mean(times))
+    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": int(cores), "kind": "oracle",
+            "sample": "chi0 of q=(0,1/2,1/2), first k-transition, 4 occupied x 100 empty bands, all G and iw "
+                      f"({flops / 1e12:.4f} TFLOP algorithmic, {t:.2f} s per sample)"}, times
+
+
+def run_reference(args):
+    """Reference arm: the CPU FP64 oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = make_workload()
+    base, times = cpu_sample(p, steps=args.steps, warmup=args.warmup)
+    t = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": base["sample"]},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    from paper_1307_8052_gb300 import binding as b
+    from paper_1307_8052_gb300 import synthetic as syn
+    from paper_1307_8052_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    b.load()
+    stream = torch.cuda.current_stream()
+
+    p = make_workload()
+    nq = len(p.qpoints)
+    om, W = b.rpa_gauss_legendre(p.nw, 1.0)
+    wq = [qp.weight for qp in p.qpoints]
+    iqs = list(range(nq))
+    Kq = pairs_per_q(p)
+
+    def make_ctx(precision):
+        ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, precision, device=local,
+                           stream=stream.cuda_stream)
+        ngs = b.load_problem(ctx, p, paw_Q=lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))
+        return ctx, ngs
+
+    ctx, ngs = make_ctx(args.precision)
+    flops = rankk_flops(ngs, Kq, p.nw)
+    b.rpa_set_profiling(ctx, True)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        b.rpa_energy(ctx, iqs, wq, om, W)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stage_ms = np.zeros(5)
+    launches = np.zeros(5, dtype=np.int64)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            E, terms = b.rpa_energy(ctx, iqs, wq, om, W)
+            ms, nl = b.rpa_get_profile(ctx)
+            stage_ms += ms
+            launches += nl
+        e1.record(stream)
+        barrier()
+    t_step = e0.elapsed_time(e1) / args.steps / 1e3
+    t_step = max_over_ranks(t_step)
+    value = world * flops / t_step / 1e12
+
+    # end to end through the public API from pinned host buffers
+    pinned = []
+    for s in p.sets:
+        pinned.append((torch.from_numpy(s.C).pin_memory(), torch.from_numpy(s.P).pin_memory()))
+    Qpin = []
+    for iq in iqs:
+        gm = b.rpa_gvectors(ctx, iq)
+        Qpin.append(torch.from_numpy(syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm)).pin_memory())
+    h2d = sum(c.numel() * 16 + pp.numel() * 16 for c, pp in pinned) + sum(q.numel() * 16 for q in Qpin)
+    h2d += sum(s.miller.nbytes + s.eps.nbytes + s.f.nbytes for s in p.sets)
+    d2h = 8 * (1 + nq * p.nw)
+
+    def e2e_step():
+        for i, s in enumerate(p.sets):
+            b.rpa_set_orbitals(ctx, i, s.k_red, s.miller, pinned[i][0], s.eps, s.f)
+            b.rpa_set_paw(ctx, i, p.paw.nproj, pinned[i][1])
+        for iq in iqs:
+            b.rpa_set_paw_Q(ctx, iq, p.paw.nproj, Qpin[iq])
+        return b.rpa_energy(ctx, iqs, wq, om, W)
+
+    e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3)
+    b.rpa_set_profiling(ctx, False)
+
+    # plain FP64 form on one q-point for the mixed-vs-FP64 statement
+    fp64 = None
+    if args.fp64_q >= 0:
+        iq = args.fp64_q
+        ctx64, ngs64 = make_ctx("fp64")
+        b.rpa_set_profiling(ctx64, True)
+        barrier()
+        e0.record(stream)
+        E64, t64 = b.rpa_energy(ctx64, [iq], [1.0], om, W)
+        e1.record(stream)
+        barrier()
+        s64 = e0.elapsed_time(e1) / 1e3
+        ms64, _ = b.rpa_get_profile(ctx64)
+        b.rpa_destroy(ctx64)
+        Emix, tmix = b.rpa_energy(ctx, [iq], [1.0], om, W)
+        f64 = rankk_flops([ngs64[iq]], [Kq[iq]], p.nw)
+        fp64 = {"q": iq, "s_per_q": s64, "chi0_tflops": f64 / s64 / 1e12,
+                "rankk_ms": ms64[2], "logdet_ms": ms64[3],
+                "speedup_mixed_vs_fp64": s64 / (t_step / nq),
+                "ec_q_fp64": E64, "ec_q_mixed": Emix, "ec_rel_error": abs(Emix - E64) / abs(E64),
+                "terms_max_rel_error": float(np.max(np.abs(tmix - t64)) / np.max(np.abs(t64)))}
+
+    peaks, peak_kind = load_peaks()
+    herk_ms = stage_ms[2] / args.steps
+    if args.precision in ("bf16x2", "bf16x3"):
+        peak = peaks.get("bf16_tflops_sustained" if args.sustained else "bf16_tflops")
+        bound = "tensor"
+    else:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = (152 * 128 * 2 * sm_mhz * 1e6 / 1e12) if args.precision == "fp32" else 1.05
+        bound = "alu"
+    achieved = flops / (herk_ms / 1e3) / 1e12
+    base = None
+    if rank == 0 and not args.no_cpu:
+        base, _ = cpu_sample(p, steps=1, warmup=0)
+    b.rpa_destroy(ctx)
+    if rank != 0:
+        return
+    stage_names = ["wf_to_grid", "pair_density_paw", "rankk_update", "logdet", "other"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x2": "bf16x2->f32",
+                                       "bf16x3": "bf16x3->f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "q_points": nq, "NG": ngs,
+                   "pairs_per_q": Kq, "nw": p.nw, "l2": "inputs larger than L2 (grids 5 GB, N 185 MB per k)",
+                   "parallelism": f"replicas x{world}"},
+        "s_per_q": t_step / nq,
+        "E_c": E,
+        "stage_ms_per_step": {n: float(m / args.steps) for n, m in zip(stage_names, stage_ms)},
+        "fp64": fp64,
+        "e2e": {"value": world * flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3},
+        "gpu_launches": int(launches.sum()),
+        "roofline": {"bound": bound, "kernel": "rank-k update (Eq. 17)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x max clock"},
+        "clocks": clk.summary(),
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16x2", "bf16x3"], default="fp32")
+    ap.add_argument("--fp64-q", type=int, default=3, help="q-point timed in plain FP64 (-1: skip)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sustained", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * rpa.h -- C ABI of the GB300 library for the non-interacting response
+ * function chi0_GG'(q, i w) and the RPA correlation energy E_c.
+ *
+ * The operations follow Yan, Li and O'Grady, "Graphics processing unit
+ * acceleration of the random phase approximation in the projector augmented
+ * wave method":
+ *   - chi0 by the sum over states, Eq. 3, accumulated as the grouped
+ *     ("multi-u") Hermitian rank-k update of Eq. 17 for every frequency;
+ *   - pair densities n_nm(G) of Eq. 4 from real-space orbital products and a
+ *     forward Fourier transform (Eq. 10), gathered on the response G sphere
+ *     (Table 1 steps 5-6), plus the PAW augmentation of Eq. 6 (steps 7-9);
+ *   - E_c of Eqs. 1-2: sum over q of w_q, over Gauss-Legendre frequencies of
+ *     W_j / (2 pi) [ln det(1 - v^1/2 chi0 v^1/2) + tr(v^1/2 chi0 v^1/2)]
+ *     (Table 1 step 13).
+ *
+ * Conventions (all functions):
+ *   - Complex arrays are interleaved (re, im) doubles.
+ *   - Lattice vectors are the rows of cell[9] (bohr); k, q are given in
+ *     reduced coordinates of the reciprocal lattice; Miller indices are int32
+ *     triples.  A grid point j = (j1, j2, j3) of the N1 x N2 x N3 grid sits at
+ *     r = sum_i (j_i / N_i) a_i.
+ *   - Orbital coefficients follow Eq. 8: psi_nk(r) = Omega^-1/2 sum_Q C_nk(Q)
+ *     exp(i (k+Q).r) with sum_Q |C_nk(Q)|^2 = 1.
+ *   - Input pointers may be host or device (CUDA) memory; the library copies
+ *     what it keeps and never retains a caller pointer after a call returns.
+ *     Output pointers may be host or device memory; device outputs are written
+ *     in order on the context's stream, host outputs are complete when the
+ *     call returns.
+ *   - Every call returns an rpa_status; rpa_last_error() gives a message.
+ *     No call aborts the process or traps on the device.  A context is not
+ *     thread-safe: use one context per host thread.
+ */
+#ifndef RPA_GB300_H
+#define RPA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpa_ctx rpa_ctx;
+
+typedef enum {
+  RPA_OK = 0,
+  RPA_ERR_ARG = 1,      /* invalid argument (sizes, indices, aliasing grid) */
+  RPA_ERR_OOM = 2,      /* device allocation failed */
+  RPA_ERR_CUDA = 3,     /* CUDA runtime/driver error */
+  RPA_ERR_NOT_HPD = 4,  /* 1 - v^1/2 chi0 v^1/2 not Hermitian positive definite */
+  RPA_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+  RPA_ERR_STATE = 6     /* call out of order (e.g. missing orbitals) */
+} rpa_status;
+
+/* Arithmetic of the rank-k update (Eq. 17) and of the pair densities.
+ * RPA_FP64   : everything in FP64.
+ * RPA_FP32   : pair densities and rank-k update in FP32 (CUDA cores), with
+ *              compensated FP32 folding of partial sums; chi0 held in FP64.
+ * RPA_BF16X2 : pair densities in FP32; rank-k update on the tensor cores with
+ *              each operand split into two bfloat16 terms (hi + lo, three
+ *              products), FP32 accumulation in tensor memory, FP64 chi0.
+ * RPA_BF16X3 : as BF16X2 with three bfloat16 terms (six products).
+ * In every mode the PAW projection products, the log-det and the frequency
+ * quadrature run in FP64. */
+typedef enum {
+  RPA_FP64 = 0,
+  RPA_FP32 = 1,
+  RPA_BF16X2 = 2,
+  RPA_BF16X3 = 3
+} rpa_precision;
+
+typedef struct {
+  double cell[9];      /* lattice vectors a1, a2, a3 as rows, bohr */
+  int32_t grid[3];     /* real-space grid N1, N2, N3 of Eq. 10 */
+  double ecut_chi;     /* response cutoff: G with |q+G|^2 / 2 <= ecut_chi (Ha) */
+  double spin_factor;  /* s in s / (Omega N_k); 2 for spin-paired orbitals */
+  int32_t nk_bz;       /* N_k of the Brillouin-zone average */
+  int32_t precision;   /* rpa_precision */
+  int32_t device;      /* CUDA device ordinal */
+  void* stream;        /* cudaStream_t to order work on; NULL: library stream */
+} rpa_params;
+
+/* Creates a context on params->device.  Validates the cell (non-singular),
+ * grid (each N_i in [2, 4096]), ecut_chi > 0, spin_factor > 0, nk_bz >= 1 and
+ * the precision.  *out receives the context; RPA_ERR_ARG on bad parameters,
+ * RPA_ERR_CUDA if the device cannot be used. */
+rpa_status rpa_create(const rpa_params* params, rpa_ctx** out);
+
+/* Releases every device allocation of the context.  NULL is ignored. */
+void rpa_destroy(rpa_ctx* ctx);
+
+/* Message of the last failing call on this context (never NULL). */
+const char* rpa_last_error(const rpa_ctx* ctx);
+
+/* Gauss-Legendre frequency grid (Sec. 2.1, 16 points in the paper) mapped to
+ * [0, inf) by w = w0 (1 + x) / (1 - x): omega[n] nodes, W[n] weights with
+ * int_0^inf f(w) dw ~ sum_j W_j f(omega_j).  Host pointers.  n in [1, 1024]. */
+rpa_status rpa_gauss_legendre(int32_t n, double omega0, double* omega, double* W);
+
+/* Orbital set kidx (Eq. 8; Table 1 step 2): the k-point k_red[3], nbands
+ * bands on npw plane waves with Miller indices miller[npw][3], coefficients
+ * C[nbands][npw] (complex), eigenvalues eps[nbands] (Ha) and occupations
+ * f[nbands] in [0, 1] per spin channel.  Replaces a previous set kidx (and
+ * drops its projections).  kidx in [0, 4096).  Miller indices must be
+ * distinct.  C may be host or device memory; miller, eps, f are host. */
+rpa_status rpa_set_orbitals(rpa_ctx* ctx, int32_t kidx, const double k_red[3],
+                            int32_t nbands, int32_t npw, const int32_t* miller,
+                            const double* C, const double* eps, const double* f);
+
+/* PAW projections of set kidx (Eq. 6; Table 1 step 7):
+ * P[nbands][sum_a nproj[a]] (complex) with P_ni = <p~^a_i | psi~_nk>, atoms
+ * in order.  nproj[a] in [1, 64].  P host or device. */
+rpa_status rpa_set_paw(rpa_ctx* ctx, int32_t kidx, int32_t natoms,
+                       const int32_t* nproj, const double* P);
+
+/* q-point iq (Eq. 2; Table 1 step 14): q_red[3] and its nk transitions
+ * k -> k+q, each given as (k_of[t], kq_of[t], G0[t][3]) meaning the orbitals
+ * at k are set k_of[t] and k + q = k' + G0 with k' the k-point of set
+ * kq_of[t].  Builds the response sphere {G : |q+G|^2/2 <= ecut_chi} in
+ * Miller-lexicographic order (first index slowest) and the Coulomb kernel
+ * v_G = 4 pi / |q+G|^2 (0 where q + G = 0).  *ng_out (nullable) receives NG.
+ * The referenced orbital sets must exist; the grid must be large enough that
+ * the Fourier route of Eq. 10 has no aliasing for them (RPA_ERR_ARG
+ * otherwise).  iq in [0, 4096).  All pointers host. */
+rpa_status rpa_set_qpoint(rpa_ctx* ctx, int32_t iq, const double q_red[3],
+                          int32_t nk, const int32_t* k_of, const int32_t* kq_of,
+                          const int32_t* G0, int32_t* ng_out);
+
+/* Number of G vectors of q-point iq and (if miller_out != NULL) their Miller
+ * indices miller_out[ng][3] in the library's order.  Host pointers. */
+rpa_status rpa_gvectors(const rpa_ctx* ctx, int32_t iq, int32_t* ng,
+                        int32_t* miller_out);
+
+/* PAW augmentation functions of q-point iq (Eq. 6, Q^a_ij(q+G)):
+ * atom after atom a block Q[ni][ni][NG] (complex), G in rpa_gvectors order.
+ * natoms/nproj must match the projections of every orbital set used by iq.
+ * Q host or device. */
+rpa_status rpa_set_paw_Q(rpa_ctx* ctx, int32_t iq, int32_t natoms,
+                         const int32_t* nproj, const double* Q);
+
+/* chi0_GG'(q, i omega_j) of q-point iq (Eq. 3 summed as Eq. 17) for nw
+ * frequencies omega[nw] (host).  Pairs (n at k, m at k+q) with f_n > f_m
+ * enter with the real time-reversal-combined weight
+ *   w = s / (Omega N_k) (f_n - f_m) 2 (e_n - e_m) / (w^2 + (e_n - e_m)^2).
+ * chi_out[nw][NG][NG] (complex, full Hermitian matrix), host or device. */
+rpa_status rpa_chi0(rpa_ctx* ctx, int32_t iq, int32_t nw, const double* omega,
+                    double* chi_out);
+
+/* E_c = sum_i wq[i] sum_j W[j] / (2 pi) e_{iqs[i]}(omega_j) (Eqs. 1-2) over
+ * nq q-points; e_q(w) = ln det(1 - M) + tr M, M = v^1/2 chi0 v^1/2, by FP64
+ * Cholesky on the device.  *Ec host; terms (nullable, host) receives
+ * e_q(omega_j) as terms[nq][nw].  RPA_ERR_NOT_HPD if a Cholesky pivot is not
+ * positive. */
+rpa_status rpa_energy(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
+                      const double* wq, int32_t nw, const double* omega,
+                      const double* W, double* Ec, double* terms);
+
+/* Per-stage device timings of the most recent rpa_chi0/rpa_energy call,
+ * measured with CUDA events on the context's stream when enabled by
+ * rpa_set_profiling(ctx, 1).  Index: 0 wavefunctions to grid, 1 pair
+ * densities (+PAW), 2 rank-k update, 3 log-det, 4 other.  ms[5] total
+ * milliseconds per stage, launches[5] kernel launches per stage. */
+rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
+rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPA_GB300_H */

@@ -234,6 +234,42 @@ def chi0(problem, iq: int, omega, Qflat=None, pair_filter=None) -> np.ndarray:
     return chi
 
 
+def chi0_sampled(problem, iq: int, omega, gidx, Qflat=None, transitions=None) -> np.ndarray:
+    """Selected elements chi0_{G_a G_b}(q, i w_j) for G indices ``gidx`` of the
+    sphere: Eq. 3 evaluated only at those G (the pair densities are computed at
+    those G alone), so full-size problems can be sampled.  ``transitions``
+    restricts the k-sum to a subset of the q-point's (k, k+q) transitions.
+    Returns (nw, len(gidx), len(gidx))."""
+    qp = problem.qpoints[iq]
+    gm_all = g_sphere(problem.cell, qp.q_red, problem.ecut_chi)
+    ng_all = len(gm_all)
+    gidx = np.asarray(gidx, dtype=np.int64)
+    gm = gm_all[gidx]
+    omega = np.asarray(omega, dtype=np.float64)
+    chi = np.zeros((len(omega), len(gidx), len(gidx)), dtype=np.complex128)
+    nproj = problem.paw.nproj if problem.paw is not None else None
+    Qsub = None
+    if Qflat is not None and nproj is not None:
+        parts, off = [], 0
+        for ni in np.asarray(nproj, dtype=np.int64):
+            blk = Qflat[off:off + ni * ni * ng_all].reshape(ni * ni, ng_all)
+            parts.append(blk[:, gidx].reshape(-1))
+            off += ni * ni * ng_all
+        Qsub = np.concatenate(parts)
+    ts = range(len(qp.k_of)) if transitions is None else transitions
+    for t in ts:
+        ik, ikp, G0 = int(qp.k_of[t]), int(qp.kq_of[t]), qp.G0[t]
+        n, nsel, msel = pair_block(problem.sets, nproj, Qsub, gm, ik, ikp, G0)
+        sk, skp = problem.sets[ik], problem.sets[ikp]
+        w = pair_weights(sk.eps[nsel], sk.f[nsel], skp.eps[msel], skp.f[msel], omega,
+                         problem.spin_factor, problem.volume, problem.nk_bz)
+        N = n.reshape(len(gidx), -1)
+        W = w.reshape(-1, len(omega))
+        for j in range(len(omega)):
+            chi[j] += (N * W[:, j][None, :]) @ N.conj().T
+    return chi
+
+
 # ---------------------------------------------------------------------------
 # correlation energy (Eqs. 1-2, Table 1 step 13)
 # ---------------------------------------------------------------------------

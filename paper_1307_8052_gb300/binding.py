@@ -1,0 +1,228 @@
+"""ctypes binding of the C ABI in include/rpa.h (argument marshalling only).
+
+Every function keeps the C name.  Array arguments may be numpy arrays (host
+memory) or torch tensors (host or CUDA memory); complex arrays are passed as
+interleaved (re, im) doubles, which is the memory layout of numpy/torch
+complex128.  Errors raise ``RpaError`` carrying the status and the library's
+message.  There is no fallback: if the shared library is missing or fails to
+load, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librpa_gb300.so")
+
+RPA_OK, RPA_ERR_ARG, RPA_ERR_OOM, RPA_ERR_CUDA, RPA_ERR_NOT_HPD, RPA_ERR_TIMEOUT, RPA_ERR_STATE = range(7)
+RPA_FP64, RPA_FP32, RPA_BF16X2, RPA_BF16X3 = range(4)
+PRECISIONS = {"fp64": RPA_FP64, "fp32": RPA_FP32, "bf16x2": RPA_BF16X2, "bf16x3": RPA_BF16X3}
+STATUS_NAMES = ["RPA_OK", "RPA_ERR_ARG", "RPA_ERR_OOM", "RPA_ERR_CUDA", "RPA_ERR_NOT_HPD", "RPA_ERR_TIMEOUT",
+                "RPA_ERR_STATE"]
+
+# exported entry points and their ctypes signatures (kept in step with include/rpa.h)
+_P = ct.c_void_p
+_I = ct.c_int32
+_D = ct.c_double
+SIGNATURES = {
+    "rpa_create": (_I, [_P, _P]),
+    "rpa_destroy": (None, [_P]),
+    "rpa_last_error": (ct.c_char_p, [_P]),
+    "rpa_gauss_legendre": (_I, [_I, _D, _P, _P]),
+    "rpa_set_orbitals": (_I, [_P, _I, _P, _I, _I, _P, _P, _P, _P]),
+    "rpa_set_paw": (_I, [_P, _I, _I, _P, _P]),
+    "rpa_set_qpoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P]),
+    "rpa_gvectors": (_I, [_P, _I, _P, _P]),
+    "rpa_set_paw_Q": (_I, [_P, _I, _I, _P, _P]),
+    "rpa_chi0": (_I, [_P, _I, _I, _P, _P]),
+    "rpa_energy": (_I, [_P, _I, _P, _P, _I, _P, _P, _P, _P]),
+    "rpa_set_profiling": (_I, [_P, _I]),
+    "rpa_get_profile": (_I, [_P, _P, _P]),
+}
+
+
+class RpaParams(ct.Structure):
+    _fields_ = [("cell", ct.c_double * 9), ("grid", ct.c_int32 * 3), ("ecut_chi", ct.c_double),
+                ("spin_factor", ct.c_double), ("nk_bz", ct.c_int32), ("precision", ct.c_int32),
+                ("device", ct.c_int32), ("stream", ct.c_void_p)]
+
+
+class RpaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_1307_8052_gb300.build.build() first")
+    lib = ct.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(x, dtype=None, keep=None):
+    """Pointer to contiguous memory of x (numpy array or torch tensor)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr") and hasattr(x, "is_contiguous"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ct.c_void_p(x.data_ptr())
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if keep is not None:
+        keep.append(a)
+    return ct.c_void_p(a.ctypes.data)
+
+
+def _check(ctx, st):
+    if st != RPA_OK:
+        msg = lib().rpa_last_error(ctx).decode() if ctx else ""
+        raise RpaError(st, msg)
+
+
+# ------------------------------------------------------------------ API (same names as the C ABI)
+def rpa_create(cell, grid, ecut_chi, spin_factor=2.0, nk_bz=1, precision="fp64", device=0, stream=0):
+    p = RpaParams()
+    p.cell[:] = [float(v) for v in np.asarray(cell, dtype=np.float64).reshape(9)]
+    p.grid[:] = [int(v) for v in grid]
+    p.ecut_chi = float(ecut_chi)
+    p.spin_factor = float(spin_factor)
+    p.nk_bz = int(nk_bz)
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.device = int(device)
+    p.stream = ct.c_void_p(int(stream)) if stream else None
+    out = ct.c_void_p()
+    st = lib().rpa_create(ct.byref(p), ct.byref(out))
+    _check(None, st)
+    return out
+
+
+def rpa_destroy(ctx):
+    lib().rpa_destroy(ctx)
+
+
+def rpa_last_error(ctx) -> str:
+    return lib().rpa_last_error(ctx).decode()
+
+
+def rpa_gauss_legendre(n, omega0=1.0):
+    om = np.zeros(n)
+    W = np.zeros(n)
+    _check(None, lib().rpa_gauss_legendre(int(n), float(omega0), om.ctypes.data_as(_P), W.ctypes.data_as(_P)))
+    return om, W
+
+
+def rpa_set_orbitals(ctx, kidx, k_red, miller, C, eps, f):
+    keep = []
+    nb, npw = int(C.shape[0]), int(C.shape[1])
+    st = lib().rpa_set_orbitals(ctx, int(kidx), _ptr(k_red, np.float64, keep), nb, npw,
+                                _ptr(miller, np.int32, keep), _ptr(C, np.complex128, keep),
+                                _ptr(eps, np.float64, keep), _ptr(f, np.float64, keep))
+    _check(ctx, st)
+
+
+def rpa_set_paw(ctx, kidx, nproj, P):
+    keep = []
+    nproj = np.asarray(nproj, dtype=np.int32)
+    _check(ctx, lib().rpa_set_paw(ctx, int(kidx), len(nproj), _ptr(nproj, np.int32, keep),
+                                  _ptr(P, np.complex128, keep)))
+
+
+def rpa_set_qpoint(ctx, iq, q_red, k_of, kq_of, G0) -> int:
+    keep = []
+    ng = ct.c_int32()
+    k_of = np.asarray(k_of, dtype=np.int32)
+    st = lib().rpa_set_qpoint(ctx, int(iq), _ptr(q_red, np.float64, keep), len(k_of), _ptr(k_of, np.int32, keep),
+                              _ptr(kq_of, np.int32, keep), _ptr(np.asarray(G0).reshape(-1, 3), np.int32, keep),
+                              ct.byref(ng))
+    _check(ctx, st)
+    return ng.value
+
+
+def rpa_gvectors(ctx, iq) -> np.ndarray:
+    ng = ct.c_int32()
+    _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
+    out = np.zeros((ng.value, 3), dtype=np.int32)
+    _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), out.ctypes.data_as(_P)))
+    return out
+
+
+def rpa_set_paw_Q(ctx, iq, nproj, Q):
+    keep = []
+    nproj = np.asarray(nproj, dtype=np.int32)
+    _check(ctx, lib().rpa_set_paw_Q(ctx, int(iq), len(nproj), _ptr(nproj, np.int32, keep),
+                                    _ptr(Q, np.complex128, keep)))
+
+
+def rpa_chi0(ctx, iq, omega, out=None):
+    """chi0[nw][NG][NG] complex128; ``out`` may be a preallocated numpy array or CUDA tensor."""
+    keep = []
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    if out is None:
+        ng = ct.c_int32()
+        _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
+        out = np.zeros((len(omega), ng.value, ng.value), dtype=np.complex128)
+    _check(ctx, lib().rpa_chi0(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), _ptr(out, None, keep)))
+    return out
+
+
+def rpa_energy(ctx, iqs, wq, omega, W):
+    """Returns (E_c, terms[nq][nw])."""
+    keep = []
+    iqs = np.ascontiguousarray(iqs, dtype=np.int32)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    terms = np.zeros((len(iqs), len(omega)))
+    E = ct.c_double()
+    st = lib().rpa_energy(ctx, len(iqs), _ptr(iqs, np.int32, keep), _ptr(wq, np.float64, keep), len(omega),
+                          _ptr(omega, np.float64, keep), _ptr(W, np.float64, keep), ct.byref(E),
+                          terms.ctypes.data_as(_P))
+    _check(ctx, st)
+    return E.value, terms
+
+
+def rpa_set_profiling(ctx, enable=True):
+    _check(ctx, lib().rpa_set_profiling(ctx, 1 if enable else 0))
+
+
+def rpa_get_profile(ctx):
+    ms = np.zeros(5)
+    nl = np.zeros(5, dtype=np.int64)
+    _check(ctx, lib().rpa_get_profile(ctx, ms.ctypes.data_as(_P), nl.ctypes.data_as(_P)))
+    return ms, nl
+
+
+# ------------------------------------------------------------------ convenience
+def load_problem(ctx, problem, qs=None, paw_Q=None):
+    """Upload every orbital set, projection set and q-point of a Problem-like object.
+    ``paw_Q(iq, gmiller) -> flat Q`` supplies augmentation functions per q."""
+    for i, s in enumerate(problem.sets):
+        rpa_set_orbitals(ctx, i, s.k_red, s.miller, s.C, s.eps, s.f)
+        if s.P is not None and problem.paw is not None:
+            rpa_set_paw(ctx, i, problem.paw.nproj, s.P)
+    ngs = []
+    for iq, qp in enumerate(problem.qpoints):
+        if qs is not None and iq not in qs:
+            continue
+        ngs.append(rpa_set_qpoint(ctx, iq, qp.q_red, qp.k_of, qp.kq_of, qp.G0))
+        if paw_Q is not None and problem.paw is not None:
+            rpa_set_paw_Q(ctx, iq, problem.paw.nproj, paw_Q(iq, rpa_gvectors(ctx, iq)))
+    return ngs

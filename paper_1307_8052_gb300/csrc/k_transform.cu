@@ -1,0 +1,340 @@
+// Plane-wave <-> real-space transforms of the RPA hot path, without cuFFT.
+//
+//  * Wavefunctions to the grid (Eq. 8; Table 1 step 3): the coefficients are
+//    scattered into their Miller box and transformed axis by axis with pruned
+//    DFTs (only the occupied Miller range is summed).
+//  * Pair densities (Eq. 10; Table 1 steps 5-6): the product
+//    conj(u_nk(r)) u_m,k+q(r) is fused into the first (slowest-axis) DFT, the
+//    middle axis follows, and the fastest axis is evaluated only on the
+//    response sphere g = G + G0 (the "mapG" gather of step 6 fused into the
+//    transform).  The PAW term of Eq. 6 (steps 8-9) is added in the same
+//    epilogue from the factorised form sum_(a,j) P_mj R^a_n(j,G) with
+//    R^a_n(j,G) = sum_i conj(P_ni) Q^a_ij(G), which equals the paper's
+//    outer-product-then-contract order exactly in exact arithmetic.
+//
+// Twiddles come from a table tw[t] = exp(2 pi i t / N), t in [0, N), filled
+// with sincospi in double precision; every phase index is reduced exactly in
+// integer arithmetic, so no angle is ever rounded before the table lookup.
+#include "rpa_internal.h"
+
+namespace rpa {
+
+static inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+__host__ __device__ inline int pmod(int64_t a, int n) {
+  int64_t r = a % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+template <typename T>
+__device__ inline void fill_twiddles(c2<T>* tw, int N) {
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)N, &s, &c);
+    tw[t] = mk<T>((T)c, (T)s);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- generic axis DFT
+template <typename T, int TO>
+__global__ void __launch_bounds__(256) dft_axis_kernel(const c2<T>* __restrict__ in, c2<T>* __restrict__ out,
+                                                       int64_t rows, int Lin, int Lout, int B, int N,
+                                                       int in_off, int out_off, int sign) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  fill_twiddles<T>(tw, N);
+  const int nchunk = (Lout + TO - 1) / TO;
+  const int64_t total = rows * nchunk * (int64_t)B;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(id % B);
+    int64_t r = id / B;
+    const int oc = (int)(r % nchunk);
+    r /= nchunk;
+    const int o0 = oc * TO;
+    int idx[TO], step[TO];
+    c2<T> acc[TO];
+#pragma unroll
+    for (int t = 0; t < TO; ++t) {
+      const int64_t j = out_off + o0 + t;
+      step[t] = pmod(sign * j, N);
+      idx[t] = pmod(sign * (int64_t)in_off * j, N);
+      acc[t] = mk<T>(0, 0);
+    }
+    const c2<T>* src = in + (r * Lin) * B + c;
+    for (int i = 0; i < Lin; ++i) {
+      const c2<T> x = src[(int64_t)i * B];
+#pragma unroll
+      for (int t = 0; t < TO; ++t) {
+        cmac<T>(acc[t], x, tw[idx[t]]);
+        idx[t] += step[t];
+        if (idx[t] >= N) idx[t] -= N;
+      }
+    }
+    c2<T>* dst = out + (r * Lout + o0) * B + c;
+#pragma unroll
+    for (int t = 0; t < TO; ++t)
+      if (o0 + t < Lout) dst[(int64_t)t * B] = acc[t];
+  }
+}
+
+template <typename T>
+cudaError_t launch_dft_axis(const c2<T>* in, c2<T>* out, int64_t batch, int A, int Lin, int Lout,
+                            int B, int N, int in_off, int out_off, int sign, cudaStream_t s) {
+  constexpr int TO = 4;
+  const int64_t rows = batch * A;
+  const int64_t total = rows * ((Lout + TO - 1) / TO) * (int64_t)B;
+  if (total == 0) return cudaSuccess;
+  dft_axis_kernel<T, TO><<<grid_for(total, 256), 256, N * sizeof(c2<T>), s>>>(in, out, rows, Lin, Lout, B, N,
+                                                                            in_off, out_off, sign);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scatter into Miller box
+template <typename T>
+__global__ void scatter_box_kernel(const double2* __restrict__ C, int nb, int npw, const int* __restrict__ pos,
+                                   int64_t box, c2<T>* __restrict__ out) {
+  const int64_t total = (int64_t)nb * npw;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(id / npw);
+    const int q = (int)(id % npw);
+    const double2 v = C[id];
+    out[(int64_t)b * box + pos[q]] = mk<T>((T)v.x, (T)v.y);
+  }
+}
+
+template <typename T>
+cudaError_t launch_scatter_box(const double2* C, int nb, int npw, const int* pos, int64_t box, c2<T>* out,
+                               cudaStream_t s) {
+  const int64_t total = (int64_t)nb * npw;
+  if (total == 0) return cudaSuccess;
+  scatter_box_kernel<T><<<grid_for(total, 256), 256, 0, s>>>(C, nb, npw, pos, box, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pair density stage A
+// T1[pl][o][j23] = sum_j1 conj(u_n(j1, j23)) u_m(j1, j23) exp(-2 pi i g1 j1 / N1), g1 = g1lo + o
+template <typename T, int TO>
+__global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
+                                                        int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
+                                                        const int* __restrict__ Ridx, int nR, int64_t p0, int np,
+                                                        int g1lo, int n1, c2<T>* __restrict__ T1) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  fill_twiddles<T>(tw, N1);
+  const int nchunk = (n1 + TO - 1) / TO;
+  const int64_t total = (int64_t)np * nchunk * N23;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int j23 = (int)(id % N23);
+    int64_t r = id / N23;
+    const int oc = (int)(r % nchunk);
+    const int pl = (int)(r / nchunk);
+    const int64_t p = p0 + pl;
+    const int n = Lidx[p / nR];
+    const int m = Ridx[p % nR];
+    const c2<T>* un = Uk + (int64_t)n * Nr + j23;
+    const c2<T>* um = Ukp + (int64_t)m * Nr + j23;
+    const int o0 = oc * TO;
+    int idx[TO], step[TO];
+    c2<T> acc[TO];
+#pragma unroll
+    for (int t = 0; t < TO; ++t) {
+      step[t] = pmod(-(int64_t)(g1lo + o0 + t), N1);
+      idx[t] = 0;
+      acc[t] = mk<T>(0, 0);
+    }
+    for (int j1 = 0; j1 < N1; ++j1) {
+      const c2<T> x = cj_mul<T>(un[(int64_t)j1 * N23], um[(int64_t)j1 * N23]);
+#pragma unroll
+      for (int t = 0; t < TO; ++t) {
+        cmac<T>(acc[t], x, tw[idx[t]]);
+        idx[t] += step[t];
+        if (idx[t] >= N1) idx[t] -= N1;
+      }
+    }
+    c2<T>* dst = T1 + ((int64_t)pl * n1 + o0) * N23 + j23;
+#pragma unroll
+    for (int t = 0; t < TO; ++t)
+      if (o0 + t < n1) dst[(int64_t)t * N23] = acc[t];
+  }
+}
+
+template <typename T>
+cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+                             const int* Ridx, int nR, int64_t p0, int np, int g1lo, int n1, c2<T>* T1,
+                             cudaStream_t s) {
+  constexpr int TO = 8;
+  const int64_t total = (int64_t)np * ((n1 + TO - 1) / TO) * N23;
+  if (total == 0) return cudaSuccess;
+  pd_stageA_kernel<T, TO><<<grid_for(total, 256), 256, N1 * sizeof(c2<T>), s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx,
+                                                                              nR, p0, np, g1lo, n1, T1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pair density stage C (+ PAW)
+template <typename T>
+__global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict__ T2, int np, int n1, int n2, int N3,
+                                                        const int* __restrict__ gfft, int NG, int g1lo, int g2lo,
+                                                        double inv_nr, const c2<T>* __restrict__ R,
+                                                        const c2<T>* __restrict__ Pm, int KP,
+                                                        const int* __restrict__ Ridx, int nR, int64_t p0,
+                                                        c2<T>* __restrict__ Nout) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  fill_twiddles<T>(tw, N3);
+  const int64_t total = (int64_t)np * NG;
+  const T scale = (T)inv_nr;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int ig = (int)(id % NG);
+    const int pl = (int)(id / NG);
+    const int g1 = gfft[3 * ig], g2 = gfft[3 * ig + 1], g3 = gfft[3 * ig + 2];
+    const c2<T>* src = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
+    const int step = pmod(-(int64_t)g3, N3);
+    int idx = 0;
+    c2<T> acc = mk<T>(0, 0);
+    for (int j3 = 0; j3 < N3; ++j3) {
+      cmac<T>(acc, src[j3], tw[idx]);
+      idx += step;
+      if (idx >= N3) idx -= N3;
+    }
+    acc.x *= scale;
+    acc.y *= scale;
+    const int64_t p = p0 + pl;
+    if (KP > 0) {
+      const int64_t a = p / nR;
+      const int64_t b = p % nR;
+      const c2<T>* pm = Pm + b * KP;
+      const c2<T>* rr = R + a * (int64_t)KP * NG + ig;
+      for (int kp = 0; kp < KP; ++kp) cmac<T>(acc, pm[kp], rr[(int64_t)kp * NG]);
+    }
+    Nout[p * NG + ig] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft, int NG, int g1lo,
+                             int g2lo, double inv_nr, const c2<T>* R, const c2<T>* Pm, int KP, const int* Ridx,
+                             int nR, int64_t p0, c2<T>* Nout, cudaStream_t s) {
+  const int64_t total = (int64_t)np * NG;
+  if (total == 0) return cudaSuccess;
+  pd_stageC_kernel<T><<<grid_for(total, 256), 256, N3 * sizeof(c2<T>), s>>>(T2, np, n1, n2, N3, gfft, NG, g1lo, g2lo,
+                                                                          inv_nr, R, Pm, KP, Ridx, nR, p0, Nout);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- PAW factor (FP64)
+template <typename T>
+__global__ void paw_R_kernel(const double2* __restrict__ Pk, int KP, const int* __restrict__ Lidx, int nL,
+                             const double2* __restrict__ Q, const int* __restrict__ atom_of_kp,
+                             const int* __restrict__ idx_in_atom, const int* __restrict__ atom_off,
+                             const int64_t* __restrict__ q_off, const int* __restrict__ nproj, int NG,
+                             c2<T>* __restrict__ R) {
+  const int64_t total = (int64_t)nL * KP * NG;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int ig = (int)(id % NG);
+    int64_t r = id / NG;
+    const int kp = (int)(r % KP);
+    const int a = (int)(r / KP);
+    const int atom = atom_of_kp[kp];
+    const int j = idx_in_atom[kp];
+    const int ni = nproj[atom];
+    const double2* pn = Pk + (int64_t)Lidx[a] * KP + atom_off[atom];
+    const double2* qa = Q + q_off[atom] + (int64_t)j * NG + ig;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < ni; ++i) {
+      // conj(P_ni) * Q_ij(G)
+      const double2 p = pn[i];
+      const double2 q = qa[(int64_t)i * ni * NG];
+      acc.x = fma(p.x, q.x, acc.x);
+      acc.x = fma(p.y, q.y, acc.x);
+      acc.y = fma(p.x, q.y, acc.y);
+      acc.y = fma(-p.y, q.x, acc.y);
+    }
+    R[id] = mk<T>((T)acc.x, (T)acc.y);
+  }
+}
+
+template <typename T>
+cudaError_t launch_paw_R(const double2* Pk, int KP, const int* Lidx, int nL, const double2* Q, const int* atom_of_kp,
+                         const int* idx_in_atom, const int* atom_off, const int64_t* q_off, const int* nproj, int NG,
+                         c2<T>* R, cudaStream_t s) {
+  const int64_t total = (int64_t)nL * KP * NG;
+  if (total == 0) return cudaSuccess;
+  paw_R_kernel<T><<<grid_for(total, 256), 256, 0, s>>>(Pk, KP, Lidx, nL, Q, atom_of_kp, idx_in_atom, atom_off, q_off,
+                                                       nproj, NG, R);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void gather_P_kernel(const double2* __restrict__ P, int KP, const int* __restrict__ Ridx, int nR,
+                                c2<T>* __restrict__ out) {
+  const int64_t total = (int64_t)nR * KP;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int kp = (int)(id % KP);
+    const int b = (int)(id / KP);
+    const double2 v = P[(int64_t)Ridx[b] * KP + kp];
+    out[id] = mk<T>((T)v.x, (T)v.y);
+  }
+}
+
+template <typename T>
+cudaError_t launch_gather_P(const double2* P, int KP, const int* Ridx, int nR, c2<T>* out, cudaStream_t s) {
+  const int64_t total = (int64_t)nR * KP;
+  if (total == 0) return cudaSuccess;
+  gather_P_kernel<T><<<grid_for(total, 256), 256, 0, s>>>(P, KP, Ridx, nR, out);
+  return cudaGetLastError();
+}
+
+__global__ void pair_params_kernel(const double* __restrict__ ek, const double* __restrict__ fk,
+                                   const double* __restrict__ ekp, const double* __restrict__ fkp,
+                                   const int* __restrict__ Lidx, int nL, const int* __restrict__ Ridx, int nR,
+                                   double* __restrict__ d, double* __restrict__ df) {
+  const int64_t total = (int64_t)nL * nR;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int n = Lidx[id / nR];
+    const int m = Ridx[id % nR];
+    d[id] = ek[n] - ekp[m];
+    const double x = fk[n] - fkp[m];
+    df[id] = x > 0.0 ? x : 0.0;
+  }
+}
+
+cudaError_t launch_pair_params(const double* ek, const double* fk, const double* ekp, const double* fkp,
+                               const int* Lidx, int nL, const int* Ridx, int nR, double* d, double* df,
+                               cudaStream_t s) {
+  const int64_t total = (int64_t)nL * nR;
+  if (total == 0) return cudaSuccess;
+  pair_params_kernel<<<grid_for(total, 256), 256, 0, s>>>(ek, fk, ekp, fkp, Lidx, nL, Ridx, nR, d, df);
+  return cudaGetLastError();
+}
+
+#define RPA_INST(T)                                                                                              \
+  template cudaError_t launch_dft_axis<T>(const c2<T>*, c2<T>*, int64_t, int, int, int, int, int, int, int, int, \
+                                          cudaStream_t);                                                         \
+  template cudaError_t launch_scatter_box<T>(const double2*, int, int, const int*, int64_t, c2<T>*, cudaStream_t); \
+  template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
+                                           int, int64_t, int, int, int, c2<T>*, cudaStream_t);                   \
+  template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \
+                                           const c2<T>*, const c2<T>*, int, const int*, int, int64_t, c2<T>*,      \
+                                           cudaStream_t);                                                        \
+  template cudaError_t launch_paw_R<T>(const double2*, int, const int*, int, const double2*, const int*,          \
+                                       const int*, const int*, const int64_t*, const int*, int, c2<T>*,          \
+                                       cudaStream_t);                                                            \
+  template cudaError_t launch_gather_P<T>(const double2*, int, const int*, int, c2<T>*, cudaStream_t);
+
+RPA_INST(float)
+RPA_INST(double)
+
+}  // namespace rpa

@@ -1,0 +1,836 @@
+// Host runtime of the C ABI declared in include/rpa.h: context, argument
+// validation, device memory, and the orchestration of the hot path
+//   wavefunctions -> grid (Eq. 8), pair densities + PAW (Eqs. 4, 6, 10),
+//   grouped rank-k update (Eq. 17), log-det + quadrature (Eqs. 1-2).
+// Every arithmetic step runs in the CUDA kernels; the host only builds index
+// lists (G spheres, Miller boxes, pair selections) and launches.
+#include "rpa.h"
+#include "rpa_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace rpa {
+cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms,
+                           double2* chi, void* scratch, size_t scratch_bytes, cudaStream_t s);
+size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
+}
+
+using namespace rpa;
+
+namespace {
+
+constexpr int kMaxIndex = 4096;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct OrbSet {
+  bool valid = false;
+  double k[3] = {0, 0, 0};
+  int nb = 0, npw = 0;
+  std::vector<int> miller;
+  std::vector<double> eps, f;
+  int mlo[3] = {0, 0, 0}, mhi[3] = {0, 0, 0};
+  double2* C = nullptr;
+  double* eps_d = nullptr;
+  double* f_d = nullptr;
+  int* pos_d = nullptr;  // flat Miller-box position of each plane wave
+  std::vector<int> L, R;  // bands with f > 0 (left of a pair), f < 1 (right)
+  int* L_d = nullptr;
+  int* R_d = nullptr;
+  int natoms = 0;
+  std::vector<int> nproj;
+  int KP = 0;
+  double2* P = nullptr;
+  void* U = nullptr;  // grids [nb][Nr] in working precision (valid while grid_stamp == ctx stamp)
+  uint64_t grid_stamp = 0;
+};
+
+struct QPt {
+  bool valid = false;
+  double q[3] = {0, 0, 0};
+  std::vector<int> k_of, kq_of, G0;
+  int NG = 0;
+  std::vector<int> gm;  // [NG][3]
+  std::vector<double> v;
+  double* v_d = nullptr;
+  int natoms = 0;
+  std::vector<int> nproj;
+  double2* Q = nullptr;
+};
+
+}  // namespace
+
+struct rpa_ctx {
+  rpa_params prm{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double B[9] = {0};  // reciprocal rows
+  double volume = 0.0;
+  std::string err;
+  std::map<int, OrbSet> sets;
+  std::map<int, QPt> qpts;
+  std::map<std::string, DevBuf> ws;
+  uint64_t stamp = 0;
+  bool profiling = false;
+  double prof_ms[5] = {0};
+  int64_t prof_launch[5] = {0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+rpa_status fail(rpa_ctx* c, rpa_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define CUDA_OK(ctx, call)                                                                          \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      if (e_ == cudaErrorMemoryAllocation) return fail(ctx, RPA_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return fail(ctx, RPA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                       \
+    }                                                                                               \
+  } while (0)
+
+rpa_status dev_alloc(rpa_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return RPA_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, RPA_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return RPA_OK;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+rpa_status workspace(rpa_ctx* c, const char* name, size_t bytes, void** out) {
+  DevBuf& b = c->ws[name];
+  if (b.cap < bytes) {
+    dev_free(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = bytes + bytes / 8;
+    rpa_status st = dev_alloc(c, &b.p, want);
+    if (st != RPA_OK) return st;
+    b.cap = want;
+  }
+  *out = b.p;
+  return RPA_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+rpa_status copy_in(rpa_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return RPA_OK;
+  const cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_OK(c, cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+  return RPA_OK;
+}
+
+void inv3(const double* m, double* out) {
+  const double a = m[0], b = m[1], cc = m[2], d = m[3], e = m[4], f = m[5], g = m[6], h = m[7], i = m[8];
+  const double A = e * i - f * h, Bc = -(d * i - f * g), Cc = d * h - e * g;
+  const double det = a * A + b * Bc + cc * Cc;
+  out[0] = A / det;
+  out[3] = Bc / det;
+  out[6] = Cc / det;
+  out[1] = -(b * i - cc * h) / det;
+  out[4] = (a * i - cc * g) / det;
+  out[7] = -(a * h - b * g) / det;
+  out[2] = (b * f - cc * e) / det;
+  out[5] = -(a * f - cc * d) / det;
+  out[8] = (a * e - b * d) / det;
+}
+
+// ---- profiling helpers (CUDA events on the context stream)
+void prof_begin(rpa_ctx* c) {
+  for (int i = 0; i < 5; ++i) {
+    c->prof_ms[i] = 0;
+    c->prof_launch[i] = 0;
+  }
+  c->ev.clear();
+  c->ev_used = 0;
+}
+cudaEvent_t next_event(rpa_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+struct StageTimer {
+  rpa_ctx* c;
+  int stage;
+  cudaEvent_t a = nullptr;
+  StageTimer(rpa_ctx* cc, int s, int64_t launches) : c(cc), stage(s) {
+    c->prof_launch[s] += launches;
+    if (c->profiling) {
+      a = next_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  void add_launches(int64_t n) { c->prof_launch[stage] += n; }
+  ~StageTimer() {
+    if (c->profiling) {
+      cudaEvent_t b = next_event(c);
+      cudaEventRecord(b, c->stream);
+      c->ev.push_back({stage, {a, b}});
+    }
+  }
+};
+void prof_end(rpa_ctx* c) {
+  if (!c->profiling) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& e : c->ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess) c->prof_ms[e.first] += ms;
+  }
+  c->ev.clear();
+}
+
+int work_bytes_per_complex(const rpa_ctx* c) { return c->prm.precision == RPA_FP64 ? 16 : 8; }
+
+// ---- stage a1: every band of a set onto the real-space grid (Eq. 8, Table 1 step 3)
+template <typename T>
+rpa_status build_grids_T(rpa_ctx* c, OrbSet& s) {
+  const int N1 = c->prm.grid[0], N2 = c->prm.grid[1], N3 = c->prm.grid[2];
+  const int64_t Nr = (int64_t)N1 * N2 * N3;
+  const size_t need = sizeof(c2<T>) * (size_t)s.nb * Nr;
+  if (!s.U) {
+    rpa_status st = dev_alloc(c, &s.U, need);
+    if (st != RPA_OK) return st;
+  }
+  const int L1 = s.mhi[0] - s.mlo[0] + 1, L2 = s.mhi[1] - s.mlo[1] + 1, L3 = s.mhi[2] - s.mlo[2] + 1;
+  const int64_t box = (int64_t)L1 * L2 * L3;
+  // process bands in batches so the intermediates stay modest
+  const int64_t per_band = box + (int64_t)L1 * L2 * N3 + (int64_t)L1 * N2 * N3;
+  int64_t nbat = std::max<int64_t>(1, std::min<int64_t>(s.nb, (int64_t)(256ll << 20) / (per_band * (int64_t)sizeof(c2<T>))));
+  void* wsp;
+  rpa_status st = workspace(c, "grid_tmp", sizeof(c2<T>) * (size_t)(nbat * per_band), &wsp);
+  if (st != RPA_OK) return st;
+  c2<T>* bx = (c2<T>*)wsp;
+  c2<T>* x1 = bx + nbat * box;
+  c2<T>* x2 = x1 + nbat * (int64_t)L1 * L2 * N3;
+  StageTimer tm(c, 0, 0);
+  for (int64_t b0 = 0; b0 < s.nb; b0 += nbat) {
+    const int nbb = (int)std::min<int64_t>(nbat, s.nb - b0);
+    CUDA_OK(c, cudaMemsetAsync(bx, 0, sizeof(c2<T>) * (size_t)(nbb * box), c->stream));
+    CUDA_OK(c, launch_scatter_box<T>(s.C + b0 * s.npw, nbb, s.npw, s.pos_d, box, bx, c->stream));
+    // axis 3 (fastest): Miller m3 -> j3
+    CUDA_OK(c, launch_dft_axis<T>(bx, x1, nbb, L1 * L2, L3, N3, 1, N3, s.mlo[2], 0, +1, c->stream));
+    // axis 2: m2 -> j2
+    CUDA_OK(c, launch_dft_axis<T>(x1, x2, nbb, L1, L2, N2, N3, N2, s.mlo[1], 0, +1, c->stream));
+    // axis 1: m1 -> j1, straight into the band's grid
+    CUDA_OK(c, launch_dft_axis<T>(x2, (c2<T>*)s.U + b0 * Nr, nbb, 1, L1, N1, N2 * N3, N1, s.mlo[0], 0, +1,
+                                  c->stream));
+    tm.add_launches(4);
+  }
+  s.grid_stamp = c->stamp;
+  return RPA_OK;
+}
+
+rpa_status build_grids(rpa_ctx* c, OrbSet& s) {
+  if (s.grid_stamp == c->stamp && s.U) return RPA_OK;
+  if (c->prm.precision == RPA_FP64) return build_grids_T<double>(c, s);
+  return build_grids_T<float>(c, s);
+}
+
+// ---- stages a2-a4 for one q-point: chi accumulates in FP64 lower triangle
+template <typename T>
+rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, double2* chi) {
+  OrbSet& sk = c->sets[Q.k_of[t]];
+  OrbSet& skp = c->sets[Q.kq_of[t]];
+  const int nL = (int)sk.L.size(), nR = (int)skp.R.size();
+  const int64_t P = (int64_t)nL * nR;
+  if (P == 0) return RPA_OK;
+  const int N1 = c->prm.grid[0], N2 = c->prm.grid[1], N3 = c->prm.grid[2];
+  const int64_t Nr = (int64_t)N1 * N2 * N3;
+  const int NG = Q.NG;
+  const int* G0 = &Q.G0[3 * t];
+  // target Fourier indices g = G + G0 and their box
+  std::vector<int> gfft(3 * (size_t)NG);
+  int glo[3] = {1 << 30, 1 << 30, 1 << 30}, ghi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int i = 0; i < NG; ++i)
+    for (int d = 0; d < 3; ++d) {
+      const int g = Q.gm[3 * i + d] + G0[d];
+      gfft[3 * i + d] = g;
+      glo[d] = std::min(glo[d], g);
+      ghi[d] = std::max(ghi[d], g);
+    }
+  const int n1 = ghi[0] - glo[0] + 1, n2 = ghi[1] - glo[1] + 1;
+  void *p_gfft, *p_d, *p_df, *p_w, *p_N, *p_T1, *p_T2;
+  rpa_status st;
+  if ((st = workspace(c, "gfft", sizeof(int) * gfft.size(), &p_gfft)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemcpyAsync(p_gfft, gfft.data(), sizeof(int) * gfft.size(), cudaMemcpyHostToDevice, c->stream));
+  if ((st = workspace(c, "pair_d", sizeof(double) * P, &p_d)) != RPA_OK) return st;
+  if ((st = workspace(c, "pair_df", sizeof(double) * P, &p_df)) != RPA_OK) return st;
+  if ((st = workspace(c, "pair_w", sizeof(T) * P * nw, &p_w)) != RPA_OK) return st;
+  if ((st = workspace(c, "Nmat", sizeof(c2<T>) * (size_t)P * NG, &p_N)) != RPA_OK) return st;
+  const double pref = c->prm.spin_factor / (c->volume * (double)c->prm.nk_bz);
+  {
+    StageTimer tm(c, 4, 2);
+    CUDA_OK(c, launch_pair_params(sk.eps_d, sk.f_d, skp.eps_d, skp.f_d, sk.L_d, nL, skp.R_d, nR, (double*)p_d,
+                                  (double*)p_df, c->stream));
+    CUDA_OK(c, launch_pair_weights((double*)p_d, (double*)p_df, omega_d, nw, P, pref,
+                                   sizeof(T) == 8 ? (double*)p_w : nullptr, sizeof(T) == 4 ? (float*)p_w : nullptr,
+                                   c->stream));
+  }
+  // PAW factors (FP64 arithmetic, stored in working precision)
+  c2<T>* Rp = nullptr;
+  c2<T>* Pm = nullptr;
+  int KP = 0;
+  const bool paw = Q.Q && sk.P && skp.P && Q.natoms > 0;
+  if (paw) {
+    if (sk.nproj != Q.nproj || skp.nproj != Q.nproj)
+      return fail(c, RPA_ERR_ARG, "PAW projector counts of the orbital sets do not match Q of this q-point");
+    KP = sk.KP;
+    std::vector<int> atom_of(KP), idx_in(KP), atom_off(Q.natoms);
+    std::vector<int64_t> q_off(Q.natoms);
+    int off = 0;
+    int64_t qo = 0;
+    for (int a = 0; a < Q.natoms; ++a) {
+      atom_off[a] = off;
+      q_off[a] = qo;
+      for (int j = 0; j < Q.nproj[a]; ++j) {
+        atom_of[off + j] = a;
+        idx_in[off + j] = j;
+      }
+      off += Q.nproj[a];
+      qo += (int64_t)Q.nproj[a] * Q.nproj[a] * NG;
+    }
+    void *p_meta, *p_R, *p_Pm;
+    const size_t meta_bytes = sizeof(int) * (2 * KP + 2 * Q.natoms) + sizeof(int64_t) * Q.natoms;
+    if ((st = workspace(c, "paw_meta", meta_bytes, &p_meta)) != RPA_OK) return st;
+    std::vector<char> meta(meta_bytes);
+    char* mp = meta.data();
+    memcpy(mp, q_off.data(), sizeof(int64_t) * Q.natoms);
+    memcpy(mp + sizeof(int64_t) * Q.natoms, atom_of.data(), sizeof(int) * KP);
+    memcpy(mp + sizeof(int64_t) * Q.natoms + sizeof(int) * KP, idx_in.data(), sizeof(int) * KP);
+    memcpy(mp + sizeof(int64_t) * Q.natoms + sizeof(int) * 2 * KP, atom_off.data(), sizeof(int) * Q.natoms);
+    memcpy(mp + sizeof(int64_t) * Q.natoms + sizeof(int) * (2 * KP + Q.natoms), Q.nproj.data(),
+           sizeof(int) * Q.natoms);
+    CUDA_OK(c, cudaMemcpyAsync(p_meta, meta.data(), meta_bytes, cudaMemcpyHostToDevice, c->stream));
+    const char* md = (const char*)p_meta;
+    const int64_t* q_off_d = (const int64_t*)md;
+    const int* atom_of_d = (const int*)(md + sizeof(int64_t) * Q.natoms);
+    const int* idx_in_d = atom_of_d + KP;
+    const int* atom_off_d = idx_in_d + KP;
+    const int* nproj_d = atom_off_d + Q.natoms;
+    if ((st = workspace(c, "paw_R", sizeof(c2<T>) * (size_t)nL * KP * NG, &p_R)) != RPA_OK) return st;
+    if ((st = workspace(c, "paw_Pm", sizeof(c2<T>) * (size_t)nR * KP, &p_Pm)) != RPA_OK) return st;
+    Rp = (c2<T>*)p_R;
+    Pm = (c2<T>*)p_Pm;
+    StageTimer tm(c, 1, 2);
+    CUDA_OK(c, launch_paw_R<T>(sk.P, KP, sk.L_d, nL, Q.Q, atom_of_d, idx_in_d, atom_off_d, q_off_d, nproj_d, NG, Rp,
+                               c->stream));
+    CUDA_OK(c, launch_gather_P<T>(skp.P, KP, skp.R_d, nR, Pm, c->stream));
+  }
+  // pair densities in chunks of pairs (intermediates sized to stay in L2)
+  const int64_t N23 = (int64_t)N2 * N3;
+  const int64_t per_pair = (int64_t)n1 * N23 + (int64_t)n1 * n2 * N3;
+  const int64_t budget = (sizeof(T) == 8 ? 160ll : 96ll) << 20;
+  int64_t PC = std::max<int64_t>(32, budget / (per_pair * (int64_t)sizeof(c2<T>)));
+  PC = std::min<int64_t>(PC, P);
+  if ((st = workspace(c, "pd_T1", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * N23), &p_T1)) != RPA_OK) return st;
+  if ((st = workspace(c, "pd_T2", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * n2 * N3), &p_T2)) != RPA_OK) return st;
+  {
+    StageTimer tm(c, 1, 0);
+    for (int64_t p0 = 0; p0 < P; p0 += PC) {
+      const int np = (int)std::min<int64_t>(PC, P - p0);
+      CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, sk.L_d, skp.R_d, nR,
+                                     p0, np, glo[0], n1, (c2<T>*)p_T1, c->stream));
+      CUDA_OK(c, launch_dft_axis<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, n2, N3, N2, 0, glo[1], -1,
+                                    c->stream));
+      CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
+                                     1.0 / (double)Nr, Rp, Pm, KP, skp.R_d, nR, p0, (c2<T>*)p_N, c->stream));
+      tm.add_launches(3);
+    }
+  }
+  // grouped rank-k update for every frequency
+  {
+    StageTimer tm(c, 2, 1);
+    const int prec = c->prm.precision;
+    if (prec == RPA_FP64 || prec == RPA_FP32) {
+      CUDA_OK(c, launch_herk_simt_w<T>((const c2<T>*)p_N, P, NG, (const T*)p_w, nw, chi, c->stream));
+    } else {
+      const int terms = prec == RPA_BF16X3 ? 3 : 2;
+      void* scr = nullptr;
+      const size_t sb = herk_tc_scratch_bytes(P, NG, nw, terms);
+      if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
+      CUDA_OK(c, launch_herk_tc((const float2*)p_N, P, NG, (const float*)p_w, nw, terms, chi, scr, sb, c->stream));
+    }
+  }
+  return RPA_OK;
+}
+
+rpa_status check_q_ready(rpa_ctx* c, int iq) {
+  auto it = c->qpts.find(iq);
+  if (it == c->qpts.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "q-point %d not set", iq);
+  QPt& Q = it->second;
+  for (size_t t = 0; t < Q.k_of.size(); ++t) {
+    auto a = c->sets.find(Q.k_of[t]);
+    auto b = c->sets.find(Q.kq_of[t]);
+    if (a == c->sets.end() || !a->second.valid || b == c->sets.end() || !b->second.valid)
+      return fail(c, RPA_ERR_STATE, "q-point %d references an orbital set that is not set", iq);
+  }
+  return RPA_OK;
+}
+
+rpa_status build_chi(rpa_ctx* c, int iq, int nw, const double* omega_host, double2** chi_out) {
+  rpa_status st = check_q_ready(c, iq);
+  if (st != RPA_OK) return st;
+  QPt& Q = c->qpts[iq];
+  const int NG = Q.NG;
+  void *p_chi, *p_om;
+  if ((st = workspace(c, "chi", sizeof(double2) * (size_t)nw * NG * NG, &p_chi)) != RPA_OK) return st;
+  if ((st = workspace(c, "omega", sizeof(double) * nw, &p_om)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemcpyAsync(p_om, omega_host, sizeof(double) * nw, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(p_chi, 0, sizeof(double2) * (size_t)nw * NG * NG, c->stream));
+  for (size_t t = 0; t < Q.k_of.size(); ++t) {
+    if ((st = build_grids(c, c->sets[Q.k_of[t]])) != RPA_OK) return st;
+    if ((st = build_grids(c, c->sets[Q.kq_of[t]])) != RPA_OK) return st;
+  }
+  for (size_t t = 0; t < Q.k_of.size(); ++t) {
+    if (c->prm.precision == RPA_FP64)
+      st = chi_block<double>(c, Q, (int)t, (const double*)p_om, nw, (double2*)p_chi);
+    else
+      st = chi_block<float>(c, Q, (int)t, (const double*)p_om, nw, (double2*)p_chi);
+    if (st != RPA_OK) return st;
+  }
+  *chi_out = (double2*)p_chi;
+  return RPA_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
+  if (!p || !out) return RPA_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < 3; ++i)
+    if (p->grid[i] < 2 || p->grid[i] > 4096) return RPA_ERR_ARG;
+  if (!(p->ecut_chi > 0.0) || !(p->spin_factor > 0.0) || p->nk_bz < 1) return RPA_ERR_ARG;
+  if (p->precision < RPA_FP64 || p->precision > RPA_BF16X3) return RPA_ERR_ARG;
+  const double* a = p->cell;
+  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return RPA_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {
+    cudaGetLastError();
+    return RPA_ERR_CUDA;
+  }
+  if (cudaSetDevice(p->device) != cudaSuccess) return RPA_ERR_CUDA;
+  rpa_ctx* c = new rpa_ctx();
+  c->prm = *p;
+  c->volume = std::fabs(det);
+  double inv[9];
+  inv3(p->cell, inv);
+  // B = 2 pi inv(cell)^T : row i of B is column i of inv(cell)
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) c->B[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
+  if (p->stream) {
+    c->stream = (cudaStream_t)p->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return RPA_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return RPA_OK;
+}
+
+void rpa_destroy(rpa_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->prm.device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->sets) {
+    OrbSet& s = kv.second;
+    dev_free(s.C); dev_free(s.eps_d); dev_free(s.f_d); dev_free(s.pos_d);
+    dev_free(s.L_d); dev_free(s.R_d); dev_free(s.P); dev_free(s.U);
+  }
+  for (auto& kv : c->qpts) {
+    dev_free(kv.second.v_d);
+    dev_free(kv.second.Q);
+  }
+  for (auto& kv : c->ws) dev_free(kv.second.p);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* rpa_last_error(const rpa_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+rpa_status rpa_gauss_legendre(int32_t n, double omega0, double* omega, double* W) {
+  if (n < 1 || n > 1024 || !(omega0 > 0.0) || !omega || !W) return RPA_ERR_ARG;
+  // Newton iteration on the Legendre polynomial P_n (three-term recurrence),
+  // root i started from cos(pi (i + 3/4) / (n + 1/2)); weight 2/((1-x^2) P_n'^2)
+  std::vector<double> x(n), w(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  // ascending nodes
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return x[a] < x[b]; });
+  for (int i = 0; i < n; ++i) {
+    const double z = x[ord[i]];
+    omega[i] = omega0 * (1.0 + z) / (1.0 - z);
+    W[i] = w[ord[i]] * 2.0 * omega0 / ((1.0 - z) * (1.0 - z));
+  }
+  return RPA_OK;
+}
+
+rpa_status rpa_set_orbitals(rpa_ctx* c, int32_t kidx, const double k_red[3], int32_t nbands, int32_t npw,
+                            const int32_t* miller, const double* C, const double* eps, const double* f) {
+  if (!c) return RPA_ERR_ARG;
+  if (kidx < 0 || kidx >= kMaxIndex) return fail(c, RPA_ERR_ARG, "kidx %d out of range", kidx);
+  if (nbands < 1 || npw < 1 || nbands > (1 << 20) || npw > (1 << 24))
+    return fail(c, RPA_ERR_ARG, "bad sizes nbands=%d npw=%d", nbands, npw);
+  if (!k_red || !miller || !C || !eps || !f) return fail(c, RPA_ERR_ARG, "null pointer argument");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  OrbSet s;
+  s.valid = true;
+  for (int d = 0; d < 3; ++d) s.k[d] = k_red[d];
+  s.nb = nbands;
+  s.npw = npw;
+  s.miller.assign(miller, miller + 3 * (size_t)npw);
+  s.eps.assign(eps, eps + nbands);
+  s.f.assign(f, f + nbands);
+  for (int i = 0; i < nbands; ++i) {
+    if (!std::isfinite(s.eps[i])) return fail(c, RPA_ERR_ARG, "eps[%d] not finite", i);
+    if (!(s.f[i] >= 0.0 && s.f[i] <= 1.0)) return fail(c, RPA_ERR_ARG, "f[%d] outside [0,1]", i);
+    if (s.f[i] > 0.0) s.L.push_back(i);
+    if (s.f[i] < 1.0) s.R.push_back(i);
+  }
+  for (int d = 0; d < 3; ++d) {
+    s.mlo[d] = 1 << 30;
+    s.mhi[d] = -(1 << 30);
+  }
+  for (int q = 0; q < npw; ++q)
+    for (int d = 0; d < 3; ++d) {
+      s.mlo[d] = std::min(s.mlo[d], s.miller[3 * q + d]);
+      s.mhi[d] = std::max(s.mhi[d], s.miller[3 * q + d]);
+    }
+  for (int d = 0; d < 3; ++d)
+    if (s.mhi[d] - s.mlo[d] + 1 > c->prm.grid[d])
+      return fail(c, RPA_ERR_ARG, "Miller range along axis %d exceeds the grid", d);
+  const int L1 = s.mhi[0] - s.mlo[0] + 1, L2 = s.mhi[1] - s.mlo[1] + 1, L3 = s.mhi[2] - s.mlo[2] + 1;
+  std::vector<int> pos(npw);
+  std::vector<char> seen((size_t)L1 * L2 * L3, 0);
+  for (int q = 0; q < npw; ++q) {
+    const int i1 = s.miller[3 * q] - s.mlo[0], i2 = s.miller[3 * q + 1] - s.mlo[1], i3 = s.miller[3 * q + 2] - s.mlo[2];
+    const size_t flat = ((size_t)i1 * L2 + i2) * L3 + i3;
+    if (seen[flat]) return fail(c, RPA_ERR_ARG, "duplicate Miller index at plane wave %d", q);
+    seen[flat] = 1;
+    pos[q] = (int)flat;
+  }
+  rpa_status st;
+  if ((st = dev_alloc(c, (void**)&s.C, sizeof(double2) * (size_t)nbands * npw)) != RPA_OK) return st;
+  auto cleanup = [&]() {
+    dev_free(s.C); dev_free(s.eps_d); dev_free(s.f_d); dev_free(s.pos_d); dev_free(s.L_d); dev_free(s.R_d);
+  };
+  if ((st = dev_alloc(c, (void**)&s.eps_d, sizeof(double) * nbands)) != RPA_OK) { cleanup(); return st; }
+  if ((st = dev_alloc(c, (void**)&s.f_d, sizeof(double) * nbands)) != RPA_OK) { cleanup(); return st; }
+  if ((st = dev_alloc(c, (void**)&s.pos_d, sizeof(int) * npw)) != RPA_OK) { cleanup(); return st; }
+  if ((st = dev_alloc(c, (void**)&s.L_d, sizeof(int) * std::max<size_t>(1, s.L.size()))) != RPA_OK) { cleanup(); return st; }
+  if ((st = dev_alloc(c, (void**)&s.R_d, sizeof(int) * std::max<size_t>(1, s.R.size()))) != RPA_OK) { cleanup(); return st; }
+  if ((st = copy_in(c, s.C, C, sizeof(double2) * (size_t)nbands * npw)) != RPA_OK) { cleanup(); return st; }
+  CUDA_OK(c, cudaMemcpyAsync(s.eps_d, s.eps.data(), sizeof(double) * nbands, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(s.f_d, s.f.data(), sizeof(double) * nbands, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(s.pos_d, pos.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, c->stream));
+  if (!s.L.empty())
+    CUDA_OK(c, cudaMemcpyAsync(s.L_d, s.L.data(), sizeof(int) * s.L.size(), cudaMemcpyHostToDevice, c->stream));
+  if (!s.R.empty())
+    CUDA_OK(c, cudaMemcpyAsync(s.R_d, s.R.data(), sizeof(int) * s.R.size(), cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  auto it = c->sets.find(kidx);
+  if (it != c->sets.end()) {
+    OrbSet& o = it->second;
+    dev_free(o.C); dev_free(o.eps_d); dev_free(o.f_d); dev_free(o.pos_d);
+    dev_free(o.L_d); dev_free(o.R_d); dev_free(o.P); dev_free(o.U);
+  }
+  c->sets[kidx] = s;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_paw(rpa_ctx* c, int32_t kidx, int32_t natoms, const int32_t* nproj, const double* P) {
+  if (!c) return RPA_ERR_ARG;
+  auto it = c->sets.find(kidx);
+  if (it == c->sets.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "orbital set %d not set", kidx);
+  if (natoms < 1 || natoms > 100000 || !nproj || !P) return fail(c, RPA_ERR_ARG, "bad PAW arguments");
+  int KP = 0;
+  for (int a = 0; a < natoms; ++a) {
+    if (nproj[a] < 1 || nproj[a] > 64) return fail(c, RPA_ERR_ARG, "nproj[%d] = %d outside [1,64]", a, nproj[a]);
+    KP += nproj[a];
+  }
+  OrbSet& s = it->second;
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  double2* Pd = nullptr;
+  rpa_status st;
+  if ((st = dev_alloc(c, (void**)&Pd, sizeof(double2) * (size_t)s.nb * KP)) != RPA_OK) return st;
+  if ((st = copy_in(c, Pd, P, sizeof(double2) * (size_t)s.nb * KP)) != RPA_OK) { dev_free(Pd); return st; }
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  dev_free(s.P);
+  s.P = Pd;
+  s.natoms = natoms;
+  s.nproj.assign(nproj, nproj + natoms);
+  s.KP = KP;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t nk, const int32_t* k_of,
+                          const int32_t* kq_of, const int32_t* G0, int32_t* ng_out) {
+  if (!c) return RPA_ERR_ARG;
+  if (iq < 0 || iq >= kMaxIndex) return fail(c, RPA_ERR_ARG, "iq %d out of range", iq);
+  if (!q_red || nk < 1 || nk > kMaxIndex || !k_of || !kq_of || !G0) return fail(c, RPA_ERR_ARG, "bad q-point arguments");
+  QPt Q;
+  Q.valid = true;
+  for (int d = 0; d < 3; ++d) Q.q[d] = q_red[d];
+  Q.k_of.assign(k_of, k_of + nk);
+  Q.kq_of.assign(kq_of, kq_of + nk);
+  Q.G0.assign(G0, G0 + 3 * (size_t)nk);
+  for (int t = 0; t < nk; ++t) {
+    for (int which = 0; which < 2; ++which) {
+      const int idx = which ? kq_of[t] : k_of[t];
+      auto it = c->sets.find(idx);
+      if (it == c->sets.end() || !it->second.valid)
+        return fail(c, RPA_ERR_STATE, "transition %d references orbital set %d that is not set", t, idx);
+    }
+  }
+  // response sphere {G : |q+G|^2/2 <= ecut}, lexicographic (first index slowest)
+  const double* B = c->B;
+  const double rmax = std::sqrt(2.0 * c->prm.ecut_chi);
+  double Binv[9];
+  inv3(B, Binv);
+  int ext[3];
+  for (int i = 0; i < 3; ++i) {
+    const double colnorm = std::sqrt(Binv[i] * Binv[i] + Binv[3 + i] * Binv[3 + i] + Binv[6 + i] * Binv[6 + i]);
+    ext[i] = (int)std::ceil(rmax * colnorm) + 2;
+  }
+  for (int g1 = -ext[0]; g1 <= ext[0]; ++g1)
+    for (int g2 = -ext[1]; g2 <= ext[1]; ++g2)
+      for (int g3 = -ext[2]; g3 <= ext[2]; ++g3) {
+        const double r[3] = {g1 + Q.q[0], g2 + Q.q[1], g3 + Q.q[2]};
+        double v[3];
+        for (int cc = 0; cc < 3; ++cc) v[cc] = r[0] * B[cc] + r[1] * B[3 + cc] + r[2] * B[6 + cc];
+        const double k2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (0.5 * k2 <= c->prm.ecut_chi) {
+          Q.gm.push_back(g1);
+          Q.gm.push_back(g2);
+          Q.gm.push_back(g3);
+          Q.v.push_back((r[0] == 0.0 && r[1] == 0.0 && r[2] == 0.0) ? 0.0 : 4.0 * M_PI / k2);
+        }
+      }
+  Q.NG = (int)Q.v.size();
+  if (Q.NG == 0) return fail(c, RPA_ERR_ARG, "empty response sphere");
+  // the Fourier route (Eq. 10) equals the plane-wave sum only without aliasing:
+  // every component Q_m - Q_n - (G + G0) must lie strictly inside (-N, N)
+  for (int t = 0; t < nk; ++t) {
+    const OrbSet& a = c->sets[k_of[t]];
+    const OrbSet& b = c->sets[kq_of[t]];
+    for (int d = 0; d < 3; ++d) {
+      int glo = 1 << 30, ghi = -(1 << 30);
+      for (int i = 0; i < Q.NG; ++i) {
+        const int g = Q.gm[3 * i + d] + G0[3 * t + d];
+        glo = std::min(glo, g);
+        ghi = std::max(ghi, g);
+      }
+      const int hi = b.mhi[d] - a.mlo[d] - glo;
+      const int lo = b.mlo[d] - a.mhi[d] - ghi;
+      if (hi > c->prm.grid[d] - 1 || lo < -(c->prm.grid[d] - 1))
+        return fail(c, RPA_ERR_ARG, "grid axis %d (N=%d) too small: pair-density transform would alias", d,
+                    c->prm.grid[d]);
+    }
+  }
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  rpa_status st;
+  if ((st = dev_alloc(c, (void**)&Q.v_d, sizeof(double) * Q.NG)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemcpyAsync(Q.v_d, Q.v.data(), sizeof(double) * Q.NG, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  auto it = c->qpts.find(iq);
+  if (it != c->qpts.end()) {
+    dev_free(it->second.v_d);
+    dev_free(it->second.Q);
+  }
+  c->qpts[iq] = Q;
+  if (ng_out) *ng_out = Q.NG;
+  return RPA_OK;
+}
+
+rpa_status rpa_gvectors(const rpa_ctx* c, int32_t iq, int32_t* ng, int32_t* miller_out) {
+  if (!c || !ng) return RPA_ERR_ARG;
+  auto it = c->qpts.find(iq);
+  if (it == c->qpts.end() || !it->second.valid) return RPA_ERR_STATE;
+  *ng = it->second.NG;
+  if (miller_out) memcpy(miller_out, it->second.gm.data(), sizeof(int32_t) * it->second.gm.size());
+  return RPA_OK;
+}
+
+rpa_status rpa_set_paw_Q(rpa_ctx* c, int32_t iq, int32_t natoms, const int32_t* nproj, const double* Qv) {
+  if (!c) return RPA_ERR_ARG;
+  auto it = c->qpts.find(iq);
+  if (it == c->qpts.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "q-point %d not set", iq);
+  if (natoms < 1 || natoms > 100000 || !nproj || !Qv) return fail(c, RPA_ERR_ARG, "bad PAW Q arguments");
+  QPt& Q = it->second;
+  int64_t tot = 0;
+  for (int a = 0; a < natoms; ++a) {
+    if (nproj[a] < 1 || nproj[a] > 64) return fail(c, RPA_ERR_ARG, "nproj[%d] outside [1,64]", a);
+    tot += (int64_t)nproj[a] * nproj[a] * Q.NG;
+  }
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  double2* Qd = nullptr;
+  rpa_status st;
+  if ((st = dev_alloc(c, (void**)&Qd, sizeof(double2) * (size_t)tot)) != RPA_OK) return st;
+  if ((st = copy_in(c, Qd, Qv, sizeof(double2) * (size_t)tot)) != RPA_OK) { dev_free(Qd); return st; }
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  dev_free(Q.Q);
+  Q.Q = Qd;
+  Q.natoms = natoms;
+  Q.nproj.assign(nproj, nproj + natoms);
+  return RPA_OK;
+}
+
+rpa_status rpa_chi0(rpa_ctx* c, int32_t iq, int32_t nw, const double* omega, double* chi_out) {
+  if (!c) return RPA_ERR_ARG;
+  if (nw < 1 || nw > 4096 || !omega || !chi_out) return fail(c, RPA_ERR_ARG, "bad rpa_chi0 arguments");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  prof_begin(c);
+  ++c->stamp;
+  double2* chi = nullptr;
+  rpa_status st = build_chi(c, iq, nw, omega, &chi);
+  if (st != RPA_OK) return st;
+  const int NG = c->qpts[iq].NG;
+  {
+    StageTimer tm(c, 4, 1);
+    CUDA_OK(c, launch_hermitian_fill(chi, nw, NG, c->stream));
+  }
+  const size_t bytes = sizeof(double2) * (size_t)nw * NG * NG;
+  const bool dev = is_device_ptr(chi_out);
+  CUDA_OK(c, cudaMemcpyAsync(chi_out, chi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (!dev || c->profiling) CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  CUDA_OK(c, cudaGetLastError());
+  prof_end(c);
+  return RPA_OK;
+}
+
+rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* wq, int32_t nw, const double* omega,
+                      const double* W, double* Ec, double* terms) {
+  if (!c) return RPA_ERR_ARG;
+  if (nq < 1 || nq > kMaxIndex || !iqs || !wq || nw < 1 || nw > 4096 || !omega || !W || !Ec)
+    return fail(c, RPA_ERR_ARG, "bad rpa_energy arguments");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  prof_begin(c);
+  ++c->stamp;
+  double E = 0.0;
+  std::vector<double> ld(nw), tr(nw);
+  for (int i = 0; i < nq; ++i) {
+    double2* chi = nullptr;
+    rpa_status st = build_chi(c, iqs[i], nw, omega, &chi);
+    if (st != RPA_OK) return st;
+    QPt& Q = c->qpts[iqs[i]];
+    const int NG = Q.NG;
+    void *p_work, *p_ld, *p_tr, *p_flag;
+    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)nw * NG * NG, &p_work)) != RPA_OK) return st;
+    if ((st = workspace(c, "logdet", sizeof(double) * nw, &p_ld)) != RPA_OK) return st;
+    if ((st = workspace(c, "trace", sizeof(double) * nw, &p_tr)) != RPA_OK) return st;
+    if ((st = workspace(c, "flag", sizeof(int), &p_flag)) != RPA_OK) return st;
+    int64_t nl = 0;
+    {
+      StageTimer tm(c, 3, 0);
+      CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
+                            c->stream, &nl));
+      tm.add_launches(nl);
+    }
+    int flag = 0;
+    CUDA_OK(c, cudaMemcpyAsync(ld.data(), p_ld, sizeof(double) * nw, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(tr.data(), p_tr, sizeof(double) * nw, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(&flag, p_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    if (flag) return fail(c, RPA_ERR_NOT_HPD, "1 - v^1/2 chi0 v^1/2 is not positive definite at q-point %d", iqs[i]);
+    double eq = 0.0;
+    for (int j = 0; j < nw; ++j) {
+      const double e = ld[j] + tr[j];
+      if (terms) terms[(size_t)i * nw + j] = e;
+      eq += W[j] * e;
+    }
+    E += wq[i] * eq / (2.0 * M_PI);
+  }
+  *Ec = E;
+  prof_end(c);
+  return RPA_OK;
+}
+
+rpa_status rpa_set_profiling(rpa_ctx* c, int32_t enable) {
+  if (!c) return RPA_ERR_ARG;
+  c->profiling = enable != 0;
+  return RPA_OK;
+}
+
+rpa_status rpa_get_profile(const rpa_ctx* c, double* ms, int64_t* launches) {
+  if (!c) return RPA_ERR_ARG;
+  for (int i = 0; i < 5; ++i) {
+    if (ms) ms[i] = c->prof_ms[i];
+    if (launches) launches[i] = c->prof_launch[i];
+  }
+  return RPA_OK;
+}
+
+}  // extern "C"

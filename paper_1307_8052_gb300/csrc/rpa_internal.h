@@ -1,0 +1,95 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace rpa {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using c2 = typename vec2<T>::type;
+
+template <typename T> __host__ __device__ inline c2<T> mk(T re, T im) { c2<T> r; r.x = re; r.y = im; return r; }
+
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cmac(c2<T>& acc, c2<T> a, c2<T> b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+template <typename T> __device__ __forceinline__ void cmac_cj(c2<T>& acc, c2<T> a, c2<T> b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.y, b.x, acc.y); acc.y = fma(-a.x, b.y, acc.y);
+}
+// conj(a) * b
+template <typename T> __device__ __forceinline__ c2<T> cj_mul(c2<T> a, c2<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// ---------------------------------------------------------------- kernels
+// Generic pruned DFT along one axis of a [batch][A][Lin][B] array:
+//   out[b][a][o][c] = sum_i in[b][a][i][c] * exp(sign * 2 pi i (in_off+i)(out_off+o) / N)
+template <typename T>
+cudaError_t launch_dft_axis(const c2<T>* in, c2<T>* out, int64_t batch, int A, int Lin, int Lout,
+                            int B, int N, int in_off, int out_off, int sign, cudaStream_t s);
+
+// Scatter plane-wave coefficients (double complex [nb][npw]) into a zeroed
+// Miller box [nb][box] at the flat positions pos[npw].
+template <typename T>
+cudaError_t launch_scatter_box(const double2* C, int nb, int npw, const int* pos, int64_t box,
+                               c2<T>* out, cudaStream_t s);
+
+// Pair densities, stage A: fused conj(u_n) u_m product and pruned DFT along
+// the slowest grid axis.  Pairs p0 .. p0+np-1 of the rectangle L x R (a-major).
+template <typename T>
+cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
+                             const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
+                             int g1lo, int n1, c2<T>* T1, cudaStream_t s);
+
+// Pair densities, stage C: DFT along the fastest axis evaluated on the sphere
+// points g = G + G0, 1/Nr normalisation, PAW term, write N[p][NG].
+template <typename T>
+cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft,
+                             int NG, int g1lo, int g2lo, double inv_nr,
+                             const c2<T>* R, const c2<T>* Pm, int KP, const int* Ridx, int nR,
+                             int64_t p0, c2<T>* Nout, cudaStream_t s);
+
+// PAW factor R_a[aL][kp][G] = sum_i conj(P_n,(a,i)) Q^a_ij(G), FP64 arithmetic.
+template <typename T>
+cudaError_t launch_paw_R(const double2* Pk, int KP, const int* Lidx, int nL, const double2* Q,
+                         const int* atom_of_kp, const int* idx_in_atom, const int* atom_off,
+                         const int64_t* q_off, const int* nproj, int NG, c2<T>* R, cudaStream_t s);
+
+// Gather projections P[m][kp] of the R set into working precision.
+template <typename T>
+cudaError_t launch_gather_P(const double2* P, int KP, const int* Ridx, int nR, c2<T>* out,
+                            cudaStream_t s);
+
+// Pair parameters: d_p = e_n - e_m and df_p = max(f_n - f_m, 0).
+cudaError_t launch_pair_params(const double* ek, const double* fk, const double* ekp,
+                               const double* fkp, const int* Lidx, int nL, const int* Ridx, int nR,
+                               double* d, double* df, cudaStream_t s);
+
+// Real pair weights of Eq. 3 (time-reversal combined), per frequency:
+//   wgt[j][p] = pref * df_p * 2 d_p / (w_j^2 + d_p^2), computed in FP64.
+cudaError_t launch_pair_weights(const double* d, const double* df, const double* omega, int nw, int64_t P,
+                                double pref, double* w64, float* w32, cudaStream_t s);
+
+// Hermitian rank-k update on CUDA cores (FP64 or FP32 with compensated folds):
+//   chi[w][i][j] += sum_p wgt[w][p] N[p][i] conj(N[p][j]) for lower-triangle tiles.
+template <typename T>
+cudaError_t launch_herk_simt_w(const c2<T>* N, int64_t P, int NG, const T* wgt, int nw, double2* chi,
+                               cudaStream_t s);
+
+// Upper triangle from lower: chi[w][i][j] = conj(chi[w][j][i]) for i < j.
+cudaError_t launch_hermitian_fill(double2* chi, int nw, int NG, cudaStream_t s);
+
+// FP64 log-det of 1 - v^1/2 chi v^1/2 by blocked Cholesky, batched over w.
+// Returns per-w e(w) = ln det + tr in eout (device), error flag in flag.
+cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work,
+                       double* logdet, double* trace, int* flag, cudaStream_t s, int64_t* launches);
+
+}  // namespace rpa

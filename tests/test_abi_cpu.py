@@ -1,0 +1,64 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every function that include/rpa.h declares, validates parameters, and
+its host-only quadrature routine agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1307_8052_gb300 import binding as b
+from paper_1307_8052_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return b.load()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "rpa.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rpa_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert "rpa_chi0" in names and "rpa_energy" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(b.SIGNATURES), "binding signatures out of step with the header"
+
+
+def test_gauss_legendre_matches_oracle(lib):
+    for n in (1, 2, 8, 16, 33):
+        om, W = b.rpa_gauss_legendre(n, 1.0)
+        omr, Wr = o.frequency_grid(n, 1.0)
+        assert np.allclose(om, omr, rtol=1e-13, atol=0)
+        assert np.allclose(W, Wr, rtol=1e-12, atol=0)
+    with pytest.raises(b.RpaError) as e:
+        b.rpa_gauss_legendre(0)
+    assert e.value.status == b.RPA_ERR_ARG
+
+
+def test_create_rejects_bad_parameters(lib):
+    for kw in ({"grid": (1, 8, 8)}, {"ecut_chi": -1.0}, {"nk_bz": 0}, {"precision": 7},
+               {"cell": np.zeros((3, 3))}):
+        args = dict(cell=np.eye(3) * 5, grid=(8, 8, 8), ecut_chi=1.0)
+        args.update(kw)
+        with pytest.raises(b.RpaError) as e:
+            b.rpa_create(**args)
+        assert e.value.status == b.RPA_ERR_ARG
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(b.RpaError) as e:
+        b.rpa_create(np.eye(3) * 5, (8, 8, 8), 1.0)
+    assert e.value.status == b.RPA_ERR_CUDA
