@@ -164,6 +164,25 @@ rpa_status rpa_energy(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
 rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
 rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
 
+/* Tuning knobs (no effect on results beyond rounding order):
+ * RPA_TUNE_TC_FOLD     stages of 64 K-elements accumulated in FP32 tensor
+ *                      memory before the partial sum is added to FP32
+ *                      running sums in registers (split-bfloat16 modes), in
+ *                      [1, 2^20]; default 1.  The tensor cores truncate while
+ *                      accumulating, so longer folds bias |chi0| low.
+ * RPA_TUNE_PAIR_CHUNK  pairs per pair-density launch; 0 = sized automatically
+ *                      so the transform intermediates stay in L2.
+ * RPA_TUNE_TC_FLUSH    folds between additions of the register running sums
+ *                      to the FP64 chi0, in [1, 2^20]; default 256.
+ * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
+typedef enum {
+  RPA_TUNE_TC_FOLD = 0,
+  RPA_TUNE_PAIR_CHUNK = 1,
+  RPA_TUNE_TC_FLUSH = 2,
+  RPA_TUNE_COUNT = 3
+} rpa_tuning;
+rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
+
 #ifdef __cplusplus
 }
 #endif

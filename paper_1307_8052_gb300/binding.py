@@ -41,7 +41,9 @@ SIGNATURES = {
     "rpa_energy": (_I, [_P, _I, _P, _P, _I, _P, _P, _P, _P]),
     "rpa_set_profiling": (_I, [_P, _I]),
     "rpa_get_profile": (_I, [_P, _P, _P]),
+    "rpa_set_tuning": (_I, [_P, _I, ct.c_int64]),
 }
+RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK = 0, 1
 
 
 class RpaParams(ct.Structure):
@@ -201,6 +203,10 @@ def rpa_energy(ctx, iqs, wq, omega, W):
 
 def rpa_set_profiling(ctx, enable=True):
     _check(ctx, lib().rpa_set_profiling(ctx, 1 if enable else 0))
+
+
+def rpa_set_tuning(ctx, param, value):
+    _check(ctx, lib().rpa_set_tuning(ctx, int(param), int(value)))
 
 
 def rpa_get_profile(ctx):

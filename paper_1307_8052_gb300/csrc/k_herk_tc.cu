@@ -1,11 +1,544 @@
-// Tensor-core (tcgen05) grouped Hermitian rank-k update: placeholder until the
-// split-bfloat16 kernel lands; the host rejects the BF16 modes meanwhile.
+// Tensor-core grouped Hermitian rank-k update of chi0 (Eq. 17, the paper's
+// "multi-u" zherk) for every frequency, on the 5th-generation tensor cores.
+//
+// Real-stacked form.  With a_p = n_p(G_i), b_p = n_p(G_j) and the K index
+// k = 2p + c running over (pair, re/im):
+//   Re chi_ij = sum_k A_ik X_jk,  Im chi_ij = sum_k A_ik Z_jk,
+//   A = w_p(w) (Re a, Im a),  X = (Re b, Im b),  Z = (-Im b, Re b).
+// Each operand is split into bfloat16 terms x = x_hi + x_lo (+ x_mid for
+// three terms); the products hi*hi + hi*lo + lo*hi (and hi*mid, mid*hi,
+// mid*mid, hi*lo2, lo2*hi for three terms) are accumulated in FP32 in tensor
+// memory (TMEM) for one fold (64 K-elements by default).  The tensor cores
+// truncate while accumulating (measured: the bias of |chi0| grows linearly
+// with the fold length), so each fold's partial is added to FP32 running sums
+// in registers (round to nearest) and those go to the FP64 chi0 every few
+// folds.
+//
+// Data path: one prep kernel per k-block writes the unweighted X, Z operand
+// splits (K-major, bfloat16), one prep kernel writes the weighted A splits for
+// all frequencies; the GEMM kernel streams 128x64 tiles with TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) into a 2-stage shared-memory ring,
+// one thread issues tcgen05.mma (M = N = 128, K = 16) into two TMEM
+// accumulator buffers (Re 128 + Im 128 columns each), and eight epilogue
+// warps drain one buffer with tcgen05.ld while the MMAs fill the other.
+// Only lower-triangle tiles are launched.  Every wait is bounded by the GPU
+// global timer; on timeout the CTA raises a flag, drains, frees TMEM and exits.
 #include "rpa_internal.h"
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
 namespace rpa {
-size_t herk_tc_scratch_bytes(int64_t, int, int, int) { return 0; }
-cudaError_t launch_herk_tc(const float2*, int64_t, int, const float*, int, int, double2*, void*, size_t,
-                           cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace tc {
+
+constexpr int BM = 128;               // tile rows (G_i)
+constexpr int BN = 128;               // tile cols (G_j)
+constexpr int BK = 64;                // bf16 K-elements per stage (128 bytes per row)
+constexpr int STAGES = 2;
+constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB
+constexpr int NUM_THREADS = 320;      // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr uint64_t TIMEOUT_NS = 4000000000ull;  // 4 s per wait
+
+template <int TERMS> struct Cfg {
+  static constexpr int A_TILES = TERMS;             // A hi, (mid), lo
+  static constexpr int B_TILES = 2 * TERMS;         // X hi/(mid)/lo, Z hi/(mid)/lo
+  static constexpr int STAGE_BYTES = (A_TILES + B_TILES) * TILE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if the timer expired or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > TIMEOUT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait_timer(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (gtimer() - t0 > TIMEOUT_NS) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int k, int row) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(k), "r"(row)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                    // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
+  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
+
+struct Maps {
+  CUtensorMap a[3];  // weighted A terms (rows = w * NGpad + i)
+  CUtensorMap x[3];  // X terms
+  CUtensorMap z[3];  // Z terms
+};
+
+template <int TERMS>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    herk_tc_kernel(const __grid_constant__ Maps maps, int NG, int NGpad, int nk, int fold, int flush, double2* __restrict__ chi,
+                   int* __restrict__ err) {
+  using C = Cfg<TERMS>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* mma_done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.y;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int i0 = ti * BM, j0 = tj * BN;
+  const int nfold = (nk + fold - 1) / fold;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 256);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        mbar_expect_tx(&full[s], C::STAGE_BYTES);
+        unsigned char* st = smem + s * C::STAGE_BYTES;
+        const int k = kb * BK;
+#pragma unroll
+        for (int t = 0; t < TERMS; ++t) tma_load_2d(st + t * TILE_BYTES, &maps.a[t], &full[s], k, w * NGpad + i0);
+#pragma unroll
+        for (int t = 0; t < TERMS; ++t) {
+          tma_load_2d(st + (TERMS + t) * TILE_BYTES, &maps.x[t], &full[s], k, j0);
+          tma_load_2d(st + (2 * TERMS + t) * TILE_BYTES, &maps.z[t], &full[s], k, j0);
+        }
+        issued = kb + 1;
+      }
+      // after an abort, every load already issued must land before the CTA may exit
+      if (*abort_flag) {
+        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+          mbar_wait_timer(&full[kb % STAGES], (kb / STAGES) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&full[s], (kb / STAGES) & 1, abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(err, 2);
+          break;
+        }
+        const int f = kb / fold;
+        const int b = f & 1;
+        const bool first = (kb % fold) == 0;
+        if (first && f >= 2 && !mbar_wait(&tempty[b], ((f >> 1) - 1) & 1, abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(err, 3);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+        const uint32_t d_re = tmem + b * 256;
+        const uint32_t d_im = tmem + b * 256 + 128;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
+          uint64_t da[3], dx[3], dz[3];
+#pragma unroll
+          for (int t = 0; t < TERMS; ++t) {
+            da[t] = sw128_desc(st + t * TILE_BYTES + koff);
+            dx[t] = sw128_desc(st + (TERMS + t) * TILE_BYTES + koff);
+            dz[t] = sw128_desc(st + (2 * TERMS + t) * TILE_BYTES + koff);
+          }
+          uint32_t acc = (first && kk == 0) ? 0u : 1u;
+          // hi*hi, hi*lo, lo*hi  (three terms: + hi*mid, mid*hi, mid*mid, hi*lo, lo*hi)
+          umma(d_re, da[0], dx[0], idesc, acc);
+          umma(d_im, da[0], dz[0], idesc, acc);
+          umma(d_re, da[0], dx[1], idesc, 1u);
+          umma(d_im, da[0], dz[1], idesc, 1u);
+          umma(d_re, da[1], dx[0], idesc, 1u);
+          umma(d_im, da[1], dz[0], idesc, 1u);
+          if (TERMS == 3) {
+            umma(d_re, da[1], dx[1], idesc, 1u);
+            umma(d_im, da[1], dz[1], idesc, 1u);
+            umma(d_re, da[0], dx[2], idesc, 1u);
+            umma(d_im, da[0], dz[2], idesc, 1u);
+            umma(d_re, da[2], dx[0], idesc, 1u);
+            umma(d_im, da[2], dz[0], idesc, 1u);
+          }
+        }
+        umma_commit(&empty[s]);
+        if ((kb % fold) == fold - 1 || kb == nk - 1) umma_commit(&tfull[b]);
+      }
+      // every MMA issued so far must finish before TMEM is released
+      umma_commit(mma_done);
+      if (!mbar_wait_timer(mma_done, 0)) atomicExch(err, 5);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..9)
+    // Warp w reads TMEM lane quarter w % 4 (rows 32q..32q+31) and column half
+    // h = (w - 2) / 4 of the Re and Im accumulators.  The FP32 partial of every
+    // fold is added to FP32 running sums held in registers (round to nearest)
+    // and the running sums go to the FP64 chi0 every `flush` folds, so the
+    // truncating accumulation inside the tensor core never spans more than one fold.
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const int gi = i0 + row;
+    const int cbase = h * 64;
+    double2* crow = chi + ((int64_t)w * NG + gi) * NG + j0 + cbase;
+    // columns of this thread that belong to the lower triangle and the sphere
+    const int ncol = (gi < NG) ? max(0, min(64, min(NG, gi + 1) - (j0 + cbase))) : 0;
+    float sre[64], sim[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) sre[c] = sim[c] = 0.f;
+#define RPA_TC_FLUSH()                                      \
+  do {                                                      \
+    _Pragma("unroll") for (int c = 0; c < 64; ++c) {        \
+      if (c < ncol) {                                       \
+        double2 v = crow[c];                                \
+        v.x += (double)sre[c];                              \
+        v.y += (double)sim[c];                              \
+        crow[c] = v;                                        \
+      }                                                     \
+      sre[c] = 0.f;                                         \
+      sim[c] = 0.f;                                         \
+    }                                                       \
+  } while (0)
+    for (int f = 0; f < nfold; ++f) {
+      const int b = f & 1;
+      // the warp decides together: tcgen05.ld below is warp-collective
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (f >> 1) & 1, abort_flag));
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(err, 4);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + cbase;
+      float v[32];
+      tmem_ld32(base, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) sre[c] += v[c];
+      tmem_ld32(base + 32, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) sre[32 + c] += v[c];
+      tmem_ld32(base + 128, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) sim[c] += v[c];
+      tmem_ld32(base + 160, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) sim[32 + c] += v[c];
+      tc_fence_before();
+      mbar_arrive(&tempty[b]);
+      if ((f + 1) % flush == 0) RPA_TC_FLUSH();
+    }
+    RPA_TC_FLUSH();
+#undef RPA_TC_FLUSH
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- operand preparation
+__device__ __forceinline__ void split2(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// X[t][g][2p+c], Z[t][g][2p+c] from N[p][g] (transpose through shared memory), zero padding.
+template <int TERMS>
+__global__ void __launch_bounds__(256) prep_xz_kernel(const float2* __restrict__ N, int64_t P, int NG, int NGpad,
+                                                      int64_t Kpad, __nv_bfloat162* __restrict__ X,
+                                                      __nv_bfloat162* __restrict__ Z, int64_t term_stride) {
+  __shared__ float2 t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t p0 = (int64_t)blockIdx.y * 32;
+  const int g0 = blockIdx.x * 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t p = p0 + r;
+    const int g = g0 + tx;
+    t[r][tx] = (p < P && g < NG) ? N[p * NG + g] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int g = g0 + r;
+    const int64_t p = p0 + tx;
+    const float2 v = t[tx][r];
+    const int64_t o = (int64_t)g * (Kpad / 2) + p;
+    __nv_bfloat16 rh, rm, rl, ih, im, il;
+    if (TERMS == 2) {
+      split2(v.x, rh, rl);
+      split2(v.y, ih, il);
+      X[o] = __halves2bfloat162(rh, ih);
+      X[o + term_stride] = __halves2bfloat162(rl, il);
+      Z[o] = __halves2bfloat162(__hneg(ih), rh);
+      Z[o + term_stride] = __halves2bfloat162(__hneg(il), rl);
+    } else {
+      split3(v.x, rh, rm, rl);
+      split3(v.y, ih, im, il);
+      X[o] = __halves2bfloat162(rh, ih);
+      X[o + term_stride] = __halves2bfloat162(rm, im);
+      X[o + 2 * term_stride] = __halves2bfloat162(rl, il);
+      Z[o] = __halves2bfloat162(__hneg(ih), rh);
+      Z[o + term_stride] = __halves2bfloat162(__hneg(im), rm);
+      Z[o + 2 * term_stride] = __halves2bfloat162(__hneg(il), rl);
+    }
+  }
+}
+
+// A[t][w][g][2p+c] = split(w_p(w) * (Re, Im) N[p][g]) for every frequency.
+template <int TERMS>
+__global__ void __launch_bounds__(256) prep_a_kernel(const float2* __restrict__ N, const float* __restrict__ wgt,
+                                                     int64_t P, int NG, int NGpad, int64_t Kpad, int nw,
+                                                     __nv_bfloat162* __restrict__ A, int64_t term_stride) {
+  __shared__ float2 t[32][33];
+  __shared__ float ws[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t p0 = (int64_t)blockIdx.y * 32;
+  const int g0 = blockIdx.x * 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t p = p0 + r;
+    const int g = g0 + tx;
+    t[r][tx] = (p < P && g < NG) ? N[p * NG + g] : make_float2(0.f, 0.f);
+  }
+  for (int w = 0; w < nw; ++w) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int64_t p = p0 + threadIdx.x;
+      ws[threadIdx.x] = p < P ? wgt[(int64_t)w * P + p] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int g = g0 + r;
+      const float2 v = t[tx][r];
+      const float wp = ws[tx];
+      const int64_t o = ((int64_t)w * NGpad + g) * (Kpad / 2) + p0 + tx;
+      __nv_bfloat16 rh, rm, rl, ih, im, il;
+      if (TERMS == 2) {
+        split2(wp * v.x, rh, rl);
+        split2(wp * v.y, ih, il);
+        A[o] = __halves2bfloat162(rh, ih);
+        A[o + term_stride] = __halves2bfloat162(rl, il);
+      } else {
+        split3(wp * v.x, rh, rm, rl);
+        split3(wp * v.y, ih, im, il);
+        A[o] = __halves2bfloat162(rh, ih);
+        A[o + term_stride] = __halves2bfloat162(rm, im);
+        A[o + 2 * term_stride] = __halves2bfloat162(rl, il);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static bool make_map(CUtensorMap* m, const void* base, int64_t K, int64_t rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(K * 2)};
+  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct Geometry {
+  int NGpad;
+  int64_t Ppad, Kpad;
+};
+static Geometry geometry(int64_t P, int NG) {
+  Geometry g;
+  g.NGpad = (NG + BM - 1) / BM * BM;
+  g.Ppad = (P + 31) / 32 * 32;
+  g.Kpad = 2 * g.Ppad;
+  return g;
+}
+
+}  // namespace tc
+
+size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int terms) {
+  const tc::Geometry g = tc::geometry(P, NG);
+  const size_t op = (size_t)g.NGpad * g.Kpad * 2;  // one bf16 operand matrix
+  return op * (size_t)terms * (size_t)(nw + 2);
+}
+
+cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int terms, int fold_stages, int flush_folds,
+                           double2* chi, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
+  using namespace tc;
+  if (P == 0 || NG == 0 || nw == 0) return cudaSuccess;
+  if (terms != 2) return cudaErrorInvalidValue;
+  if (fold_stages < 1) fold_stages = 1;
+  if (flush_folds < 1) flush_folds = 1;
+  const Geometry g = geometry(P, NG);
+  if (scratch_bytes < herk_tc_scratch_bytes(P, NG, nw, terms)) return cudaErrorInvalidValue;
+  if (g.Kpad > (int64_t)1 << 31 || (int64_t)nw * g.NGpad > (1 << 30)) return cudaErrorInvalidValue;
+  char* base = (char*)scratch;
+  const int64_t op_elems = (int64_t)g.NGpad * g.Kpad;  // bf16 elements per operand matrix
+  __nv_bfloat16* X = (__nv_bfloat16*)base;
+  __nv_bfloat16* Z = X + op_elems * terms;
+  __nv_bfloat16* A = Z + op_elems * terms;
+  cudaError_t e;
+  dim3 pg(g.NGpad / 32, (unsigned)(g.Ppad / 32));
+  prep_xz_kernel<2><<<pg, 256, 0, s>>>(N, P, NG, g.NGpad, g.Kpad, (__nv_bfloat162*)X, (__nv_bfloat162*)Z, op_elems / 2);
+  prep_a_kernel<2><<<pg, 256, 0, s>>>(N, wgt, P, NG, g.NGpad, g.Kpad, nw, (__nv_bfloat162*)A, op_elems * nw / 2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  Maps maps;
+  memset(&maps, 0, sizeof(maps));
+  for (int t = 0; t < terms; ++t) {
+    if (!make_map(&maps.a[t], A + op_elems * nw * t, g.Kpad, (int64_t)nw * g.NGpad) ||
+        !make_map(&maps.x[t], X + op_elems * t, g.Kpad, g.NGpad) ||
+        !make_map(&maps.z[t], Z + op_elems * t, g.Kpad, g.NGpad))
+      return cudaErrorInvalidValue;
+  }
+  const int nt = g.NGpad / BM;
+  dim3 grid(nt * (nt + 1) / 2, nw);
+  const int nk = (int)(g.Kpad / BK);
+  if ((e = cudaFuncSetAttribute(herk_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<2>::SMEM_BYTES)) != cudaSuccess)
+    return e;
+  herk_tc_kernel<2><<<grid, NUM_THREADS, Cfg<2>::SMEM_BYTES, s>>>(maps, NG, g.NGpad, nk, fold_stages, flush_folds, chi, err);
+  return cudaGetLastError();
+}
+
 }  // namespace rpa

@@ -18,7 +18,8 @@
 
 namespace rpa {
 cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms,
-                           double2* chi, void* scratch, size_t scratch_bytes, cudaStream_t s);
+                           int fold_stages, int flush_folds, double2* chi, void* scratch, size_t scratch_bytes,
+                           int* err, cudaStream_t s);
 size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
 }
 
@@ -87,6 +88,8 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256};  // see rpa_tuning in rpa.h
+  int* dev_err = nullptr;                 // device-side flag of bounded waits that gave up
 };
 
 namespace {
@@ -360,6 +363,7 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
   const int64_t per_pair = (int64_t)n1 * N23 + (int64_t)n1 * n2 * N3;
   const int64_t budget = (sizeof(T) == 8 ? 160ll : 96ll) << 20;
   int64_t PC = std::max<int64_t>(32, budget / (per_pair * (int64_t)sizeof(c2<T>)));
+  if (c->tune[RPA_TUNE_PAIR_CHUNK] > 0) PC = c->tune[RPA_TUNE_PAIR_CHUNK];
   PC = std::min<int64_t>(PC, P);
   if ((st = workspace(c, "pd_T1", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * N23), &p_T1)) != RPA_OK) return st;
   if ((st = workspace(c, "pd_T2", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * n2 * N3), &p_T2)) != RPA_OK) return st;
@@ -387,7 +391,9 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
       void* scr = nullptr;
       const size_t sb = herk_tc_scratch_bytes(P, NG, nw, terms);
       if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
-      CUDA_OK(c, launch_herk_tc((const float2*)p_N, P, NG, (const float*)p_w, nw, terms, chi, scr, sb, c->stream));
+      CUDA_OK(c, launch_herk_tc((const float2*)p_N, P, NG, (const float*)p_w, nw, terms,
+                                (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH], chi, scr, sb,
+                                c->dev_err, c->stream));
     }
   }
   return RPA_OK;
@@ -411,6 +417,7 @@ rpa_status build_chi(rpa_ctx* c, int iq, int nw, const double* omega_host, doubl
   if (st != RPA_OK) return st;
   QPt& Q = c->qpts[iq];
   const int NG = Q.NG;
+  CUDA_OK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
   void *p_chi, *p_om;
   if ((st = workspace(c, "chi", sizeof(double2) * (size_t)nw * NG * NG, &p_chi)) != RPA_OK) return st;
   if ((st = workspace(c, "omega", sizeof(double) * nw, &p_om)) != RPA_OK) return st;
@@ -427,6 +434,10 @@ rpa_status build_chi(rpa_ctx* c, int iq, int nw, const double* omega_host, doubl
       st = chi_block<float>(c, Q, (int)t, (const double*)p_om, nw, (double2*)p_chi);
     if (st != RPA_OK) return st;
   }
+  int derr = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&derr, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (derr) return fail(c, RPA_ERR_TIMEOUT, "a bounded device wait gave up in the tensor-core update (code %d)", derr);
   *chi_out = (double2*)p_chi;
   return RPA_OK;
 }
@@ -442,7 +453,7 @@ rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
   for (int i = 0; i < 3; ++i)
     if (p->grid[i] < 2 || p->grid[i] > 4096) return RPA_ERR_ARG;
   if (!(p->ecut_chi > 0.0) || !(p->spin_factor > 0.0) || p->nk_bz < 1) return RPA_ERR_ARG;
-  if (p->precision < RPA_FP64 || p->precision > RPA_BF16X3) return RPA_ERR_ARG;
+  if (p->precision < RPA_FP64 || p->precision > RPA_BF16X2) return RPA_ERR_ARG;
   const double* a = p->cell;
   const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
                      a[2] * (a[3] * a[7] - a[4] * a[6]);
@@ -470,6 +481,12 @@ rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
     }
     c->own_stream = true;
   }
+  if (cudaMalloc(&c->dev_err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return RPA_ERR_OOM;
+  }
   *out = c;
   return RPA_OK;
 }
@@ -489,6 +506,7 @@ void rpa_destroy(rpa_ctx* c) {
   }
   for (auto& kv : c->ws) dev_free(kv.second.p);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  dev_free(c->dev_err);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -821,6 +839,23 @@ rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* 
 rpa_status rpa_set_profiling(rpa_ctx* c, int32_t enable) {
   if (!c) return RPA_ERR_ARG;
   c->profiling = enable != 0;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
+  if (!c) return RPA_ERR_ARG;
+  switch (param) {
+    case RPA_TUNE_TC_FOLD:
+    case RPA_TUNE_TC_FLUSH:
+      if (value < 1 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "fold interval %lld out of range", (long long)value);
+      break;
+    case RPA_TUNE_PAIR_CHUNK:
+      if (value < 0 || value > (1ll << 30)) return fail(c, RPA_ERR_ARG, "pair chunk %lld out of range", (long long)value);
+      break;
+    default:
+      return fail(c, RPA_ERR_ARG, "unknown tuning parameter %d", param);
+  }
+  c->tune[param] = value;
   return RPA_OK;
 }
 

@@ -10,13 +10,16 @@ from paper_1307_8052_gb300.build import build
 
 pytestmark = pytest.mark.gpu
 
-# tolerances: FP64 mode to the benchmark spec's 1e-10 relative on E_c (chi0 elementwise
-# relative to its largest element); FP32 and split-bfloat16 modes to 1e-6 on E_c
+# Tolerances.  E_c: 1e-10 relative in FP64, 1e-6 relative in the FP32 and
+# split-bfloat16 modes.  chi0: elementwise, relative to its largest element.
+# Per-frequency terms e(w): the E_c bound, except bf16x2 where a two-term
+# bfloat16 split represents each operand to 2^-16 relative; on the 240-pair
+# tiny case that averages down only to ~1.5e-6 per term, so the per-term bound
+# there is 5e-6 (the summed E_c still has to meet 1e-6).
 TOL = {
-    "fp64": dict(chi=1e-11, ec=1e-10),
-    "fp32": dict(chi=4e-6, ec=1e-6),
-    "bf16x2": dict(chi=2e-5, ec=1e-6),
-    "bf16x3": dict(chi=4e-6, ec=1e-6),
+    "fp64": dict(chi=1e-11, ec=1e-10, term=1e-10),
+    "fp32": dict(chi=4e-6, ec=1e-6, term=1e-6),
+    "bf16x2": dict(chi=2e-5, ec=1e-6, term=5e-6),
 }
 
 
@@ -46,7 +49,7 @@ def _rel(a, b_):
     return np.abs(a - b_).max() / np.abs(b_).max()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
 def test_config0_chi_and_energy(precision):
     p = syn.config0()
     om, W = o.frequency_grid(p.nw)
@@ -60,12 +63,12 @@ def test_config0_chi_and_energy(precision):
         E, terms = b.rpa_energy(ctx, [0], [1.0], om, W)
         Er, tr = o.energy(p, om, W)
         assert abs(E - Er) < TOL[precision]["ec"] * abs(Er)
-        assert np.abs(terms[0] - tr[0]).max() < TOL[precision]["ec"] * np.abs(tr).max()
+        assert np.abs(terms[0] - tr[0]).max() < TOL[precision]["term"] * np.abs(tr).max()
     finally:
         b.rpa_destroy(ctx)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
 def test_small_mesh_umklapp_paw_all_q(precision):
     """2x1x1 mesh (umklapp at q = 1/2), ragged Miller boxes, two PAW atoms."""
     p = syn.small_problem()
@@ -112,7 +115,7 @@ def test_device_pointers_match_host():
         b.rpa_destroy(ctx_d)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
 def test_config1_geometry_two_transitions(precision):
     """Full config-1 geometry (9 bohr box, 40^3 grid, 20 Ha orbitals, NG ~ 1200,
     3 x 13 projectors) with a band subset and two transitions of q = (0, 1/2, 1/2),
@@ -136,6 +139,46 @@ def test_config1_geometry_two_transitions(precision):
         chi = b.rpa_chi0(ctx, 0, om)
         ref = o.chi0(p, 0, om, _oracle_Q(p, 0))
         assert _rel(chi, ref) < TOL[precision]["chi"]
+    finally:
+        b.rpa_destroy(ctx)
+
+
+def test_config1_full_size_sampled_bf16x2():
+    """The bench's workload at full size (all 8 k, 16 occupied x 1200 empty bands,
+    PAW) in the bench's mode and launch configuration: chi0 elements on sampled
+    G rows/columns against the oracle evaluated at those G only, plus properties
+    that hold at any size (Hermitian, non-positive diagonal)."""
+    p = syn.config1()
+    iq = 3
+    om, _ = o.frequency_grid(16)
+    ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, "bf16x2")
+    try:
+        b.load_problem(ctx, p, qs=[iq], paw_Q=lambda i, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[i].q_red, gm))
+        chi = b.rpa_chi0(ctx, iq, om)
+    finally:
+        b.rpa_destroy(ctx)
+    ng = chi.shape[1]
+    gidx = [0, 1, 17, ng // 2, ng - 2, ng - 1]
+    ref = o.chi0_sampled(p, iq, om, gidx, _oracle_Q(p, iq))
+    got = chi[:, gidx][:, :, gidx]
+    assert np.abs(got - ref).max() / np.abs(ref).max() < TOL["bf16x2"]["chi"]
+    assert np.array_equal(chi[3], chi[3].conj().T)
+    assert np.all(np.einsum("wii->wi", chi).real <= 0)
+
+
+def test_tuning_knobs_change_rounding_only():
+    p = syn.small_problem(config_tag=95)
+    om, _ = o.frequency_grid(4)
+    ctx = _ctx(p, "bf16x2")
+    try:
+        a = b.rpa_chi0(ctx, 1, om)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FOLD, 4)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_PAIR_CHUNK, 7)
+        c = b.rpa_chi0(ctx, 1, om)
+        assert _rel(c, a) < TOL["bf16x2"]["chi"]
+        with pytest.raises(b.RpaError) as e:
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FOLD, 0)
+        assert e.value.status == b.RPA_ERR_ARG
     finally:
         b.rpa_destroy(ctx)
 
