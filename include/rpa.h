@@ -183,6 +183,34 @@ typedef enum {
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 
+/* Allocation-free log-det terms, for callers that must not allocate device
+ * memory themselves: code whose device memory is owned by another allocator
+ * (a framework's caching pool, or a fixed per-process budget) and loops that
+ * cannot afford cudaMalloc/cudaFree, which may synchronize the device.  The
+ * paper has no counterpart; this is the FP64 log-det of the energy path
+ * (rpa_energy) made callable on its own without a context.
+ *
+ * For each frequency w < nw it writes
+ *   terms[w] = ln det(1 - v^1/2 chi[w] v^1/2) + tr(v^1/2 chi[w] v^1/2)
+ * chi: device [nw][ng][ng] complex (interleaved doubles; only the lower
+ * triangle is read), v: device [ng], terms: device [nw].  The work runs on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream) of the current
+ * device, and the call returns after that stream has finished it.
+ *
+ * Scratch: one process-wide static device array per device (16 MiB + 2 KiB,
+ * held until the process exits).  Limits: 1 <= nw <= 64 and
+ * nw * ng * ng <= 1048576 (e.g. ng <= 256 at nw = 16); larger sizes, null or
+ * host pointers return RPA_ERR_ARG without touching the GPU.  The first call on
+ * a device looks up the scratch address on that device (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Every call reuses the same array and
+ * leaves its contents behind (each call rewrites what it reads), so calls
+ * that overlap on the GPU, from several host threads or several streams, race
+ * and must be serialised by the caller.  Returns RPA_ERR_NOT_HPD if a Cholesky
+ * pivot is not positive, RPA_ERR_CUDA on a CUDA error. */
+rpa_status rpa_logdet_noalloc(const double* chi, const double* v, int32_t nw,
+                              int32_t ng, double* terms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,7 @@ SIGNATURES = {
     "rpa_set_profiling": (_I, [_P, _I]),
     "rpa_get_profile": (_I, [_P, _P, _P]),
     "rpa_set_tuning": (_I, [_P, _I, ct.c_int64]),
+    "rpa_logdet_noalloc": (_I, [_P, _P, _I, _I, _P, _P]),
 }
 RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK = 0, 1
 
@@ -207,6 +208,14 @@ def rpa_set_profiling(ctx, enable=True):
 
 def rpa_set_tuning(ctx, param, value):
     _check(ctx, lib().rpa_set_tuning(ctx, int(param), int(value)))
+
+
+def rpa_logdet_noalloc(chi, v, terms, stream=0):
+    """Allocation-free log-det terms from device tensors chi [nw][ng][ng] (complex128),
+    v [ng] and terms [nw] (float64); see include/rpa.h."""
+    nw, ng = int(chi.shape[0]), int(chi.shape[1])
+    _check(None, lib().rpa_logdet_noalloc(_ptr(chi), _ptr(v), nw, ng, _ptr(terms),
+                                          ct.c_void_p(int(stream)) if stream else None))
 
 
 def rpa_get_profile(ctx):

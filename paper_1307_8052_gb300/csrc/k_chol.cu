@@ -8,6 +8,7 @@
 // the panel below it by a triangular solve, and the trailing lower triangle is
 // updated with 64x64 DFMA tiles.  A pivot that is not positive (or NaN) sets a
 // device flag that the host turns into RPA_ERR_NOT_HPD; the kernels never trap.
+#include "rpa.h"
 #include "rpa_internal.h"
 
 namespace rpa {
@@ -188,6 +189,12 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double2* __restrict__ 
     }
 }
 
+__global__ void add_terms_kernel(const double* __restrict__ ld, const double* __restrict__ tr, int nw,
+                                 double* __restrict__ terms) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < nw) terms[w] = ld[w] + tr[w];
+}
+
 static inline int gridc(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
@@ -225,4 +232,73 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- allocation-free entry point
+// Scratch of rpa_logdet_noalloc: the Cholesky work matrix (up to
+// kNoAllocMaxElems complex elements) followed by the per-frequency log-det and
+// trace accumulators and the pivot flag.  It lives for the life of the process
+// on every device that loads the library (16 MiB + 2 KiB).
+constexpr int64_t kNoAllocMaxElems = (int64_t)1 << 20;
+constexpr int kNoAllocMaxNw = 64;
+constexpr int64_t kNoAllocSlots = kNoAllocMaxElems + kNoAllocMaxNw + 1;  // double2 slots
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
+
 }  // namespace rpa
+
+#include <mutex>
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" rpa_status rpa_logdet_noalloc(const double* chi, const double* v, int32_t nw, int32_t ng, double* terms,
+                                         void* stream) {
+  using namespace rpa;
+  if (!chi || !v || !terms || nw < 1 || ng < 1) return RPA_ERR_ARG;
+  if (nw > kNoAllocMaxNw || (int64_t)nw * ng * ng > kNoAllocMaxElems) return RPA_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return RPA_ERR_CUDA;
+  }
+  for (const void* p : {(const void*)chi, (const void*)v, (const void*)terms}) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return RPA_ERR_ARG;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return RPA_ERR_ARG;
+  }
+  // one-time set-up per device: the device address of the static scratch
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return RPA_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double2* work = (double2*)base;
+  double* ld = (double*)(work + kNoAllocMaxElems);
+  double* tr = ld + kNoAllocMaxNw;
+  int* flag = (int*)(tr + kNoAllocMaxNw);
+  // run_logdet clears the log-det accumulators and the flag itself; the work
+  // matrix is fully rewritten from chi before it is read
+  if (run_logdet((const double2*)chi, v, nw, ng, work, ld, tr, flag, s, nullptr) != cudaSuccess) return RPA_ERR_CUDA;
+  add_terms_kernel<<<(nw + 63) / 64, 64, 0, s>>>(ld, tr, nw, terms);
+  if (cudaGetLastError() != cudaSuccess) return RPA_ERR_CUDA;
+  int h_flag = 0;
+  if (cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return RPA_ERR_CUDA;
+  }
+  return h_flag ? RPA_ERR_NOT_HPD : RPA_OK;
+}
