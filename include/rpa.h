@@ -82,7 +82,7 @@ typedef struct {
 } rpa_params;
 
 /* Creates a context on params->device.  Validates the cell (non-singular),
- * grid (each N_i in [2, 4096]), ecut_chi > 0, spin_factor > 0, nk_bz >= 1 and
+ * grid (each N_i in [2, 768]), ecut_chi > 0, spin_factor > 0, nk_bz >= 1 and
  * the precision.  *out receives the context; RPA_ERR_ARG on bad parameters,
  * RPA_ERR_CUDA if the device cannot be used. */
 rpa_status rpa_create(const rpa_params* params, rpa_ctx** out);
@@ -174,12 +174,18 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      so the transform intermediates stay in L2.
  * RPA_TUNE_TC_FLUSH    folds between additions of the register running sums
  *                      to the FP64 chi0, in [1, 2^20]; default 256.
+ * RPA_TUNE_PD_GRID     0 (default): wavefunctions and pair densities use,
+ *                      per axis, the smallest grid on which the transform of
+ *                      Eq. 10 has no aliasing for the transitions of the call
+ *                      (never larger than params.grid); results equal the
+ *                      plane-wave sums of Eq. 4 either way.  1: params.grid.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
   RPA_TUNE_PAIR_CHUNK = 1,
   RPA_TUNE_TC_FLUSH = 2,
-  RPA_TUNE_COUNT = 3
+  RPA_TUNE_PD_GRID = 3,
+  RPA_TUNE_COUNT = 4
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

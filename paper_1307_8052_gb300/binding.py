@@ -44,7 +44,7 @@ SIGNATURES = {
     "rpa_set_tuning": (_I, [_P, _I, ct.c_int64]),
     "rpa_logdet_noalloc": (_I, [_P, _P, _I, _I, _P, _P]),
 }
-RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK = 0, 1
+RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID = 0, 1, 2, 3
 
 
 class RpaParams(ct.Structure):

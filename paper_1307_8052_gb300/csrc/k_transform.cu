@@ -121,49 +121,82 @@ cudaError_t launch_scatter_box(const double2* C, int nb, int npw, const int* pos
 
 // ---------------------------------------------------------------- pair density stage A
 // T1[pl][o][j23] = sum_j1 conj(u_n(j1, j23)) u_m(j1, j23) exp(-2 pi i g1 j1 / N1), g1 = g1lo + o
-template <typename T, int TO>
+// The twiddle matrix tw[j][o] = exp(-2 pi i (lo+o) j / N) of the pruned outputs
+// sits in shared memory; every thread of a warp reads the same entry (broadcast).
+template <typename T>
+__device__ inline void fill_twiddle_matrix(c2<T>* tw, int N, int lo, int nout, int NO) {
+  for (int e = threadIdx.x; e < N * NO; e += blockDim.x) {
+    const int j = e / NO, o = e % NO;
+    if (o < nout) {
+      const int t = pmod(-(int64_t)(lo + o) * j, N);
+      double s, c;
+      sincospi(2.0 * (double)t / (double)N, &s, &c);
+      tw[e] = mk<T>((T)c, (T)s);
+    } else {
+      tw[e] = mk<T>(0, 0);
+    }
+  }
+  __syncthreads();
+}
+
+// Each thread owns one (j2, j3) line point and PP consecutive pairs, and keeps
+// all NO outputs g1 of each pair in registers while it streams j1.
+template <typename T, int NO, int PP>
 __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
                                                         int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
                                                         const int* __restrict__ Ridx, int nR, int64_t p0, int np,
                                                         int g1lo, int n1, c2<T>* __restrict__ T1) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
-  fill_twiddles<T>(tw, N1);
-  const int nchunk = (n1 + TO - 1) / TO;
-  const int64_t total = (int64_t)np * nchunk * N23;
-  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    const int j23 = (int)(id % N23);
-    int64_t r = id / N23;
-    const int oc = (int)(r % nchunk);
-    const int pl = (int)(r / nchunk);
-    const int64_t p = p0 + pl;
-    const int n = Lidx[p / nR];
-    const int m = Ridx[p % nR];
-    const c2<T>* un = Uk + (int64_t)n * Nr + j23;
-    const c2<T>* um = Ukp + (int64_t)m * Nr + j23;
-    const int o0 = oc * TO;
-    int idx[TO], step[TO];
-    c2<T> acc[TO];
+  const int nchunk = (n1 + NO - 1) / NO;
+  const int ngrp = (np + PP - 1) / PP;
+  for (int oc = 0; oc < nchunk; ++oc) {
+    const int o0 = oc * NO;
+    const int nout = min(NO, n1 - o0);
+    if (oc) __syncthreads();
+    fill_twiddle_matrix<T>(tw, N1, g1lo + o0, nout, NO);
+    const int64_t total = (int64_t)ngrp * N23;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+      const int j23 = (int)(id % N23);
+      const int grp = (int)(id / N23);
+      const c2<T>* un[PP];
+      const c2<T>* um[PP];
 #pragma unroll
-    for (int t = 0; t < TO; ++t) {
-      step[t] = pmod(-(int64_t)(g1lo + o0 + t), N1);
-      idx[t] = 0;
-      acc[t] = mk<T>(0, 0);
-    }
-    for (int j1 = 0; j1 < N1; ++j1) {
-      const c2<T> x = cj_mul<T>(un[(int64_t)j1 * N23], um[(int64_t)j1 * N23]);
+      for (int q = 0; q < PP; ++q) {
+        const int pl = min(grp * PP + q, np - 1);
+        const int64_t p = p0 + pl;
+        un[q] = Uk + (int64_t)Lidx[p / nR] * Nr + j23;
+        um[q] = Ukp + (int64_t)Ridx[p % nR] * Nr + j23;
+      }
+      c2<T> acc[PP][NO];
 #pragma unroll
-      for (int t = 0; t < TO; ++t) {
-        cmac<T>(acc[t], x, tw[idx[t]]);
-        idx[t] += step[t];
-        if (idx[t] >= N1) idx[t] -= N1;
+      for (int q = 0; q < PP; ++q)
+#pragma unroll
+        for (int t = 0; t < NO; ++t) acc[q][t] = mk<T>(0, 0);
+      for (int j1 = 0; j1 < N1; ++j1) {
+        c2<T> x[PP];
+#pragma unroll
+        for (int q = 0; q < PP; ++q) x[q] = cj_mul<T>(un[q][(int64_t)j1 * N23], um[q][(int64_t)j1 * N23]);
+        const c2<T>* twj = tw + j1 * NO;
+#pragma unroll
+        for (int t = 0; t < NO; ++t) {
+          const c2<T> f = twj[t];
+#pragma unroll
+          for (int q = 0; q < PP; ++q) cmac<T>(acc[q][t], x[q], f);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PP; ++q) {
+        const int pl = grp * PP + q;
+        if (pl < np) {
+          c2<T>* dst = T1 + ((int64_t)pl * n1 + o0) * N23 + j23;
+#pragma unroll
+          for (int t = 0; t < NO; ++t)
+            if (t < nout) dst[(int64_t)t * N23] = acc[q][t];
+        }
       }
     }
-    c2<T>* dst = T1 + ((int64_t)pl * n1 + o0) * N23 + j23;
-#pragma unroll
-    for (int t = 0; t < TO; ++t)
-      if (o0 + t < n1) dst[(int64_t)t * N23] = acc[t];
   }
 }
 
@@ -171,11 +204,68 @@ template <typename T>
 cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
                              const int* Ridx, int nR, int64_t p0, int np, int g1lo, int n1, c2<T>* T1,
                              cudaStream_t s) {
-  constexpr int TO = 8;
-  const int64_t total = (int64_t)np * ((n1 + TO - 1) / TO) * N23;
+  constexpr int NO = 16;
+  constexpr int PP = sizeof(T) == 4 ? 2 : 1;
+  const int64_t total = (int64_t)((np + PP - 1) / PP) * N23;
   if (total == 0) return cudaSuccess;
-  pd_stageA_kernel<T, TO><<<grid_for(total, 256), 256, N1 * sizeof(c2<T>), s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx,
-                                                                              nR, p0, np, g1lo, n1, T1);
+  const int smem = N1 * NO * (int)sizeof(c2<T>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pd_stageA_kernel<T, NO, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  pd_stageA_kernel<T, NO, PP><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np,
+                                                                     g1lo, n1, T1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pair density stage B
+// T2[pl][o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i g2 j2 / N2), g2 = g2lo + o2
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict__ T1, c2<T>* __restrict__ T2,
+                                                        int64_t rows, int N2, int N3, int g2lo, int n2) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  const int nchunk = (n2 + NO - 1) / NO;
+  for (int oc = 0; oc < nchunk; ++oc) {
+    const int o0 = oc * NO;
+    const int nout = min(NO, n2 - o0);
+    if (oc) __syncthreads();
+    fill_twiddle_matrix<T>(tw, N2, g2lo + o0, nout, NO);
+    const int64_t total = rows * N3;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+      const int j3 = (int)(id % N3);
+      const int64_t r = id / N3;  // (pl, o1)
+      const c2<T>* src = T1 + r * (int64_t)N2 * N3 + j3;
+      c2<T> acc[NO];
+#pragma unroll
+      for (int t = 0; t < NO; ++t) acc[t] = mk<T>(0, 0);
+      for (int j2 = 0; j2 < N2; ++j2) {
+        const c2<T> x = src[(int64_t)j2 * N3];
+        const c2<T>* twj = tw + j2 * NO;
+#pragma unroll
+        for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x, twj[t]);
+      }
+      c2<T>* dst = T2 + (r * n2 + o0) * N3 + j3;
+#pragma unroll
+      for (int t = 0; t < NO; ++t)
+        if (t < nout) dst[(int64_t)t * N3] = acc[t];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, int g2lo, int n2,
+                             cudaStream_t s) {
+  constexpr int NO = 16;
+  const int64_t rows = (int64_t)np * n1;
+  if (rows == 0) return cudaSuccess;
+  const int smem = N2 * NO * (int)sizeof(c2<T>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pd_stageB_kernel<T, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  pd_stageB_kernel<T, NO><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, g2lo, n2);
   return cudaGetLastError();
 }
 
@@ -324,6 +414,7 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
   template cudaError_t launch_dft_axis<T>(const c2<T>*, c2<T>*, int64_t, int, int, int, int, int, int, int, int, \
                                           cudaStream_t);                                                         \
   template cudaError_t launch_scatter_box<T>(const double2*, int, int, const int*, int64_t, c2<T>*, cudaStream_t); \
+  template cudaError_t launch_pd_stageB<T>(const c2<T>*, c2<T>*, int, int, int, int, int, int, cudaStream_t);     \
   template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
                                            int, int64_t, int, int, int, c2<T>*, cudaStream_t);                   \
   template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \

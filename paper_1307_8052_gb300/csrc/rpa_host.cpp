@@ -28,6 +28,9 @@ using namespace rpa;
 namespace {
 
 constexpr int kMaxIndex = 4096;
+// twiddle matrices of the pruned transforms (grid axis x 16 outputs, complex
+// double) must fit in shared memory
+constexpr int kMaxGrid = 768;
 
 struct DevBuf {
   void* p = nullptr;
@@ -53,6 +56,7 @@ struct OrbSet {
   int KP = 0;
   double2* P = nullptr;
   void* U = nullptr;  // grids [nb][Nr] in working precision (valid while grid_stamp == ctx stamp)
+  size_t Ubytes = 0;
   uint64_t grid_stamp = 0;
 };
 
@@ -88,7 +92,8 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0};  // see rpa_tuning in rpa.h
+  int tg[3] = {0, 0, 0};  // transform grid of the current call (<= prm.grid)
   int* dev_err = nullptr;                 // device-side flag of bounded waits that gave up
 };
 
@@ -226,12 +231,18 @@ int work_bytes_per_complex(const rpa_ctx* c) { return c->prm.precision == RPA_FP
 // ---- stage a1: every band of a set onto the real-space grid (Eq. 8, Table 1 step 3)
 template <typename T>
 rpa_status build_grids_T(rpa_ctx* c, OrbSet& s) {
-  const int N1 = c->prm.grid[0], N2 = c->prm.grid[1], N3 = c->prm.grid[2];
+  const int N1 = c->tg[0], N2 = c->tg[1], N3 = c->tg[2];
   const int64_t Nr = (int64_t)N1 * N2 * N3;
   const size_t need = sizeof(c2<T>) * (size_t)s.nb * Nr;
+  if (s.U && s.Ubytes < need) {
+    dev_free(s.U);
+    s.U = nullptr;
+    s.Ubytes = 0;
+  }
   if (!s.U) {
     rpa_status st = dev_alloc(c, &s.U, need);
     if (st != RPA_OK) return st;
+    s.Ubytes = need;
   }
   const int L1 = s.mhi[0] - s.mlo[0] + 1, L2 = s.mhi[1] - s.mlo[1] + 1, L3 = s.mhi[2] - s.mlo[2] + 1;
   const int64_t box = (int64_t)L1 * L2 * L3;
@@ -268,6 +279,42 @@ rpa_status build_grids(rpa_ctx* c, OrbSet& s) {
   return build_grids_T<float>(c, s);
 }
 
+// ---- transform grid of a call
+// The product conj(u_nk) u_m,k' has plane-wave components Q_m - Q_n; the
+// transform of Eq. 10 evaluated at g = G + G0 equals the plane-wave sum of
+// Eq. 4 exactly when no other component is congruent to g modulo N, i.e. when
+// max(Q_m) - min(Q_n) - min(g) <= N - 1 and min(Q_m) - max(Q_n) - max(g) >= 1 - N.
+// The smallest N per axis that satisfies this for every transition of the
+// call (and holds each orbital sphere) gives identical results with fewer grid
+// points than the caller's grid, which is the upper bound (rpa_set_qpoint
+// checked it).  RPA_TUNE_PD_GRID = 1 keeps the caller's grid instead.
+void choose_transform_grid(rpa_ctx* c, const int* iqs, int nq) {
+  for (int d = 0; d < 3; ++d) c->tg[d] = 2;
+  if (c->tune[RPA_TUNE_PD_GRID] == 1) {
+    for (int d = 0; d < 3; ++d) c->tg[d] = c->prm.grid[d];
+    return;
+  }
+  for (int i = 0; i < nq; ++i) {
+    const QPt& Q = c->qpts[iqs[i]];
+    for (size_t t = 0; t < Q.k_of.size(); ++t) {
+      const OrbSet& a = c->sets[Q.k_of[t]];
+      const OrbSet& b = c->sets[Q.kq_of[t]];
+      for (int d = 0; d < 3; ++d) {
+        int glo = 1 << 30, ghi = -(1 << 30);
+        for (int g = 0; g < Q.NG; ++g) {
+          const int v = Q.gm[3 * g + d] + Q.G0[3 * t + d];
+          glo = std::min(glo, v);
+          ghi = std::max(ghi, v);
+        }
+        int need = std::max(b.mhi[d] - a.mlo[d] - glo, ghi + a.mhi[d] - b.mlo[d]) + 1;
+        need = std::max(need, std::max(a.mhi[d] - a.mlo[d] + 1, b.mhi[d] - b.mlo[d] + 1));
+        c->tg[d] = std::max(c->tg[d], need);
+      }
+    }
+  }
+  for (int d = 0; d < 3; ++d) c->tg[d] = std::min(c->tg[d], c->prm.grid[d]);
+}
+
 // ---- stages a2-a4 for one q-point: chi accumulates in FP64 lower triangle
 template <typename T>
 rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, double2* chi) {
@@ -276,7 +323,7 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
   const int nL = (int)sk.L.size(), nR = (int)skp.R.size();
   const int64_t P = (int64_t)nL * nR;
   if (P == 0) return RPA_OK;
-  const int N1 = c->prm.grid[0], N2 = c->prm.grid[1], N3 = c->prm.grid[2];
+  const int N1 = c->tg[0], N2 = c->tg[1], N3 = c->tg[2];
   const int64_t Nr = (int64_t)N1 * N2 * N3;
   const int NG = Q.NG;
   const int* G0 = &Q.G0[3 * t];
@@ -373,8 +420,7 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
       const int np = (int)std::min<int64_t>(PC, P - p0);
       CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, sk.L_d, skp.R_d, nR,
                                      p0, np, glo[0], n1, (c2<T>*)p_T1, c->stream));
-      CUDA_OK(c, launch_dft_axis<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, n2, N3, N2, 0, glo[1], -1,
-                                    c->stream));
+      CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, glo[1], n2, c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
                                      1.0 / (double)Nr, Rp, Pm, KP, skp.R_d, nR, p0, (c2<T>*)p_N, c->stream));
       tm.add_launches(3);
@@ -451,7 +497,7 @@ rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
   if (!p || !out) return RPA_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < 3; ++i)
-    if (p->grid[i] < 2 || p->grid[i] > 4096) return RPA_ERR_ARG;
+    if (p->grid[i] < 2 || p->grid[i] > kMaxGrid) return RPA_ERR_ARG;
   if (!(p->ecut_chi > 0.0) || !(p->spin_factor > 0.0) || p->nk_bz < 1) return RPA_ERR_ARG;
   if (p->precision < RPA_FP64 || p->precision > RPA_BF16X2) return RPA_ERR_ARG;
   const double* a = p->cell;
@@ -772,8 +818,11 @@ rpa_status rpa_chi0(rpa_ctx* c, int32_t iq, int32_t nw, const double* omega, dou
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   prof_begin(c);
   ++c->stamp;
+  rpa_status st = check_q_ready(c, iq);
+  if (st != RPA_OK) return st;
+  choose_transform_grid(c, &iq, 1);
   double2* chi = nullptr;
-  rpa_status st = build_chi(c, iq, nw, omega, &chi);
+  st = build_chi(c, iq, nw, omega, &chi);
   if (st != RPA_OK) return st;
   const int NG = c->qpts[iq].NG;
   {
@@ -797,6 +846,11 @@ rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* 
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   prof_begin(c);
   ++c->stamp;
+  for (int i = 0; i < nq; ++i) {
+    rpa_status st = check_q_ready(c, iqs[i]);
+    if (st != RPA_OK) return st;
+  }
+  choose_transform_grid(c, iqs, nq);
   double E = 0.0;
   std::vector<double> ld(nw), tr(nw);
   for (int i = 0; i < nq; ++i) {
@@ -851,6 +905,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_PAIR_CHUNK:
       if (value < 0 || value > (1ll << 30)) return fail(c, RPA_ERR_ARG, "pair chunk %lld out of range", (long long)value);
+      break;
+    case RPA_TUNE_PD_GRID:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "transform grid choice must be 0 or 1");
       break;
     default:
       return fail(c, RPA_ERR_ARG, "unknown tuning parameter %d", param);

@@ -183,6 +183,22 @@ def test_tuning_knobs_change_rounding_only():
         b.rpa_destroy(ctx)
 
 
+def test_minimal_transform_grid_equals_caller_grid():
+    """The alias-free minimal transform grid and the caller's full grid give the
+    same chi0 (both equal the plane-wave sums of Eq. 4)."""
+    p = syn.small_problem(config_tag=96, grid=(20, 22, 18))
+    om, _ = o.frequency_grid(3)
+    ctx = _ctx(p, "fp64")
+    try:
+        a = b.rpa_chi0(ctx, 1, om)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_PD_GRID, 1)
+        c = b.rpa_chi0(ctx, 1, om)
+    finally:
+        b.rpa_destroy(ctx)
+    assert _rel(a, c) < 1e-12
+    assert _rel(a, o.chi0(p, 1, om, _oracle_Q(p, 1))) < TOL["fp64"]["chi"]
+
+
 def test_not_hpd_is_reported_not_trapped():
     """Mirrored band energies (occupied above empty by the same gaps) flip the sign
     of chi0, so 1 - v^1/2 chi0 v^1/2 has eigenvalues below zero: the Cholesky
