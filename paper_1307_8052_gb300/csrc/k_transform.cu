@@ -121,13 +121,18 @@ cudaError_t launch_scatter_box(const double2* C, int nb, int npw, const int* pos
 
 // ---------------------------------------------------------------- pair density stage A
 // T1[pl][o][j23] = sum_j1 conj(u_n(j1, j23)) u_m(j1, j23) exp(-2 pi i g1 j1 / N1), g1 = g1lo + o
-// The twiddle matrix tw[j][o] = exp(-2 pi i (lo+o) j / N) of the pruned outputs
-// sits in shared memory; every thread of a warp reads the same entry (broadcast).
+// The twiddle matrices tw[oc][j][o] = exp(-2 pi i (lo + 16 oc + o) j / N) of the
+// pruned outputs are built once per transform (FP64 sincospi of an exactly
+// reduced integer phase) in global memory; each block copies its chunk into
+// shared memory, where every thread of a warp reads the same entry (broadcast).
 template <typename T>
-__device__ inline void fill_twiddle_matrix(c2<T>* tw, int N, int lo, int nout, int NO) {
-  for (int e = threadIdx.x; e < N * NO; e += blockDim.x) {
-    const int j = e / NO, o = e % NO;
-    if (o < nout) {
+__global__ void twiddle_matrix_kernel(c2<T>* __restrict__ tw, int N, int lo, int n, int NO, int nchunk) {
+  const int64_t total = (int64_t)nchunk * N * NO;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int oc = (int)(e / ((int64_t)N * NO));
+    const int r = (int)(e % ((int64_t)N * NO));
+    const int j = r / NO, o = oc * NO + r % NO;
+    if (o < n) {
       const int t = pmod(-(int64_t)(lo + o) * j, N);
       double s, c;
       sincospi(2.0 * (double)t / (double)N, &s, &c);
@@ -136,6 +141,21 @@ __device__ inline void fill_twiddle_matrix(c2<T>* tw, int N, int lo, int nout, i
       tw[e] = mk<T>(0, 0);
     }
   }
+}
+
+template <typename T>
+cudaError_t launch_twiddle_matrix(c2<T>* tw, int N, int lo, int n, cudaStream_t s) {
+  constexpr int NO = 16;
+  const int nchunk = (n + NO - 1) / NO;
+  const int64_t total = (int64_t)nchunk * N * NO;
+  if (total == 0) return cudaSuccess;
+  twiddle_matrix_kernel<T><<<grid_for(total, 256), 256, 0, s>>>(tw, N, lo, n, NO, nchunk);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__device__ inline void load_twiddle_matrix(c2<T>* tw, const c2<T>* __restrict__ src, int count) {
+  for (int e = threadIdx.x; e < count; e += blockDim.x) tw[e] = src[e];
   __syncthreads();
 }
 
@@ -145,7 +165,8 @@ template <typename T, int NO, int PP>
 __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
                                                         int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
                                                         const int* __restrict__ Ridx, int nR, int64_t p0, int np,
-                                                        int g1lo, int n1, c2<T>* __restrict__ T1) {
+                                                        const c2<T>* __restrict__ twg, int n1,
+                                                        c2<T>* __restrict__ T1) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
   const int nchunk = (n1 + NO - 1) / NO;
@@ -154,7 +175,7 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
     const int o0 = oc * NO;
     const int nout = min(NO, n1 - o0);
     if (oc) __syncthreads();
-    fill_twiddle_matrix<T>(tw, N1, g1lo + o0, nout, NO);
+    load_twiddle_matrix<T>(tw, twg + (int64_t)oc * N1 * NO, N1 * NO);
     const int64_t total = (int64_t)ngrp * N23;
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x) {
@@ -202,7 +223,7 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
 
 template <typename T>
 cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                             const int* Ridx, int nR, int64_t p0, int np, int g1lo, int n1, c2<T>* T1,
+                             const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
                              cudaStream_t s) {
   constexpr int NO = 16;
   constexpr int PP = sizeof(T) == 4 ? 2 : 1;
@@ -214,7 +235,7 @@ cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int 
     if (e != cudaSuccess) return e;
   }
   pd_stageA_kernel<T, NO, PP><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np,
-                                                                     g1lo, n1, T1);
+                                                                     tw, n1, T1);
   return cudaGetLastError();
 }
 
@@ -222,7 +243,8 @@ cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int 
 // T2[pl][o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i g2 j2 / N2), g2 = g2lo + o2
 template <typename T, int NO>
 __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict__ T1, c2<T>* __restrict__ T2,
-                                                        int64_t rows, int N2, int N3, int g2lo, int n2) {
+                                                        int64_t rows, int N2, int N3,
+                                                        const c2<T>* __restrict__ twg, int n2) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
   const int nchunk = (n2 + NO - 1) / NO;
@@ -230,7 +252,7 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
     const int o0 = oc * NO;
     const int nout = min(NO, n2 - o0);
     if (oc) __syncthreads();
-    fill_twiddle_matrix<T>(tw, N2, g2lo + o0, nout, NO);
+    load_twiddle_matrix<T>(tw, twg + (int64_t)oc * N2 * NO, N2 * NO);
     const int64_t total = rows * N3;
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x) {
@@ -255,7 +277,7 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
 }
 
 template <typename T>
-cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, int g2lo, int n2,
+cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
                              cudaStream_t s) {
   constexpr int NO = 16;
   const int64_t rows = (int64_t)np * n1;
@@ -265,7 +287,7 @@ cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2,
     cudaError_t e = cudaFuncSetAttribute(pd_stageB_kernel<T, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  pd_stageB_kernel<T, NO><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, g2lo, n2);
+  pd_stageB_kernel<T, NO><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, tw, n2);
   return cudaGetLastError();
 }
 
@@ -414,9 +436,11 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
   template cudaError_t launch_dft_axis<T>(const c2<T>*, c2<T>*, int64_t, int, int, int, int, int, int, int, int, \
                                           cudaStream_t);                                                         \
   template cudaError_t launch_scatter_box<T>(const double2*, int, int, const int*, int64_t, c2<T>*, cudaStream_t); \
-  template cudaError_t launch_pd_stageB<T>(const c2<T>*, c2<T>*, int, int, int, int, int, int, cudaStream_t);     \
+  template cudaError_t launch_pd_stageB<T>(const c2<T>*, c2<T>*, int, int, int, int, const c2<T>*, int,          \
+                                           cudaStream_t);                                                        \
+  template cudaError_t launch_twiddle_matrix<T>(c2<T>*, int, int, int, cudaStream_t);                             \
   template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
-                                           int, int64_t, int, int, int, c2<T>*, cudaStream_t);                   \
+                                           int, int64_t, int, const c2<T>*, int, c2<T>*, cudaStream_t);          \
   template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \
                                            const c2<T>*, const c2<T>*, int, const int*, int, int64_t, c2<T>*,      \
                                            cudaStream_t);                                                        \

@@ -414,13 +414,20 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
   PC = std::min<int64_t>(PC, P);
   if ((st = workspace(c, "pd_T1", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * N23), &p_T1)) != RPA_OK) return st;
   if ((st = workspace(c, "pd_T2", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * n2 * N3), &p_T2)) != RPA_OK) return st;
+  void *p_twA, *p_twB;
+  const size_t twA_n = (size_t)((n1 + 15) / 16) * N1 * 16, twB_n = (size_t)((n2 + 15) / 16) * N2 * 16;
+  if ((st = workspace(c, "twA", sizeof(c2<T>) * twA_n, &p_twA)) != RPA_OK) return st;
+  if ((st = workspace(c, "twB", sizeof(c2<T>) * twB_n, &p_twB)) != RPA_OK) return st;
   {
-    StageTimer tm(c, 1, 0);
+    StageTimer tm(c, 1, 2);
+    CUDA_OK(c, launch_twiddle_matrix<T>((c2<T>*)p_twA, N1, glo[0], n1, c->stream));
+    CUDA_OK(c, launch_twiddle_matrix<T>((c2<T>*)p_twB, N2, glo[1], n2, c->stream));
     for (int64_t p0 = 0; p0 < P; p0 += PC) {
       const int np = (int)std::min<int64_t>(PC, P - p0);
       CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, sk.L_d, skp.R_d, nR,
-                                     p0, np, glo[0], n1, (c2<T>*)p_T1, c->stream));
-      CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, glo[1], n2, c->stream));
+                                     p0, np, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
+      CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
+                                     c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
                                      1.0 / (double)Nr, Rp, Pm, KP, skp.R_d, nR, p0, (c2<T>*)p_N, c->stream));
       tm.add_launches(3);

@@ -47,12 +47,17 @@ cudaError_t launch_scatter_box(const double2* C, int nb, int npw, const int* pos
 template <typename T>
 cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
                              const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
-                             int g1lo, int n1, c2<T>* T1, cudaStream_t s);
+                             const c2<T>* tw, int n1, c2<T>* T1, cudaStream_t s);
+
+// Twiddle matrices tw[oc][j][o] = exp(-2 pi i (lo + 16 oc + o) j / N) for the
+// n pruned outputs of an N-point axis (16 outputs per chunk), FP64-accurate.
+template <typename T>
+cudaError_t launch_twiddle_matrix(c2<T>* tw, int N, int lo, int n, cudaStream_t s);
 
 // Pair densities, stage B: pruned DFT along the middle axis,
 //   T2[pl][o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i (g2lo+o2) j2 / N2).
 template <typename T>
-cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, int g2lo, int n2,
+cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
                              cudaStream_t s);
 
 // Pair densities, stage C: DFT along the fastest axis evaluated on the sphere
