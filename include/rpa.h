@@ -156,6 +156,26 @@ rpa_status rpa_energy(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
                       const double* wq, int32_t nw, const double* omega,
                       const double* W, double* Ec, double* terms);
 
+/* Gradient of E_c (the derivative of Eqs. 1-2 through Eq. 3/17, the PAW term of
+ * Eq. 6 and the pair densities of Eqs. 4/10), scaled by dEc.  Same q-points,
+ * weights and frequencies as rpa_energy; *Ec (nullable, host) receives E_c.
+ * Convention: g = 2 dE/d(conj z), so dE = Re sum conj(g) dz (PyTorch's complex
+ * gradient).  For each s < nsets, set_ids[s] names an orbital set and
+ *   dC[s] [nbands][npw] complex  receives dE/dC (nullable array or entry),
+ *   dP[s] [nbands][sum nproj]    receives dE/dP (nullable; sets without PAW skipped),
+ * and dchi[i] (nullable) [nw][NG][NG] complex receives dE/dchi0(q_i, i w_j) =
+ * dEc w_q W_j / (2 pi) v^1/2 [1 - (1 - M)^-1] v^1/2.  Band energies and
+ * occupations are held fixed.  The pair densities of each (k, k+q) block are
+ * recomputed, not stored.  Outputs may be host or device memory.  The
+ * (1 - M)^-1 step runs in FP64 on the device (blocked substitution with the
+ * Cholesky factor). */
+rpa_status rpa_energy_backward(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
+                               const double* wq, int32_t nw, const double* omega,
+                               const double* W, double dEc, double* Ec,
+                               int32_t nsets, const int32_t* set_ids,
+                               double* const* dC, double* const* dP,
+                               double* const* dchi);
+
 /* Per-stage device timings of the most recent rpa_chi0/rpa_energy call,
  * measured with CUDA events on the context's stream when enabled by
  * rpa_set_profiling(ctx, 1).  Index: 0 wavefunctions to grid, 1 pair

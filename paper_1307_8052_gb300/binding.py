@@ -43,6 +43,7 @@ SIGNATURES = {
     "rpa_get_profile": (_I, [_P, _P, _P]),
     "rpa_set_tuning": (_I, [_P, _I, ct.c_int64]),
     "rpa_logdet_noalloc": (_I, [_P, _P, _I, _I, _P, _P]),
+    "rpa_energy_backward": (_I, [_P, _I, _P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
 }
 RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID = 0, 1, 2, 3
 
@@ -200,6 +201,32 @@ def rpa_energy(ctx, iqs, wq, omega, W):
                           terms.ctypes.data_as(_P))
     _check(ctx, st)
     return E.value, terms
+
+
+def rpa_energy_backward(ctx, iqs, wq, omega, W, dEc=1.0, sets=(), dC=None, dP=None, dchi=None):
+    """Gradient of E_c.  ``sets`` lists orbital-set indices; ``dC[s]`` / ``dP[s]``
+    are output buffers (numpy arrays or CUDA tensors, complex128, shaped like the
+    set's C / P; entries may be None) and ``dchi[i]`` ([nw][NG][NG] complex128)
+    per q-point.  Returns E_c."""
+    keep = []
+    iqs = np.ascontiguousarray(iqs, dtype=np.int32)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    sets = np.ascontiguousarray(sets, dtype=np.int32)
+
+    def ptr_array(bufs, n):
+        if bufs is None:
+            return None
+        arr = (ct.c_void_p * n)(*[(_ptr(x, None, keep).value if x is not None else None) for x in bufs])
+        keep.append(arr)
+        return ct.cast(arr, ct.c_void_p)
+
+    E = ct.c_double()
+    st = lib().rpa_energy_backward(ctx, len(iqs), _ptr(iqs, np.int32, keep), _ptr(wq, np.float64, keep), len(omega),
+                                   _ptr(omega, np.float64, keep), _ptr(W, np.float64, keep), float(dEc),
+                                   ct.byref(E), len(sets), _ptr(sets, np.int32, keep) if len(sets) else None,
+                                   ptr_array(dC, len(sets)), ptr_array(dP, len(sets)), ptr_array(dchi, len(iqs)))
+    _check(ctx, st)
+    return E.value
 
 
 def rpa_set_profiling(ctx, enable=True):

@@ -1,0 +1,608 @@
+// Adjoint (reverse mode) of the chi0 / E_c path, for dE_c/dchi0 and the
+// gradients with respect to the plane-wave coefficients C and projections P.
+// Gradients follow the PyTorch complex convention g = 2 dE/d(conj z), so that
+// dE = Re sum conj(g) dz.
+//
+//  * dE/dchi(q, w_j) = (w_q W_j / 2 pi) v^1/2 [1 - (1 - M_j)^-1] v^1/2
+//    (derivative of Eqs. 1-2); (1 - M)^-1 = L^-H L^-1 from the FP64 Cholesky
+//    factor by a blocked forward substitution and a Gram product.
+//  * nbar_p = 2 sum_j w_p(w_j) Gamma_j n_p (adjoint of the rank-k update, Eq. 17).
+//  * PAW (Eq. 6): gP_n += sum_m sum_G conj(nbar_nm) sum_j P_mj Q_ij, and
+//    gP_m += sum_n sum_G nbar_nm conj(R_n(j,G)) with R_n(j,G) = sum_i conj(P_ni) Q_ij(G).
+//  * Pair densities (Eq. 10): xbar(r) = (1/N_r) sum_G nbar(G) exp(+i (G+G0).r)
+//    by the transposed pruned transforms, ubar_m += xbar u_n,
+//    ubar_n += conj(xbar) u_m, and gC(Q) = sum_r exp(-i Q.r) ubar(r).
+#include "rpa_internal.h"
+
+namespace rpa {
+
+static inline int gridx(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
+}
+
+__host__ __device__ inline int pmod_a(int64_t a, int n) {
+  int64_t r = a % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+// ---------------------------------------------------------------- complex FP64 GEMM
+// C[z] = beta C[z] + alpha opA(A[z]) B[z]; opA = 0: A is M x K (row-major, lda),
+// opA = 1: A is stored K x M and used conjugate-transposed.
+constexpr int ZT = 64, ZK = 16;
+
+__global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2 alpha, const double2* __restrict__ A,
+                                                    int64_t lda, int64_t sA, int opA, const double2* __restrict__ B,
+                                                    int64_t ldb, int64_t sB, double2 beta, double2* __restrict__ C,
+                                                    int64_t ldc, int64_t sC) {
+  __shared__ double2 As[ZK][ZT];
+  __shared__ double2 Bs[ZK][ZT];
+  const int z = blockIdx.z;
+  A += z * sA;
+  B += z * sB;
+  C += z * sC;
+  const int m0 = blockIdx.y * ZT, n0 = blockIdx.x * ZT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += ZK) {
+#pragma unroll
+    for (int q = 0; q < (ZK * ZT) / 256; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      // A tile: element (row m0+r, k k0+kk)
+      {
+        const int r = e / ZK, kk = e % ZK;
+        double2 v = make_double2(0.0, 0.0);
+        if (m0 + r < M && k0 + kk < K) {
+          if (opA == 0) {
+            v = A[(int64_t)(m0 + r) * lda + k0 + kk];
+          } else {
+            const double2 t = A[(int64_t)(k0 + kk) * lda + m0 + r];
+            v = make_double2(t.x, -t.y);
+          }
+        }
+        As[kk][r] = v;
+      }
+      {
+        const int kk = e / ZT, c = e % ZT;
+        Bs[kk][c] = (k0 + kk < K && n0 + c < N) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ZK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac<double>(acc[r][c], a[r], b[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int m = m0 + ty + 16 * r, n = n0 + tx + 16 * c;
+      if (m < M && n < N) {
+        double2* p = C + (int64_t)m * ldc + n;
+        const double2 old = (beta.x == 0.0 && beta.y == 0.0) ? make_double2(0.0, 0.0) : *p;
+        const double2 a = acc[r][c];
+        double2 v;
+        v.x = beta.x * old.x - beta.y * old.y + alpha.x * a.x - alpha.y * a.y;
+        v.y = beta.x * old.y + beta.y * old.x + alpha.x * a.y + alpha.y * a.x;
+        *p = v;
+      }
+    }
+}
+
+cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2* A, int64_t lda, int64_t sA, int opA,
+                         const double2* B, int64_t ldb, int64_t sB, double2 beta, double2* C, int64_t ldc,
+                         int64_t sC, int batch, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT, batch);
+  zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, opA, B, ldb, sB, beta, C, ldc, sC);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- (1 - M)^-1 from the Cholesky factor
+constexpr int FB = 32;
+
+__global__ void set_identity_kernel(double2* __restrict__ Y, int n, int nw) {
+  const int64_t total = (int64_t)nw * n * n;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % n);
+    const int i = (int)((id / n) % n);
+    Y[id] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// Y[i0 .. i0+b) <- L_ii^-1 Y[i0 .. i0+b), one column of Y per thread.
+__global__ void __launch_bounds__(256) fwd_sub_diag_kernel(const double2* __restrict__ L, double2* __restrict__ Y,
+                                                           int n, int i0, int b) {
+  __shared__ double2 Ld[FB][FB + 1];
+  const int w = blockIdx.y;
+  const double2* Lw = L + (int64_t)w * n * n;
+  double2* Yw = Y + (int64_t)w * n * n;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int r = e / b, l = e % b;
+    Ld[r][l] = (l <= r) ? Lw[(int64_t)(i0 + r) * n + i0 + l] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double2 y[FB];
+#pragma unroll
+  for (int r = 0; r < FB; ++r) y[r] = (r < b) ? Yw[(int64_t)(i0 + r) * n + c] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int r = 0; r < FB; ++r) {
+    if (r < b) {
+      double2 s = y[r];
+#pragma unroll
+      for (int l = 0; l < FB; ++l) {
+        if (l < r) {
+          const double2 a = Ld[r][l], x = y[l];
+          s.x -= a.x * x.x - a.y * x.y;
+          s.y -= a.x * x.y + a.y * x.x;
+        }
+      }
+      const double d = 1.0 / Ld[r][r].x;
+      y[r] = make_double2(s.x * d, s.y * d);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < FB; ++r)
+    if (r < b) Yw[(int64_t)(i0 + r) * n + c] = y[r];
+}
+
+// Gamma = c_w v^1/2 (I - W) v^1/2 (W = (1-M)^-1), stored as FP64 and optionally FP32.
+__global__ void gamma_kernel(const double2* __restrict__ Wm, const double* __restrict__ v, const double* __restrict__ cw,
+                             int n, int nw, double2* __restrict__ G64, float2* __restrict__ G32) {
+  const int64_t total = (int64_t)nw * n * n;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % n);
+    const int64_t r = id / n;
+    const int i = (int)(r % n);
+    const int w = (int)(r / n);
+    const double s = cw[w] * sqrt(v[i]) * sqrt(v[j]);
+    const double2 x = Wm[id];
+    // Hermitian part of (I - W); W is Hermitian up to rounding
+    const double2 xt = Wm[((int64_t)w * n + j) * n + i];
+    double re = -(0.5 * (x.x + xt.x)), im = -(0.5 * (x.y - xt.y));
+    if (i == j) {
+      re += 1.0;
+      im = 0.0;
+    }
+    const double2 g = make_double2(s * re, s * im);
+    if (G64) G64[id] = g;
+    if (G32) G32[id] = make_float2((float)g.x, (float)g.y);
+  }
+}
+
+cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
+                      double2* G64, float2* G32, cudaStream_t s, int64_t* launches) {
+  cudaError_t e;
+  int64_t nl = 0;
+  set_identity_kernel<<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Y, n, nw);
+  ++nl;
+  for (int i0 = 0; i0 < n; i0 += FB) {
+    const int b = (n - i0) < FB ? (n - i0) : FB;
+    if (i0 > 0) {
+      // Y[i0:i0+b, :] -= L[i0:i0+b, 0:i0] Y[0:i0, :]
+      if ((e = launch_zgemm(b, n, i0, make_double2(-1.0, 0.0), L + (int64_t)i0 * n, n, (int64_t)n * n, 0, Y, n,
+                            (int64_t)n * n, make_double2(1.0, 0.0), Y + (int64_t)i0 * n, n, (int64_t)n * n, nw, s)) !=
+          cudaSuccess)
+        return e;
+      ++nl;
+    }
+    fwd_sub_diag_kernel<<<dim3((n + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
+    ++nl;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // W = Y^H Y = L^-H L^-1 = (1 - M)^-1
+  if ((e = launch_zgemm(n, n, n, make_double2(1.0, 0.0), Y, n, (int64_t)n * n, 1, Y, n, (int64_t)n * n,
+                        make_double2(0.0, 0.0), Wm, n, (int64_t)n * n, nw, s)) != cudaSuccess)
+    return e;
+  gamma_kernel<<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Wm, v, cw, n, nw, G64, G32);
+  nl += 2;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- nbar = 2 sum_w w_p(w) Gamma_w n_p
+// Nbar[p][G] = 2 sum_w wgt[w][p] sum_G' Gamma_w[G][G'] N[p][G'] = 2 sum_(w,G') A[p][(w,G')] conj(Gamma_w[G'][G]).
+template <typename T>
+__global__ void __launch_bounds__(256) nbar_kernel(const c2<T>* __restrict__ N, int64_t P, int NG,
+                                                   const T* __restrict__ wgt, const c2<T>* __restrict__ Gam, int nw,
+                                                   c2<T>* __restrict__ Nbar) {
+  __shared__ c2<T> As[ZK][ZT];
+  __shared__ c2<T> Bs[ZK][ZT];
+  const int64_t p0 = (int64_t)blockIdx.y * ZT;
+  const int g0 = blockIdx.x * ZT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  c2<T> acc[4][4];
+  double hi[4][4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      acc[r][c] = mk<T>(0, 0);
+      hi[r][c][0] = hi[r][c][1] = 0.0;
+    }
+  for (int w = 0; w < nw; ++w) {
+    const c2<T>* Gw = Gam + (int64_t)w * NG * NG;
+    const T* ww = wgt + (int64_t)w * P;
+    for (int k0 = 0; k0 < NG; k0 += ZK) {
+#pragma unroll
+      for (int q = 0; q < (ZK * ZT) / 256; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        {
+          const int r = e / ZK, kk = e % ZK;
+          const int64_t p = p0 + r;
+          c2<T> a = mk<T>(0, 0);
+          if (p < P && k0 + kk < NG) {
+            a = N[p * NG + k0 + kk];
+            const T s = ww[p];
+            a.x *= s;
+            a.y *= s;
+          }
+          As[kk][r] = a;
+        }
+        {
+          const int kk = e / ZT, c = e % ZT;
+          c2<T> b = mk<T>(0, 0);
+          if (k0 + kk < NG && g0 + c < NG) {
+            b = Gw[(int64_t)(k0 + kk) * NG + g0 + c];
+            b.y = -b.y;
+          }
+          Bs[kk][c] = b;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < ZK; ++kk) {
+        c2<T> a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cmac<T>(acc[r][c], a[r], b[c]);
+      }
+      __syncthreads();
+    }
+    // fold each frequency's partial into FP64 so FP32 rounding does not grow with nw
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        hi[r][c][0] += (double)acc[r][c].x;
+        hi[r][c][1] += (double)acc[r][c].y;
+        acc[r][c] = mk<T>(0, 0);
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t p = p0 + ty + 16 * r;
+      const int g = g0 + tx + 16 * c;
+      if (p < P && g < NG) Nbar[p * NG + g] = mk<T>((T)(2.0 * hi[r][c][0]), (T)(2.0 * hi[r][c][1]));
+    }
+}
+
+template <typename T>
+cudaError_t launch_nbar(const c2<T>* N, int64_t P, int NG, const T* wgt, const c2<T>* Gam, int nw, c2<T>* Nbar,
+                        cudaStream_t s) {
+  if (P == 0) return cudaSuccess;
+  dim3 grid((NG + ZT - 1) / ZT, (unsigned)((P + ZT - 1) / ZT));
+  nbar_kernel<T><<<grid, 256, 0, s>>>(N, P, NG, wgt, Gam, nw, Nbar);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- PAW adjoint
+// Y[aL][kp][G] = sum_b conj(Nbar[(aL, b)][G]) Pm[b][kp]
+template <typename T>
+__global__ void paw_adj_y_kernel(const c2<T>* __restrict__ Nbar, int nL, int nR, int NG, const c2<T>* __restrict__ Pm,
+                                 int KP, c2<T>* __restrict__ Y) {
+  const int64_t total = (int64_t)nL * KP * NG;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int ig = (int)(id % NG);
+    const int64_t r = id / NG;
+    const int kp = (int)(r % KP);
+    const int a = (int)(r / KP);
+    c2<T> acc = mk<T>(0, 0);
+    const c2<T>* nb = Nbar + (int64_t)a * nR * NG + ig;
+    for (int b = 0; b < nR; ++b) cmac<T>(acc, mk<T>(nb[(int64_t)b * NG].x, -nb[(int64_t)b * NG].y), Pm[(int64_t)b * KP + kp]);
+    Y[id] = acc;
+  }
+}
+
+// gPk[Lidx[aL]][kp_i] += sum_j sum_G Q^a_ij(G) Y[aL][(a,j)][G]   (one block per (aL, kp_i))
+template <typename T>
+__global__ void __launch_bounds__(256) paw_adj_pk_kernel(const c2<T>* __restrict__ Y, int NG, int KP,
+                                                         const double2* __restrict__ Q, const int* __restrict__ atom_of_kp,
+                                                         const int* __restrict__ idx_in_atom,
+                                                         const int* __restrict__ atom_off,
+                                                         const int64_t* __restrict__ q_off,
+                                                         const int* __restrict__ nproj, const int* __restrict__ Lidx,
+                                                         double2* __restrict__ gP) {
+  __shared__ double red[2][256];
+  const int kpi = blockIdx.x % KP;
+  const int aL = blockIdx.x / KP;
+  const int atom = atom_of_kp[kpi];
+  const int i = idx_in_atom[kpi];
+  const int ni = nproj[atom];
+  double sx = 0.0, sy = 0.0;
+  for (int j = 0; j < ni; ++j) {
+    const c2<T>* y = Y + ((int64_t)aL * KP + atom_off[atom] + j) * NG;
+    const double2* qij = Q + q_off[atom] + ((int64_t)i * ni + j) * NG;
+    for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+      const double2 q = qij[g];
+      const c2<T> yy = y[g];
+      sx += q.x * (double)yy.x - q.y * (double)yy.y;
+      sy += q.x * (double)yy.y + q.y * (double)yy.x;
+    }
+  }
+  red[0][threadIdx.x] = sx;
+  red[1][threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double2* dst = gP + (int64_t)Lidx[aL] * KP + kpi;
+    dst->x += red[0][0];
+    dst->y += red[1][0];
+  }
+}
+
+// gPkp[Ridx[b]][kp] += sum_aL sum_G Nbar[(aL, b)][G] conj(R[aL][kp][G])   (one block per (b, kp))
+template <typename T>
+__global__ void __launch_bounds__(256) paw_adj_pkp_kernel(const c2<T>* __restrict__ Nbar, const c2<T>* __restrict__ R,
+                                                          int nL, int nR, int NG, int KP, const int* __restrict__ Ridx,
+                                                          double2* __restrict__ gP) {
+  __shared__ double red[2][256];
+  const int kp = blockIdx.x % KP;
+  const int b = blockIdx.x / KP;
+  double sx = 0.0, sy = 0.0;
+  for (int aL = 0; aL < nL; ++aL) {
+    const c2<T>* nb = Nbar + ((int64_t)aL * nR + b) * NG;
+    const c2<T>* rr = R + ((int64_t)aL * KP + kp) * NG;
+    for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+      const c2<T> x = nb[g], y = rr[g];
+      sx += (double)x.x * y.x + (double)x.y * y.y;
+      sy += (double)x.y * y.x - (double)x.x * y.y;
+    }
+  }
+  red[0][threadIdx.x] = sx;
+  red[1][threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double2* dst = gP + (int64_t)Ridx[b] * KP + kp;
+    dst->x += red[0][0];
+    dst->y += red[1][0];
+  }
+}
+
+template <typename T>
+cudaError_t launch_paw_adjoint(const c2<T>* Nbar, const c2<T>* R, const c2<T>* Pm, int nL, int nR, int NG, int KP,
+                               const double2* Q, const int* atom_of_kp, const int* idx_in_atom, const int* atom_off,
+                               const int64_t* q_off, const int* nproj, const int* Lidx, const int* Ridx, c2<T>* Ywork,
+                               double2* gPk, double2* gPkp, cudaStream_t s) {
+  if ((int64_t)nL * nR * KP == 0) return cudaSuccess;
+  paw_adj_y_kernel<T><<<gridx((int64_t)nL * KP * NG), 256, 0, s>>>(Nbar, nL, nR, NG, Pm, KP, Ywork);
+  paw_adj_pk_kernel<T><<<nL * KP, 256, 0, s>>>(Ywork, NG, KP, Q, atom_of_kp, idx_in_atom, atom_off, q_off, nproj,
+                                                Lidx, gPk);
+  paw_adj_pkp_kernel<T><<<nR * KP, 256, 0, s>>>(Nbar, R, nL, nR, NG, KP, Ridx, gPkp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pair-density adjoint
+// Stage C^T: T2bar[pl][o1][o2][j3] = (1/N_r) sum_{G in column (o1,o2)} Nbar[p][G] exp(+2 pi i g3 j3 / N3).
+// Column lists: col_start[n1*n2+1], col_g[k] = sphere index, col_g3[k] = g3 of that point.
+template <typename T>
+__global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict__ Nbar, int NG, int64_t p0, int np,
+                                                         int ncol, int N3, const int* __restrict__ col_start,
+                                                         const int* __restrict__ col_g, const int* __restrict__ col_g3,
+                                                         double inv_nr, c2<T>* __restrict__ T2) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  for (int t = threadIdx.x; t < N3; t += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)N3, &s, &c);
+    tw[t] = mk<T>((T)c, (T)s);
+  }
+  __syncthreads();
+  const int64_t total = (int64_t)np * ncol * N3;
+  const T scale = (T)inv_nr;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j3 = (int)(id % N3);
+    const int64_t r = id / N3;
+    const int col = (int)(r % ncol);
+    const int pl = (int)(r / ncol);
+    const c2<T>* nb = Nbar + (p0 + pl) * NG;
+    c2<T> acc = mk<T>(0, 0);
+    for (int k = col_start[col]; k < col_start[col + 1]; ++k) {
+      const int t = pmod_a((int64_t)col_g3[k] * j3, N3);
+      cmac<T>(acc, nb[col_g[k]], tw[t]);
+    }
+    acc.x *= scale;
+    acc.y *= scale;
+    T2[id] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int ncol, int N3, const int* col_start,
+                              const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2, cudaStream_t s) {
+  const int64_t total = (int64_t)np * ncol * N3;
+  if (total == 0) return cudaSuccess;
+  adj_stageC_kernel<T><<<gridx(total), 256, N3 * sizeof(c2<T>), s>>>(Nbar, NG, p0, np, ncol, N3, col_start, col_g,
+                                                                     col_g3, inv_nr, T2);
+  return cudaGetLastError();
+}
+
+// Stage A^T with the products: for the chunk's pairs (all with the same occupied
+// band n), xbar[pl][j1][j23] = sum_o1 T1bar[pl][o1][j23] exp(+2 pi i g1 j1 / N1);
+// ubar_m[j] += xbar u_n[j] (distinct m per pair: no race) and xbar is kept for
+// the ubar_n reduction.  The twiddle table is tw[o1][j1] (FP64-accurate).
+template <typename T>
+__global__ void __launch_bounds__(256) adj_stageA_kernel(const c2<T>* __restrict__ T1, int np, int n1, int N1, int N23,
+                                                         const c2<T>* __restrict__ tw, const c2<T>* __restrict__ Un,
+                                                         const c2<T>* __restrict__ Ukp, const int* __restrict__ Ridx,
+                                                         int nR, int64_t p0, c2<T>* __restrict__ Ubar_kp,
+                                                         c2<T>* __restrict__ Xbar) {
+  const int64_t Nr = (int64_t)N1 * N23;
+  const int64_t total = (int64_t)np * N23;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j23 = (int)(id % N23);
+    const int pl = (int)(id / N23);
+    const int m = Ridx[(p0 + pl) % nR];
+    const c2<T>* src = T1 + (int64_t)pl * n1 * N23 + j23;
+    for (int j1 = 0; j1 < N1; ++j1) {
+      c2<T> x = mk<T>(0, 0);
+      for (int o = 0; o < n1; ++o) cmac<T>(x, src[(int64_t)o * N23], tw[o * N1 + j1]);
+      const int64_t jj = (int64_t)j1 * N23 + j23;
+      Xbar[(int64_t)pl * Nr + jj] = x;
+      c2<T>* ub = Ubar_kp + (int64_t)m * Nr + jj;
+      c2<T> v = *ub;
+      cmac<T>(v, x, Un[jj]);
+      *ub = v;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_adj_stageA(const c2<T>* T1, int np, int n1, int N1, int N23, const c2<T>* tw, const c2<T>* Un,
+                              const c2<T>* Ukp, const int* Ridx, int nR, int64_t p0, c2<T>* Ubar_kp, c2<T>* Xbar,
+                              cudaStream_t s) {
+  const int64_t total = (int64_t)np * N23;
+  if (total == 0) return cudaSuccess;
+  adj_stageA_kernel<T><<<gridx(total), 256, 0, s>>>(T1, np, n1, N1, N23, tw, Un, Ukp, Ridx, nR, p0, Ubar_kp, Xbar);
+  return cudaGetLastError();
+}
+
+// ubar_n[j] += sum_pl conj(xbar[pl][j]) u_m(pl)[j]   (thread per grid point)
+template <typename T>
+__global__ void adj_un_kernel(const c2<T>* __restrict__ Xbar, int np, int64_t Nr, const c2<T>* __restrict__ Ukp,
+                              const int* __restrict__ Ridx, int nR, int64_t p0, c2<T>* __restrict__ Ubar_n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Nr; j += (int64_t)gridDim.x * blockDim.x) {
+    c2<T> acc = Ubar_n[j];
+    for (int pl = 0; pl < np; ++pl) {
+      const c2<T> x = Xbar[(int64_t)pl * Nr + j];
+      const c2<T> u = Ukp[(int64_t)Ridx[(p0 + pl) % nR] * Nr + j];
+      // conj(x) * u
+      acc.x += x.x * u.x + x.y * u.y;
+      acc.y += x.x * u.y - x.y * u.x;
+    }
+    Ubar_n[j] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t launch_adj_un(const c2<T>* Xbar, int np, int64_t Nr, const c2<T>* Ukp, const int* Ridx, int nR, int64_t p0,
+                          c2<T>* Ubar_n, cudaStream_t s) {
+  if (Nr == 0 || np == 0) return cudaSuccess;
+  adj_un_kernel<T><<<gridx(Nr), 256, 0, s>>>(Xbar, np, Nr, Ukp, Ridx, nR, p0, Ubar_n);
+  return cudaGetLastError();
+}
+
+// Twiddles of the transposed transforms: tw[jc][o][jj] = exp(+2 pi i (lo + o)(16 jc + jj) / N)
+// (layout of the stage-B kernel with input axis o and 16 outputs j per chunk), and
+// the plain matrix tw[o][j] used by stage A^T.
+template <typename T>
+__global__ void twiddle_adj_kernel(c2<T>* __restrict__ tw, int N, int lo, int nin, int chunked) {
+  const int nch = (N + 15) / 16;
+  const int64_t total = chunked ? (int64_t)nch * nin * 16 : (int64_t)nin * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int o, j;
+    if (chunked) {
+      const int jc = (int)(e / ((int64_t)nin * 16));
+      const int r = (int)(e % ((int64_t)nin * 16));
+      o = r / 16;
+      j = jc * 16 + r % 16;
+    } else {
+      o = (int)(e / N);
+      j = (int)(e % N);
+    }
+    if (j < N) {
+      const int t = pmod_a((int64_t)(lo + o) * j, N);
+      double s, c;
+      sincospi(2.0 * (double)t / (double)N, &s, &c);
+      tw[e] = mk<T>((T)c, (T)s);
+    } else {
+      tw[e] = mk<T>(0, 0);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_twiddle_adj(c2<T>* tw, int N, int lo, int nin, int chunked, cudaStream_t s) {
+  const int64_t total = chunked ? (int64_t)((N + 15) / 16) * nin * 16 : (int64_t)nin * N;
+  twiddle_adj_kernel<T><<<gridx(total), 256, 0, s>>>(tw, N, lo, nin, chunked);
+  return cudaGetLastError();
+}
+
+// Gather a Miller box back onto the plane-wave list and accumulate in FP64:
+// dC[b][q] += box[b][pos[q]].
+template <typename T>
+__global__ void gather_box_kernel(const c2<T>* __restrict__ box, int nb, int npw, const int* __restrict__ pos,
+                                  int64_t boxsz, double2* __restrict__ dC) {
+  const int64_t total = (int64_t)nb * npw;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(id / npw), q = (int)(id % npw);
+    const c2<T> v = box[(int64_t)b * boxsz + pos[q]];
+    dC[id].x += (double)v.x;
+    dC[id].y += (double)v.y;
+  }
+}
+
+template <typename T>
+cudaError_t launch_gather_box(const c2<T>* box, int nb, int npw, const int* pos, int64_t boxsz, double2* dC,
+                              cudaStream_t s) {
+  const int64_t total = (int64_t)nb * npw;
+  if (total == 0) return cudaSuccess;
+  gather_box_kernel<T><<<gridx(total), 256, 0, s>>>(box, nb, npw, pos, boxsz, dC);
+  return cudaGetLastError();
+}
+
+#define RPA_ADJ_INST(T)                                                                                                \
+  template cudaError_t launch_nbar<T>(const c2<T>*, int64_t, int, const T*, const c2<T>*, int, c2<T>*, cudaStream_t);  \
+  template cudaError_t launch_paw_adjoint<T>(const c2<T>*, const c2<T>*, const c2<T>*, int, int, int, int,             \
+                                             const double2*, const int*, const int*, const int*, const int64_t*,       \
+                                             const int*, const int*, const int*, c2<T>*, double2*, double2*,           \
+                                             cudaStream_t);                                                            \
+  template cudaError_t launch_adj_stageC<T>(const c2<T>*, int, int64_t, int, int, int, const int*, const int*,         \
+                                            const int*, double, c2<T>*, cudaStream_t);                                 \
+  template cudaError_t launch_adj_stageA<T>(const c2<T>*, int, int, int, int, const c2<T>*, const c2<T>*,              \
+                                            const c2<T>*, const int*, int, int64_t, c2<T>*, c2<T>*, cudaStream_t);     \
+  template cudaError_t launch_adj_un<T>(const c2<T>*, int, int64_t, const c2<T>*, const int*, int, int64_t, c2<T>*,    \
+                                        cudaStream_t);                                                                 \
+  template cudaError_t launch_twiddle_adj<T>(c2<T>*, int, int, int, int, cudaStream_t);                                \
+  template cudaError_t launch_gather_box<T>(const c2<T>*, int, int, const int*, int64_t, double2*, cudaStream_t);
+
+RPA_ADJ_INST(float)
+RPA_ADJ_INST(double)
+
+}  // namespace rpa

@@ -21,6 +21,32 @@ cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt,
                            int fold_stages, int flush_folds, double2* chi, void* scratch, size_t scratch_bytes,
                            int* err, cudaStream_t s);
 size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
+// adjoint kernels (k_adjoint.cu)
+cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
+                      double2* G64, float2* G32, cudaStream_t s, int64_t* launches);
+template <typename T>
+cudaError_t launch_nbar(const c2<T>* N, int64_t P, int NG, const T* wgt, const c2<T>* Gam, int nw, c2<T>* Nbar,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_paw_adjoint(const c2<T>* Nbar, const c2<T>* R, const c2<T>* Pm, int nL, int nR, int NG, int KP,
+                               const double2* Q, const int* atom_of_kp, const int* idx_in_atom, const int* atom_off,
+                               const int64_t* q_off, const int* nproj, const int* Lidx, const int* Ridx, c2<T>* Ywork,
+                               double2* gPk, double2* gPkp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int ncol, int N3, const int* col_start,
+                              const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_stageA(const c2<T>* T1, int np, int n1, int N1, int N23, const c2<T>* tw, const c2<T>* Un,
+                              const c2<T>* Ukp, const int* Ridx, int nR, int64_t p0, c2<T>* Ubar_kp, c2<T>* Xbar,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_un(const c2<T>* Xbar, int np, int64_t Nr, const c2<T>* Ukp, const int* Ridx, int nR, int64_t p0,
+                          c2<T>* Ubar_n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_twiddle_adj(c2<T>* tw, int N, int lo, int nin, int chunked, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_box(const c2<T>* box, int nb, int npw, const int* pos, int64_t boxsz, double2* dC,
+                              cudaStream_t s);
 }
 
 using namespace rpa;
@@ -316,19 +342,53 @@ void choose_transform_grid(rpa_ctx* c, const int* iqs, int nq) {
 }
 
 // ---- stages a2-a4 for one q-point: chi accumulates in FP64 lower triangle
+// Everything one (k, k+q) block leaves on the device after its pair densities.
 template <typename T>
-rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, double2* chi) {
+struct Block {
+  OrbSet* sk = nullptr;
+  OrbSet* skp = nullptr;
+  int nL = 0, nR = 0, NG = 0, N1 = 0, N2 = 0, N3 = 0, n1 = 0, n2 = 0, KP = 0;
+  int64_t P = 0, Nr = 0, PC = 0;
+  int glo[3] = {0, 0, 0};
+  std::vector<int> gfft;
+  T* w = nullptr;                    // [nw][P] pair weights
+  c2<T>* N = nullptr;                // [P][NG] pair densities
+  c2<T>* R = nullptr;                // [nL][KP][NG] PAW factors
+  c2<T>* Pm = nullptr;               // [nR][KP]
+  c2<T>* T1 = nullptr;               // transform scratch
+  c2<T>* T2 = nullptr;
+  const int64_t* q_off = nullptr;    // PAW metadata (device)
+  const int* atom_of = nullptr;
+  const int* idx_in = nullptr;
+  const int* atom_off = nullptr;
+  const int* nproj = nullptr;
+};
+
+// stages a2-a3 (pair densities + PAW) and the pair weights of one transition
+template <typename T>
+rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, Block<T>& B) {
   OrbSet& sk = c->sets[Q.k_of[t]];
   OrbSet& skp = c->sets[Q.kq_of[t]];
+  B.sk = &sk;
+  B.skp = &skp;
   const int nL = (int)sk.L.size(), nR = (int)skp.R.size();
   const int64_t P = (int64_t)nL * nR;
+  B.nL = nL;
+  B.nR = nR;
+  B.P = P;
   if (P == 0) return RPA_OK;
   const int N1 = c->tg[0], N2 = c->tg[1], N3 = c->tg[2];
   const int64_t Nr = (int64_t)N1 * N2 * N3;
   const int NG = Q.NG;
+  B.N1 = N1;
+  B.N2 = N2;
+  B.N3 = N3;
+  B.Nr = Nr;
+  B.NG = NG;
   const int* G0 = &Q.G0[3 * t];
   // target Fourier indices g = G + G0 and their box
-  std::vector<int> gfft(3 * (size_t)NG);
+  std::vector<int>& gfft = B.gfft;
+  gfft.assign(3 * (size_t)NG, 0);
   int glo[3] = {1 << 30, 1 << 30, 1 << 30}, ghi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
   for (int i = 0; i < NG; ++i)
     for (int d = 0; d < 3; ++d) {
@@ -338,6 +398,9 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
       ghi[d] = std::max(ghi[d], g);
     }
   const int n1 = ghi[0] - glo[0] + 1, n2 = ghi[1] - glo[1] + 1;
+  B.n1 = n1;
+  B.n2 = n2;
+  for (int d = 0; d < 3; ++d) B.glo[d] = glo[d];
   void *p_gfft, *p_d, *p_df, *p_w, *p_N, *p_T1, *p_T2;
   rpa_status st;
   if ((st = workspace(c, "gfft", sizeof(int) * gfft.size(), &p_gfft)) != RPA_OK) return st;
@@ -396,6 +459,11 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
     const int* idx_in_d = atom_of_d + KP;
     const int* atom_off_d = idx_in_d + KP;
     const int* nproj_d = atom_off_d + Q.natoms;
+    B.q_off = q_off_d;
+    B.atom_of = atom_of_d;
+    B.idx_in = idx_in_d;
+    B.atom_off = atom_off_d;
+    B.nproj = nproj_d;
     if ((st = workspace(c, "paw_R", sizeof(c2<T>) * (size_t)nL * KP * NG, &p_R)) != RPA_OK) return st;
     if ((st = workspace(c, "paw_Pm", sizeof(c2<T>) * (size_t)nR * KP, &p_Pm)) != RPA_OK) return st;
     Rp = (c2<T>*)p_R;
@@ -433,21 +501,35 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
       tm.add_launches(3);
     }
   }
-  // grouped rank-k update for every frequency
-  {
-    StageTimer tm(c, 2, 1);
-    const int prec = c->prm.precision;
-    if (prec == RPA_FP64 || prec == RPA_FP32) {
-      CUDA_OK(c, launch_herk_simt_w<T>((const c2<T>*)p_N, P, NG, (const T*)p_w, nw, chi, c->stream));
-    } else {
-      const int terms = prec == RPA_BF16X3 ? 3 : 2;
-      void* scr = nullptr;
-      const size_t sb = herk_tc_scratch_bytes(P, NG, nw, terms);
-      if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
-      CUDA_OK(c, launch_herk_tc((const float2*)p_N, P, NG, (const float*)p_w, nw, terms,
-                                (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH], chi, scr, sb,
-                                c->dev_err, c->stream));
-    }
+  B.w = (T*)p_w;
+  B.N = (c2<T>*)p_N;
+  B.R = Rp;
+  B.Pm = Pm;
+  B.KP = KP;
+  B.T1 = (c2<T>*)p_T1;
+  B.T2 = (c2<T>*)p_T2;
+  B.PC = PC;
+  return RPA_OK;
+}
+
+// stages a2-a4 for one transition: pair densities, then the grouped rank-k update
+template <typename T>
+rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, double2* chi) {
+  Block<T> B;
+  rpa_status st = pairs_block<T>(c, Q, t, omega_d, nw, B);
+  if (st != RPA_OK || B.P == 0) return st;
+  StageTimer tm(c, 2, 1);
+  const int prec = c->prm.precision;
+  if (prec == RPA_FP64 || prec == RPA_FP32) {
+    CUDA_OK(c, launch_herk_simt_w<T>(B.N, B.P, B.NG, B.w, nw, chi, c->stream));
+  } else {
+    const int terms = prec == RPA_BF16X3 ? 3 : 2;
+    void* scr = nullptr;
+    const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
+    if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
+    CUDA_OK(c, launch_herk_tc((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms,
+                              (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH], chi, scr, sb,
+                              c->dev_err, c->stream));
   }
   return RPA_OK;
 }
@@ -492,6 +574,238 @@ rpa_status build_chi(rpa_ctx* c, int iq, int nw, const double* omega_host, doubl
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   if (derr) return fail(c, RPA_ERR_TIMEOUT, "a bounded device wait gave up in the tensor-core update (code %d)", derr);
   *chi_out = (double2*)p_chi;
+  return RPA_OK;
+}
+
+// ---- adjoint of one transition: nbar (Eq. 17 adjoint), PAW adjoint (Eq. 6),
+// transposed pair-density transforms with the orbital products (Eq. 10)
+struct AdjState {
+  std::map<int, void*> ubar;      // per set: dE/du grids [nb][Nr] in working precision
+  std::map<int, double2*> gP;     // per set: dE/dP accumulators [nb][KP] (FP64)
+};
+
+template <typename T>
+rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, const c2<T>* Gam,
+                          AdjState& A) {
+  Block<T> B;
+  rpa_status st = pairs_block<T>(c, Q, t, omega_d, nw, B);
+  if (st != RPA_OK || B.P == 0) return st;
+  OrbSet& sk = *B.sk;
+  OrbSet& skp = *B.skp;
+  const int NG = B.NG, nL = B.nL, nR = B.nR, n1 = B.n1, n2 = B.n2;
+  const int N1 = B.N1, N2 = B.N2, N3 = B.N3;
+  const int64_t Nr = B.Nr, N23 = (int64_t)N2 * N3;
+  void *p_nbar, *p_y, *p_cols, *p_twa, *p_twb, *p_xbar;
+  if ((st = workspace(c, "Nbar", sizeof(c2<T>) * (size_t)B.P * NG, &p_nbar)) != RPA_OK) return st;
+  c2<T>* Nbar = (c2<T>*)p_nbar;
+  StageTimer tm(c, 4, 0);
+  CUDA_OK(c, launch_nbar<T>(B.N, B.P, NG, B.w, Gam, nw, Nbar, c->stream));
+  tm.add_launches(1);
+  if (B.KP > 0) {
+    if ((st = workspace(c, "paw_y", sizeof(c2<T>) * (size_t)nL * B.KP * NG, &p_y)) != RPA_OK) return st;
+    CUDA_OK(c, launch_paw_adjoint<T>(Nbar, B.R, B.Pm, nL, nR, NG, B.KP, Q.Q, B.atom_of, B.idx_in, B.atom_off,
+                                     B.q_off, B.nproj, sk.L_d, skp.R_d, (c2<T>*)p_y, A.gP[Q.k_of[t]],
+                                     A.gP[Q.kq_of[t]], c->stream));
+    tm.add_launches(3);
+  }
+  // sphere points grouped by (g1, g2) column for the transposed fastest-axis transform
+  const int ncol = n1 * n2;
+  std::vector<int> cstart(ncol + 1, 0), cg(NG), cg3(NG);
+  for (int i = 0; i < NG; ++i) ++cstart[1 + (B.gfft[3 * i] - B.glo[0]) * n2 + (B.gfft[3 * i + 1] - B.glo[1])];
+  for (int k = 0; k < ncol; ++k) cstart[k + 1] += cstart[k];
+  {
+    std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+    for (int i = 0; i < NG; ++i) {
+      const int col = (B.gfft[3 * i] - B.glo[0]) * n2 + (B.gfft[3 * i + 1] - B.glo[1]);
+      cg[fill[col]] = i;
+      cg3[fill[col]++] = B.gfft[3 * i + 2];
+    }
+  }
+  const size_t cbytes = sizeof(int) * (cstart.size() + 2 * (size_t)NG);
+  if ((st = workspace(c, "adj_cols", cbytes, &p_cols)) != RPA_OK) return st;
+  std::vector<int> cbuf(cstart);
+  cbuf.insert(cbuf.end(), cg.begin(), cg.end());
+  cbuf.insert(cbuf.end(), cg3.begin(), cg3.end());
+  CUDA_OK(c, cudaMemcpyAsync(p_cols, cbuf.data(), cbytes, cudaMemcpyHostToDevice, c->stream));
+  const int* col_start = (const int*)p_cols;
+  const int* col_g = col_start + ncol + 1;
+  const int* col_g3 = col_g + NG;
+  if ((st = workspace(c, "tw_adjB", sizeof(c2<T>) * (size_t)((N2 + 15) / 16) * n2 * 16, &p_twb)) != RPA_OK) return st;
+  if ((st = workspace(c, "tw_adjA", sizeof(c2<T>) * (size_t)n1 * N1, &p_twa)) != RPA_OK) return st;
+  CUDA_OK(c, launch_twiddle_adj<T>((c2<T>*)p_twb, N2, B.glo[1], n2, 1, c->stream));
+  CUDA_OK(c, launch_twiddle_adj<T>((c2<T>*)p_twa, N1, B.glo[0], n1, 0, c->stream));
+  // chunks never straddle an occupied band, so every chunk shares u_n
+  const int64_t PCb = std::max<int64_t>(1, std::min<int64_t>(B.PC, nR));
+  if ((st = workspace(c, "Xbar", sizeof(c2<T>) * (size_t)(PCb * Nr), &p_xbar)) != RPA_OK) return st;
+  c2<T>* ub_k = (c2<T>*)A.ubar[Q.k_of[t]];
+  c2<T>* ub_kp = (c2<T>*)A.ubar[Q.kq_of[t]];
+  for (int a = 0; a < nL; ++a) {
+    for (int m0 = 0; m0 < nR; m0 += (int)PCb) {
+      const int np = (int)std::min<int64_t>(PCb, nR - m0);
+      const int64_t p0 = (int64_t)a * nR + m0;
+      CUDA_OK(c, launch_adj_stageC<T>(Nbar, NG, p0, np, ncol, N3, col_start, col_g, col_g3, 1.0 / (double)Nr, B.T2,
+                                      c->stream));
+      CUDA_OK(c, launch_pd_stageB<T>(B.T2, B.T1, np, n1, n2, N3, (const c2<T>*)p_twb, N2, c->stream));
+      CUDA_OK(c, launch_adj_stageA<T>(B.T1, np, n1, N1, (int)N23, (const c2<T>*)p_twa,
+                                      (const c2<T>*)sk.U + (int64_t)sk.L[a] * Nr, (const c2<T>*)skp.U, skp.R_d, nR,
+                                      p0, ub_kp, (c2<T>*)p_xbar, c->stream));
+      CUDA_OK(c, launch_adj_un<T>((const c2<T>*)p_xbar, np, Nr, (const c2<T>*)skp.U, skp.R_d, nR, p0,
+                                  ub_k + (int64_t)sk.L[a] * Nr, c->stream));
+      tm.add_launches(4);
+    }
+  }
+  return RPA_OK;
+}
+
+// dE/dC of one set from its dE/du grids: the adjoint of Eq. 8 is the forward
+// pruned transform onto the set's Miller box, gathered at its plane waves.
+template <typename T>
+rpa_status ubar_to_dC(rpa_ctx* c, OrbSet& s, const c2<T>* ub, double2* dC) {
+  const int N1 = c->tg[0], N2 = c->tg[1], N3 = c->tg[2];
+  const int64_t Nr = (int64_t)N1 * N2 * N3, N23 = (int64_t)N2 * N3;
+  const int L1 = s.mhi[0] - s.mlo[0] + 1, L2 = s.mhi[1] - s.mlo[1] + 1, L3 = s.mhi[2] - s.mlo[2] + 1;
+  const int64_t box = (int64_t)L1 * L2 * L3;
+  const int64_t per_band = (int64_t)L1 * N23 + (int64_t)L1 * L2 * N3 + box;
+  const int64_t nbat = std::max<int64_t>(1, std::min<int64_t>(s.nb, (int64_t)(256ll << 20) / (per_band * (int64_t)sizeof(c2<T>))));
+  void* wsp;
+  rpa_status st = workspace(c, "grid_tmp", sizeof(c2<T>) * (size_t)(nbat * per_band), &wsp);
+  if (st != RPA_OK) return st;
+  c2<T>* x1 = (c2<T>*)wsp;
+  c2<T>* x2 = x1 + nbat * (int64_t)L1 * N23;
+  c2<T>* bx = x2 + nbat * (int64_t)L1 * L2 * N3;
+  StageTimer tm(c, 4, 0);
+  for (int64_t b0 = 0; b0 < s.nb; b0 += nbat) {
+    const int nbb = (int)std::min<int64_t>(nbat, s.nb - b0);
+    CUDA_OK(c, launch_dft_axis<T>(ub + b0 * Nr, x1, nbb, 1, N1, L1, (int)N23, N1, 0, s.mlo[0], -1, c->stream));
+    CUDA_OK(c, launch_dft_axis<T>(x1, x2, nbb, L1, N2, L2, N3, N2, 0, s.mlo[1], -1, c->stream));
+    CUDA_OK(c, launch_dft_axis<T>(x2, bx, nbb, L1 * L2, N3, L3, 1, N3, 0, s.mlo[2], -1, c->stream));
+    CUDA_OK(c, launch_gather_box<T>(bx, nbb, s.npw, s.pos_d, box, dC + b0 * s.npw, c->stream));
+    tm.add_launches(4);
+  }
+  return RPA_OK;
+}
+
+template <typename T>
+rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* wq, int nw, const double* omega,
+                             const double* W, double dEc, double* Ec_out, int nsets, const int* set_ids,
+                             double* const* dC, double* const* dP, double* const* dchi) {
+  rpa_status st;
+  // every set a q-point touches needs grids and zeroed adjoint accumulators
+  AdjState A;
+  std::vector<int> touched;
+  for (int i = 0; i < nq; ++i) {
+    QPt& Q = c->qpts[iqs[i]];
+    for (size_t t = 0; t < Q.k_of.size(); ++t)
+      for (int id : {Q.k_of[t], Q.kq_of[t]})
+        if (std::find(touched.begin(), touched.end(), id) == touched.end()) touched.push_back(id);
+  }
+  const int64_t Nr = (int64_t)c->tg[0] * c->tg[1] * c->tg[2];
+  for (int id : touched) {
+    OrbSet& s = c->sets[id];
+    if ((st = build_grids(c, s)) != RPA_OK) return st;
+    void* p;
+    const std::string key = "ubar" + std::to_string(id);
+    if ((st = workspace(c, key.c_str(), sizeof(c2<T>) * (size_t)s.nb * Nr, &p)) != RPA_OK) return st;
+    CUDA_OK(c, cudaMemsetAsync(p, 0, sizeof(c2<T>) * (size_t)s.nb * Nr, c->stream));
+    A.ubar[id] = p;
+    if (s.P) {
+      const std::string kp = "gP" + std::to_string(id);
+      if ((st = workspace(c, kp.c_str(), sizeof(double2) * (size_t)s.nb * s.KP, &p)) != RPA_OK) return st;
+      CUDA_OK(c, cudaMemsetAsync(p, 0, sizeof(double2) * (size_t)s.nb * s.KP, c->stream));
+      A.gP[id] = (double2*)p;
+    } else {
+      A.gP[id] = nullptr;
+    }
+  }
+  double E = 0.0;
+  std::vector<double> ld(nw), tr(nw), cw(nw);
+  for (int i = 0; i < nq; ++i) {
+    double2* chi = nullptr;
+    if ((st = build_chi(c, iqs[i], nw, omega, &chi)) != RPA_OK) return st;
+    QPt& Q = c->qpts[iqs[i]];
+    const int NG = Q.NG;
+    const size_t mat = sizeof(double2) * (size_t)nw * NG * NG;
+    void *p_work, *p_ld, *p_tr, *p_flag, *p_Y, *p_W, *p_G64, *p_G32 = nullptr, *p_cw;
+    if ((st = workspace(c, "chol", mat, &p_work)) != RPA_OK) return st;
+    if ((st = workspace(c, "logdet", sizeof(double) * nw, &p_ld)) != RPA_OK) return st;
+    if ((st = workspace(c, "trace", sizeof(double) * nw, &p_tr)) != RPA_OK) return st;
+    if ((st = workspace(c, "flag", sizeof(int), &p_flag)) != RPA_OK) return st;
+    if ((st = workspace(c, "adj_Y", mat, &p_Y)) != RPA_OK) return st;
+    if ((st = workspace(c, "adj_W", mat, &p_W)) != RPA_OK) return st;
+    if ((st = workspace(c, "gamma64", mat, &p_G64)) != RPA_OK) return st;
+    if (sizeof(T) == 4 && (st = workspace(c, "gamma32", mat / 2, &p_G32)) != RPA_OK) return st;
+    if ((st = workspace(c, "cw", sizeof(double) * nw, &p_cw)) != RPA_OK) return st;
+    int64_t nl = 0;
+    {
+      StageTimer tm(c, 3, 0);
+      CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
+                            c->stream, &nl));
+      tm.add_launches(nl);
+    }
+    int flag = 0;
+    CUDA_OK(c, cudaMemcpyAsync(ld.data(), p_ld, sizeof(double) * nw, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(tr.data(), p_tr, sizeof(double) * nw, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(&flag, p_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    if (flag) return fail(c, RPA_ERR_NOT_HPD, "1 - v^1/2 chi0 v^1/2 is not positive definite at q-point %d", iqs[i]);
+    double eq = 0.0;
+    for (int j = 0; j < nw; ++j) {
+      eq += W[j] * (ld[j] + tr[j]);
+      cw[j] = dEc * wq[i] * W[j] / (2.0 * M_PI);
+    }
+    E += wq[i] * eq / (2.0 * M_PI);
+    CUDA_OK(c, cudaMemcpyAsync(p_cw, cw.data(), sizeof(double) * nw, cudaMemcpyHostToDevice, c->stream));
+    nl = 0;
+    {
+      StageTimer tm(c, 3, 0);
+      CUDA_OK(c, run_gamma((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y, (double2*)p_W,
+                           (double2*)p_G64, (float2*)p_G32, c->stream, &nl));
+      tm.add_launches(nl);
+    }
+    if (dchi && dchi[i]) {
+      const bool dev = is_device_ptr(dchi[i]);
+      CUDA_OK(c, cudaMemcpyAsync(dchi[i], p_G64, mat, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+    }
+    const void* omega_d = nullptr;
+    if ((st = workspace(c, "omega", sizeof(double) * nw, (void**)&omega_d)) != RPA_OK) return st;
+    const c2<T>* Gam = sizeof(T) == 8 ? (const c2<T>*)p_G64 : (const c2<T>*)p_G32;
+    for (size_t t = 0; t < Q.k_of.size(); ++t)
+      if ((st = backward_block<T>(c, Q, (int)t, (const double*)omega_d, nw, Gam, A)) != RPA_OK) return st;
+  }
+  // gradients with respect to C and P of the requested sets
+  for (int s = 0; s < nsets; ++s) {
+    const int id = set_ids[s];
+    auto it = c->sets.find(id);
+    if (it == c->sets.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "orbital set %d not set", id);
+    OrbSet& os = it->second;
+    if (dC && dC[s]) {
+      void* p;
+      if ((st = workspace(c, "dC", sizeof(double2) * (size_t)os.nb * os.npw, &p)) != RPA_OK) return st;
+      CUDA_OK(c, cudaMemsetAsync(p, 0, sizeof(double2) * (size_t)os.nb * os.npw, c->stream));
+      if (A.ubar.count(id))
+        if ((st = ubar_to_dC<T>(c, os, (const c2<T>*)A.ubar[id], (double2*)p)) != RPA_OK) return st;
+      const bool dev = is_device_ptr(dC[s]);
+      CUDA_OK(c, cudaMemcpyAsync(dC[s], p, sizeof(double2) * (size_t)os.nb * os.npw,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+      CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (dP && dP[s] && os.P) {
+      const size_t bytes = sizeof(double2) * (size_t)os.nb * os.KP;
+      const bool dev = is_device_ptr(dP[s]);
+      if (A.gP.count(id) && A.gP[id]) {
+        CUDA_OK(c, cudaMemcpyAsync(dP[s], A.gP[id], bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   c->stream));
+      } else if (dev) {
+        CUDA_OK(c, cudaMemsetAsync(dP[s], 0, bytes, c->stream));
+      } else {
+        memset(dP[s], 0, bytes);
+      }
+    }
+  }
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  CUDA_OK(c, cudaGetLastError());
+  if (Ec_out) *Ec_out = E;
   return RPA_OK;
 }
 
@@ -893,6 +1207,31 @@ rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* 
     E += wq[i] * eq / (2.0 * M_PI);
   }
   *Ec = E;
+  prof_end(c);
+  return RPA_OK;
+}
+
+rpa_status rpa_energy_backward(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* wq, int32_t nw,
+                               const double* omega, const double* W, double dEc, double* Ec, int32_t nsets,
+                               const int32_t* set_ids, double* const* dC, double* const* dP, double* const* dchi) {
+  if (!c) return RPA_ERR_ARG;
+  if (nq < 1 || nq > kMaxIndex || !iqs || !wq || nw < 1 || nw > 4096 || !omega || !W || nsets < 0 ||
+      (nsets > 0 && !set_ids) || !std::isfinite(dEc))
+    return fail(c, RPA_ERR_ARG, "bad rpa_energy_backward arguments");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  prof_begin(c);
+  ++c->stamp;
+  for (int i = 0; i < nq; ++i) {
+    rpa_status st = check_q_ready(c, iqs[i]);
+    if (st != RPA_OK) return st;
+  }
+  choose_transform_grid(c, iqs, nq);
+  rpa_status st;
+  if (c->prm.precision == RPA_FP64)
+    st = energy_backward_T<double>(c, nq, iqs, wq, nw, omega, W, dEc, Ec, nsets, set_ids, dC, dP, dchi);
+  else
+    st = energy_backward_T<float>(c, nq, iqs, wq, nw, omega, W, dEc, Ec, nsets, set_ids, dC, dP, dchi);
+  if (st != RPA_OK) return st;
   prof_end(c);
   return RPA_OK;
 }
