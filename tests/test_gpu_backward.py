@@ -68,6 +68,26 @@ def test_backward_matches_oracle_gradient(precision, tol):
         assert _rel(dchi[i], gchi[iq]) < max(tol, 1e-10), ("dchi", iq)
 
 
+def test_autograd_function_matches_direct_backward():
+    import torch
+    from paper_1307_8052_gb300.autograd import RpaEngine, RpaEnergy
+    p = _problem(tag=99)
+    qf = lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm)
+    eng = RpaEngine(p, "fp64", paw_Q=qf)
+    try:
+        Cs = [torch.from_numpy(s.C.copy()).cuda().requires_grad_(True) for s in p.sets]
+        Ps = [torch.from_numpy(s.P.copy()).cuda().requires_grad_(True) for s in p.sets]
+        E = RpaEnergy.apply(eng, *Cs, *Ps)
+        (2.5 * E).backward()
+        E_ref, dC, dP, _ = _grad(eng.ctx, p, eng.omega, eng.W, eng.iqs)
+        assert abs(E.item() - E_ref) < 1e-12 * abs(E_ref)
+        for s in range(len(p.sets)):
+            assert _rel(Cs[s].grad.cpu().numpy(), 2.5 * dC[s]) < 1e-12
+            assert _rel(Ps[s].grad.cpu().numpy(), 2.5 * dP[s]) < 1e-12
+    finally:
+        eng.close()
+
+
 def test_backward_central_differences_fp64():
     """Central differences (h = 1e-6) of the GPU energy along random directions of C and P."""
     p = _problem(tag=98)
