@@ -156,6 +156,35 @@ rpa_status rpa_energy(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
                       const double* wq, int32_t nw, const double* omega,
                       const double* W, double* Ec, double* terms);
 
+/* Split form of rpa_energy for batching and CUDA graphs (the paper's point of
+ * grouping many small independent pieces of work, Sec. 3.2, taken to whole
+ * q-point evaluations).  rpa_set_frequencies stores the nw frequencies on the
+ * device (host pointer).  rpa_energy_enqueue queues every kernel of an E_c
+ * evaluation over the q-points iqs[nq] on the context's stream and returns
+ * without waiting; nothing in it synchronises the host, so it can be captured.
+ * rpa_energy_collect waits for that stream and reduces the queued evaluation
+ * with the weights wq[nq] and W[nw] (host) into *Ec and terms[nq][nw]
+ * (nullable), reporting RPA_ERR_NOT_HPD / RPA_ERR_TIMEOUT as rpa_energy does. */
+rpa_status rpa_set_frequencies(rpa_ctx* ctx, int32_t nw, const double* omega);
+rpa_status rpa_energy_enqueue(rpa_ctx* ctx, int32_t nq, const int32_t* iqs);
+rpa_status rpa_energy_collect(rpa_ctx* ctx, const double* wq, const double* W,
+                              double* Ec, double* terms);
+
+/* One CUDA graph holding the E_c evaluations of n contexts (for example many
+ * (q, cell) instances of different sizes).  All contexts must have been
+ * created with the same caller-provided stream and device and have their
+ * frequencies set.  ctx i evaluates nq[i] q-points, listed one context after
+ * the other in iqs.  rpa_graph_create runs every evaluation once to size the
+ * buffers, then captures them into a graph.  rpa_graph_launch replays it on
+ * that stream; afterwards call rpa_energy_collect on each context.  The
+ * graph is bound to the contexts' buffers: do not change orbitals, q-points,
+ * tuning or frequencies of those contexts while the graph is alive. */
+typedef struct rpa_graph rpa_graph;
+rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq,
+                            const int32_t* iqs, rpa_graph** out);
+rpa_status rpa_graph_launch(rpa_graph* graph);
+void rpa_graph_destroy(rpa_graph* graph);
+
 /* Gradient of E_c (the derivative of Eqs. 1-2 through Eq. 3/17, the PAW term of
  * Eq. 6 and the pair densities of Eqs. 4/10), scaled by dEc.  Same q-points,
  * weights and frequencies as rpa_energy; *Ec (nullable, host) receives E_c.

@@ -44,6 +44,12 @@ SIGNATURES = {
     "rpa_set_tuning": (_I, [_P, _I, ct.c_int64]),
     "rpa_logdet_noalloc": (_I, [_P, _P, _I, _I, _P, _P]),
     "rpa_energy_backward": (_I, [_P, _I, _P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
+    "rpa_set_frequencies": (_I, [_P, _I, _P]),
+    "rpa_energy_enqueue": (_I, [_P, _I, _P]),
+    "rpa_energy_collect": (_I, [_P, _P, _P, _P, _P]),
+    "rpa_graph_create": (_I, [_P, _I, _P, _P, _P]),
+    "rpa_graph_launch": (_I, [_P]),
+    "rpa_graph_destroy": (None, [_P]),
 }
 RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID = 0, 1, 2, 3
 
@@ -227,6 +233,48 @@ def rpa_energy_backward(ctx, iqs, wq, omega, W, dEc=1.0, sets=(), dC=None, dP=No
                                    ptr_array(dC, len(sets)), ptr_array(dP, len(sets)), ptr_array(dchi, len(iqs)))
     _check(ctx, st)
     return E.value
+
+
+def rpa_set_frequencies(ctx, omega):
+    keep = []
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    _check(ctx, lib().rpa_set_frequencies(ctx, len(omega), _ptr(omega, np.float64, keep)))
+
+
+def rpa_energy_enqueue(ctx, iqs):
+    keep = []
+    iqs = np.ascontiguousarray(iqs, dtype=np.int32)
+    _check(ctx, lib().rpa_energy_enqueue(ctx, len(iqs), _ptr(iqs, np.int32, keep)))
+
+
+def rpa_energy_collect(ctx, wq, W, nq):
+    keep = []
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    terms = np.zeros((nq, len(W)))
+    E = ct.c_double()
+    _check(ctx, lib().rpa_energy_collect(ctx, _ptr(wq, np.float64, keep), _ptr(W, np.float64, keep), ct.byref(E),
+                                         terms.ctypes.data_as(_P)))
+    return E.value, terms
+
+
+def rpa_graph_create(ctxs, iq_lists):
+    arr = (ct.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    nq = np.array([len(x) for x in iq_lists], dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.int32) for x in iq_lists]))
+    out = ct.c_void_p()
+    st = lib().rpa_graph_create(ct.cast(arr, ct.c_void_p), len(ctxs), nq.ctypes.data_as(_P), flat.ctypes.data_as(_P),
+                                ct.byref(out))
+    if st != RPA_OK:
+        raise RpaError(st, lib().rpa_last_error(ctxs[0]).decode())
+    return out
+
+
+def rpa_graph_launch(g):
+    _check(None, lib().rpa_graph_launch(g))
+
+
+def rpa_graph_destroy(g):
+    lib().rpa_graph_destroy(g)
 
 
 def rpa_set_profiling(ctx, enable=True):

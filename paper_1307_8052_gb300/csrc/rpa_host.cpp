@@ -97,6 +97,9 @@ struct QPt {
   int natoms = 0;
   std::vector<int> nproj;
   double2* Q = nullptr;
+  int* gfft_d = nullptr;    // [nk][NG][3] transform indices g = G + G0 of every transition
+  char* paw_meta_d = nullptr;  // PAW index tables (q offsets, atom of projector, ...)
+  int KP = 0;
 };
 
 }  // namespace
@@ -119,6 +122,9 @@ struct rpa_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0};  // see rpa_tuning in rpa.h
+  double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
+  int nw_set = 0;
+  std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
   int tg[3] = {0, 0, 0};  // transform grid of the current call (<= prm.grid)
   int* dev_err = nullptr;                 // device-side flag of bounded waits that gave up
 };
@@ -362,20 +368,37 @@ struct Block {
   const int* idx_in = nullptr;
   const int* atom_off = nullptr;
   const int* nproj = nullptr;
+  int a0 = 0;                        // first occupied row of this block
+  const int* Lsub = nullptr;         // device list of the block's occupied bands
 };
 
-// stages a2-a3 (pair densities + PAW) and the pair weights of one transition
+// Occupied-band rows [a0, a1) of a transition form one block: the pair
+// rectangle is always whole rows x all empty bands, so every kernel sees a
+// plain (nL x nR) rectangle.  Rows per block bound the N and operand buffers.
+int rows_per_block(const rpa_ctx* c, int nL, int nR, int NG, int nw) {
+  const int64_t NGpad = (NG + 127) / 128 * 128;
+  const int64_t budget = (int64_t)6 << 30;  // tensor-core operands: NGpad * 2P * 2 terms * 2 B * (nw + 2)
+  int64_t pmax = budget / (NGpad * 8 * (nw + 2));
+  if (c->prm.precision == RPA_FP64 || c->prm.precision == RPA_FP32) pmax = ((int64_t)2 << 30) / (16 * NG);
+  int64_t rows = std::max<int64_t>(1, pmax / std::max(1, nR));
+  return (int)std::min<int64_t>(rows, nL);
+}
+
+// stages a2-a3 (pair densities + PAW) and the pair weights of rows [a0, a1) of one transition
 template <typename T>
-rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, Block<T>& B) {
+rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* omega_d, int nw, Block<T>& B) {
   OrbSet& sk = c->sets[Q.k_of[t]];
   OrbSet& skp = c->sets[Q.kq_of[t]];
   B.sk = &sk;
   B.skp = &skp;
-  const int nL = (int)sk.L.size(), nR = (int)skp.R.size();
+  const int nL = a1 - a0, nR = (int)skp.R.size();
+  const int* Lsub = sk.L_d + a0;
   const int64_t P = (int64_t)nL * nR;
   B.nL = nL;
   B.nR = nR;
   B.P = P;
+  B.a0 = a0;
+  B.Lsub = Lsub;
   if (P == 0) return RPA_OK;
   const int N1 = c->tg[0], N2 = c->tg[1], N3 = c->tg[2];
   const int64_t Nr = (int64_t)N1 * N2 * N3;
@@ -386,7 +409,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
   B.Nr = Nr;
   B.NG = NG;
   const int* G0 = &Q.G0[3 * t];
-  // target Fourier indices g = G + G0 and their box
+  // target Fourier indices g = G + G0 (cached on the device per transition) and their box
   std::vector<int>& gfft = B.gfft;
   gfft.assign(3 * (size_t)NG, 0);
   int glo[3] = {1 << 30, 1 << 30, 1 << 30}, ghi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
@@ -401,10 +424,9 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
   B.n1 = n1;
   B.n2 = n2;
   for (int d = 0; d < 3; ++d) B.glo[d] = glo[d];
-  void *p_gfft, *p_d, *p_df, *p_w, *p_N, *p_T1, *p_T2;
+  void* p_gfft = Q.gfft_d + (size_t)3 * NG * t;
+  void *p_d, *p_df, *p_w, *p_N, *p_T1, *p_T2;
   rpa_status st;
-  if ((st = workspace(c, "gfft", sizeof(int) * gfft.size(), &p_gfft)) != RPA_OK) return st;
-  CUDA_OK(c, cudaMemcpyAsync(p_gfft, gfft.data(), sizeof(int) * gfft.size(), cudaMemcpyHostToDevice, c->stream));
   if ((st = workspace(c, "pair_d", sizeof(double) * P, &p_d)) != RPA_OK) return st;
   if ((st = workspace(c, "pair_df", sizeof(double) * P, &p_df)) != RPA_OK) return st;
   if ((st = workspace(c, "pair_w", sizeof(T) * P * nw, &p_w)) != RPA_OK) return st;
@@ -412,7 +434,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
   const double pref = c->prm.spin_factor / (c->volume * (double)c->prm.nk_bz);
   {
     StageTimer tm(c, 4, 2);
-    CUDA_OK(c, launch_pair_params(sk.eps_d, sk.f_d, skp.eps_d, skp.f_d, sk.L_d, nL, skp.R_d, nR, (double*)p_d,
+    CUDA_OK(c, launch_pair_params(sk.eps_d, sk.f_d, skp.eps_d, skp.f_d, Lsub, nL, skp.R_d, nR, (double*)p_d,
                                   (double*)p_df, c->stream));
     CUDA_OK(c, launch_pair_weights((double*)p_d, (double*)p_df, omega_d, nw, P, pref,
                                    sizeof(T) == 8 ? (double*)p_w : nullptr, sizeof(T) == 4 ? (float*)p_w : nullptr,
@@ -427,33 +449,8 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
     if (sk.nproj != Q.nproj || skp.nproj != Q.nproj)
       return fail(c, RPA_ERR_ARG, "PAW projector counts of the orbital sets do not match Q of this q-point");
     KP = sk.KP;
-    std::vector<int> atom_of(KP), idx_in(KP), atom_off(Q.natoms);
-    std::vector<int64_t> q_off(Q.natoms);
-    int off = 0;
-    int64_t qo = 0;
-    for (int a = 0; a < Q.natoms; ++a) {
-      atom_off[a] = off;
-      q_off[a] = qo;
-      for (int j = 0; j < Q.nproj[a]; ++j) {
-        atom_of[off + j] = a;
-        idx_in[off + j] = j;
-      }
-      off += Q.nproj[a];
-      qo += (int64_t)Q.nproj[a] * Q.nproj[a] * NG;
-    }
-    void *p_meta, *p_R, *p_Pm;
-    const size_t meta_bytes = sizeof(int) * (2 * KP + 2 * Q.natoms) + sizeof(int64_t) * Q.natoms;
-    if ((st = workspace(c, "paw_meta", meta_bytes, &p_meta)) != RPA_OK) return st;
-    std::vector<char> meta(meta_bytes);
-    char* mp = meta.data();
-    memcpy(mp, q_off.data(), sizeof(int64_t) * Q.natoms);
-    memcpy(mp + sizeof(int64_t) * Q.natoms, atom_of.data(), sizeof(int) * KP);
-    memcpy(mp + sizeof(int64_t) * Q.natoms + sizeof(int) * KP, idx_in.data(), sizeof(int) * KP);
-    memcpy(mp + sizeof(int64_t) * Q.natoms + sizeof(int) * 2 * KP, atom_off.data(), sizeof(int) * Q.natoms);
-    memcpy(mp + sizeof(int64_t) * Q.natoms + sizeof(int) * (2 * KP + Q.natoms), Q.nproj.data(),
-           sizeof(int) * Q.natoms);
-    CUDA_OK(c, cudaMemcpyAsync(p_meta, meta.data(), meta_bytes, cudaMemcpyHostToDevice, c->stream));
-    const char* md = (const char*)p_meta;
+    void *p_R, *p_Pm;
+    const char* md = Q.paw_meta_d;
     const int64_t* q_off_d = (const int64_t*)md;
     const int* atom_of_d = (const int*)(md + sizeof(int64_t) * Q.natoms);
     const int* idx_in_d = atom_of_d + KP;
@@ -469,7 +466,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
     Rp = (c2<T>*)p_R;
     Pm = (c2<T>*)p_Pm;
     StageTimer tm(c, 1, 2);
-    CUDA_OK(c, launch_paw_R<T>(sk.P, KP, sk.L_d, nL, Q.Q, atom_of_d, idx_in_d, atom_off_d, q_off_d, nproj_d, NG, Rp,
+    CUDA_OK(c, launch_paw_R<T>(sk.P, KP, Lsub, nL, Q.Q, atom_of_d, idx_in_d, atom_off_d, q_off_d, nproj_d, NG, Rp,
                                c->stream));
     CUDA_OK(c, launch_gather_P<T>(skp.P, KP, skp.R_d, nR, Pm, c->stream));
   }
@@ -492,7 +489,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
     CUDA_OK(c, launch_twiddle_matrix<T>((c2<T>*)p_twB, N2, glo[1], n2, c->stream));
     for (int64_t p0 = 0; p0 < P; p0 += PC) {
       const int np = (int)std::min<int64_t>(PC, P - p0);
-      CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, sk.L_d, skp.R_d, nR,
+      CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d, nR,
                                      p0, np, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
       CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                      c->stream));
@@ -515,21 +512,26 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw,
 // stages a2-a4 for one transition: pair densities, then the grouped rank-k update
 template <typename T>
 rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, double2* chi) {
-  Block<T> B;
-  rpa_status st = pairs_block<T>(c, Q, t, omega_d, nw, B);
-  if (st != RPA_OK || B.P == 0) return st;
-  StageTimer tm(c, 2, 1);
-  const int prec = c->prm.precision;
-  if (prec == RPA_FP64 || prec == RPA_FP32) {
-    CUDA_OK(c, launch_herk_simt_w<T>(B.N, B.P, B.NG, B.w, nw, chi, c->stream));
-  } else {
-    const int terms = prec == RPA_BF16X3 ? 3 : 2;
-    void* scr = nullptr;
-    const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
-    if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
-    CUDA_OK(c, launch_herk_tc((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms,
-                              (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH], chi, scr, sb,
-                              c->dev_err, c->stream));
+  const int nL = (int)c->sets[Q.k_of[t]].L.size(), nR = (int)c->sets[Q.kq_of[t]].R.size();
+  const int rows = rows_per_block(c, nL, nR, Q.NG, nw);
+  for (int a0 = 0; a0 < nL; a0 += rows) {
+    Block<T> B;
+    rpa_status st = pairs_block<T>(c, Q, t, a0, std::min(nL, a0 + rows), omega_d, nw, B);
+    if (st != RPA_OK) return st;
+    if (B.P == 0) continue;
+    StageTimer tm(c, 2, 1);
+    const int prec = c->prm.precision;
+    if (prec == RPA_FP64 || prec == RPA_FP32) {
+      CUDA_OK(c, launch_herk_simt_w<T>(B.N, B.P, B.NG, B.w, nw, chi, c->stream));
+    } else {
+      const int terms = prec == RPA_BF16X3 ? 3 : 2;
+      void* scr = nullptr;
+      const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
+      if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
+      CUDA_OK(c, launch_herk_tc((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms,
+                                (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH], chi, scr, sb,
+                                c->dev_err, c->stream));
+    }
   }
   return RPA_OK;
 }
@@ -544,6 +546,87 @@ rpa_status check_q_ready(rpa_ctx* c, int iq) {
     if (a == c->sets.end() || !a->second.valid || b == c->sets.end() || !b->second.valid)
       return fail(c, RPA_ERR_STATE, "q-point %d references an orbital set that is not set", iq);
   }
+  return RPA_OK;
+}
+
+// chi0 of one q-point, enqueued without any host synchronisation (frequencies
+// already on the device); bounded-wait failures land in c->dev_err.
+rpa_status build_chi_async(rpa_ctx* c, int iq, int nw, const double* p_om, double2** chi_out) {
+  rpa_status st = check_q_ready(c, iq);
+  if (st != RPA_OK) return st;
+  QPt& Q = c->qpts[iq];
+  const int NG = Q.NG;
+  void* p_chi;
+  if ((st = workspace(c, "chi", sizeof(double2) * (size_t)nw * NG * NG, &p_chi)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemsetAsync(p_chi, 0, sizeof(double2) * (size_t)nw * NG * NG, c->stream));
+  for (size_t t = 0; t < Q.k_of.size(); ++t) {
+    if ((st = build_grids(c, c->sets[Q.k_of[t]])) != RPA_OK) return st;
+    if ((st = build_grids(c, c->sets[Q.kq_of[t]])) != RPA_OK) return st;
+  }
+  for (size_t t = 0; t < Q.k_of.size(); ++t) {
+    if (c->prm.precision == RPA_FP64)
+      st = chi_block<double>(c, Q, (int)t, p_om, nw, (double2*)p_chi);
+    else
+      st = chi_block<float>(c, Q, (int)t, p_om, nw, (double2*)p_chi);
+    if (st != RPA_OK) return st;
+  }
+  *chi_out = (double2*)p_chi;
+  return RPA_OK;
+}
+
+// all device work of an E_c evaluation: chi0 and log-det terms of every q-point
+// into res_ld / res_tr / res_flag; no host synchronisation, so it can be captured
+rpa_status energy_enqueue(rpa_ctx* c, int nq, const int* iqs, int nw, const double* omega_d) {
+  rpa_status st;
+  void *p_ld, *p_tr, *p_fl;
+  if ((st = workspace(c, "res_ld", sizeof(double) * (size_t)nq * nw, &p_ld)) != RPA_OK) return st;
+  if ((st = workspace(c, "res_tr", sizeof(double) * (size_t)nq * nw, &p_tr)) != RPA_OK) return st;
+  if ((st = workspace(c, "res_flag", sizeof(int) * (size_t)nq, &p_fl)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+  for (int i = 0; i < nq; ++i) {
+    double2* chi = nullptr;
+    if ((st = build_chi_async(c, iqs[i], nw, omega_d, &chi)) != RPA_OK) return st;
+    QPt& Q = c->qpts[iqs[i]];
+    void* p_work;
+    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)nw * Q.NG * Q.NG, &p_work)) != RPA_OK) return st;
+    int64_t nl = 0;
+    StageTimer tm(c, 3, 0);
+    CUDA_OK(c, run_logdet(chi, Q.v_d, nw, Q.NG, (double2*)p_work, (double*)p_ld + (size_t)i * nw,
+                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, c->stream, &nl));
+    tm.add_launches(nl);
+  }
+  c->enq_iqs.assign(iqs, iqs + nq);
+  return RPA_OK;
+}
+
+// waits for the enqueued evaluation and reduces it on the host
+rpa_status energy_collect(rpa_ctx* c, int nw, const double* wq, const double* W, double* Ec, double* terms) {
+  const int nq = (int)c->enq_iqs.size();
+  if (nq == 0) return fail(c, RPA_ERR_STATE, "no energy evaluation enqueued");
+  std::vector<double> ld((size_t)nq * nw), tr((size_t)nq * nw);
+  std::vector<int> flag(nq);
+  int derr = 0;
+  CUDA_OK(c, cudaMemcpyAsync(ld.data(), c->ws["res_ld"].p, sizeof(double) * ld.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(tr.data(), c->ws["res_tr"].p, sizeof(double) * tr.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(flag.data(), c->ws["res_flag"].p, sizeof(int) * nq, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(&derr, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (derr) return fail(c, RPA_ERR_TIMEOUT, "a bounded device wait gave up in the tensor-core update (code %d)", derr);
+  double E = 0.0;
+  for (int i = 0; i < nq; ++i) {
+    if (flag[i])
+      return fail(c, RPA_ERR_NOT_HPD, "1 - v^1/2 chi0 v^1/2 is not positive definite at q-point %d", c->enq_iqs[i]);
+    double eq = 0.0;
+    for (int j = 0; j < nw; ++j) {
+      const double e = ld[(size_t)i * nw + j] + tr[(size_t)i * nw + j];
+      if (terms) terms[(size_t)i * nw + j] = e;
+      eq += W[j] * e;
+    }
+    E += wq[i] * eq / (2.0 * M_PI);
+  }
+  *Ec = E;
   return RPA_OK;
 }
 
@@ -585,10 +668,10 @@ struct AdjState {
 };
 
 template <typename T>
-rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, const c2<T>* Gam,
-                          AdjState& A) {
+rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* omega_d, int nw,
+                          const c2<T>* Gam, AdjState& A) {
   Block<T> B;
-  rpa_status st = pairs_block<T>(c, Q, t, omega_d, nw, B);
+  rpa_status st = pairs_block<T>(c, Q, t, a0, a1, omega_d, nw, B);
   if (st != RPA_OK || B.P == 0) return st;
   OrbSet& sk = *B.sk;
   OrbSet& skp = *B.skp;
@@ -604,7 +687,7 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int 
   if (B.KP > 0) {
     if ((st = workspace(c, "paw_y", sizeof(c2<T>) * (size_t)nL * B.KP * NG, &p_y)) != RPA_OK) return st;
     CUDA_OK(c, launch_paw_adjoint<T>(Nbar, B.R, B.Pm, nL, nR, NG, B.KP, Q.Q, B.atom_of, B.idx_in, B.atom_off,
-                                     B.q_off, B.nproj, sk.L_d, skp.R_d, (c2<T>*)p_y, A.gP[Q.k_of[t]],
+                                     B.q_off, B.nproj, B.Lsub, skp.R_d, (c2<T>*)p_y, A.gP[Q.k_of[t]],
                                      A.gP[Q.kq_of[t]], c->stream));
     tm.add_launches(3);
   }
@@ -647,10 +730,10 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int 
                                       c->stream));
       CUDA_OK(c, launch_pd_stageB<T>(B.T2, B.T1, np, n1, n2, N3, (const c2<T>*)p_twb, N2, c->stream));
       CUDA_OK(c, launch_adj_stageA<T>(B.T1, np, n1, N1, (int)N23, (const c2<T>*)p_twa,
-                                      (const c2<T>*)sk.U + (int64_t)sk.L[a] * Nr, (const c2<T>*)skp.U, skp.R_d, nR,
+                                      (const c2<T>*)sk.U + (int64_t)sk.L[B.a0 + a] * Nr, (const c2<T>*)skp.U, skp.R_d, nR,
                                       p0, ub_kp, (c2<T>*)p_xbar, c->stream));
       CUDA_OK(c, launch_adj_un<T>((const c2<T>*)p_xbar, np, Nr, (const c2<T>*)skp.U, skp.R_d, nR, p0,
-                                  ub_k + (int64_t)sk.L[a] * Nr, c->stream));
+                                  ub_k + (int64_t)sk.L[B.a0 + a] * Nr, c->stream));
       tm.add_launches(4);
     }
   }
@@ -771,7 +854,14 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     if ((st = workspace(c, "omega", sizeof(double) * nw, (void**)&omega_d)) != RPA_OK) return st;
     const c2<T>* Gam = sizeof(T) == 8 ? (const c2<T>*)p_G64 : (const c2<T>*)p_G32;
     for (size_t t = 0; t < Q.k_of.size(); ++t)
-      if ((st = backward_block<T>(c, Q, (int)t, (const double*)omega_d, nw, Gam, A)) != RPA_OK) return st;
+    {
+      const int nL = (int)c->sets[Q.k_of[t]].L.size(), nR = (int)c->sets[Q.kq_of[t]].R.size();
+      const int rows = rows_per_block(c, nL, nR, NG, nw);
+      for (int a0 = 0; a0 < nL; a0 += rows)
+        if ((st = backward_block<T>(c, Q, (int)t, a0, std::min(nL, a0 + rows), (const double*)omega_d, nw, Gam,
+                                    A)) != RPA_OK)
+          return st;
+    }
   }
   // gradients with respect to C and P of the requested sets
   for (int s = 0; s < nsets; ++s) {
@@ -869,11 +959,14 @@ void rpa_destroy(rpa_ctx* c) {
   }
   for (auto& kv : c->qpts) {
     dev_free(kv.second.v_d);
+    dev_free(kv.second.gfft_d);
+    dev_free(kv.second.paw_meta_d);
     dev_free(kv.second.Q);
   }
   for (auto& kv : c->ws) dev_free(kv.second.p);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   dev_free(c->dev_err);
+  dev_free(c->omega_d);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1089,11 +1182,23 @@ rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t
   rpa_status st;
   if ((st = dev_alloc(c, (void**)&Q.v_d, sizeof(double) * Q.NG)) != RPA_OK) return st;
   CUDA_OK(c, cudaMemcpyAsync(Q.v_d, Q.v.data(), sizeof(double) * Q.NG, cudaMemcpyHostToDevice, c->stream));
+  // transform indices g = G + G0 of every transition, kept on the device
+  std::vector<int> gfft((size_t)3 * Q.NG * nk);
+  for (int t = 0; t < nk; ++t)
+    for (int i = 0; i < Q.NG; ++i)
+      for (int d = 0; d < 3; ++d) gfft[((size_t)t * Q.NG + i) * 3 + d] = Q.gm[3 * i + d] + G0[3 * t + d];
+  if ((st = dev_alloc(c, (void**)&Q.gfft_d, sizeof(int) * gfft.size())) != RPA_OK) {
+    dev_free(Q.v_d);
+    return st;
+  }
+  CUDA_OK(c, cudaMemcpyAsync(Q.gfft_d, gfft.data(), sizeof(int) * gfft.size(), cudaMemcpyHostToDevice, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   auto it = c->qpts.find(iq);
   if (it != c->qpts.end()) {
     dev_free(it->second.v_d);
     dev_free(it->second.Q);
+    dev_free(it->second.gfft_d);
+    dev_free(it->second.paw_meta_d);
   }
   c->qpts[iq] = Q;
   if (ng_out) *ng_out = Q.NG;
@@ -1125,9 +1230,48 @@ rpa_status rpa_set_paw_Q(rpa_ctx* c, int32_t iq, int32_t natoms, const int32_t* 
   rpa_status st;
   if ((st = dev_alloc(c, (void**)&Qd, sizeof(double2) * (size_t)tot)) != RPA_OK) return st;
   if ((st = copy_in(c, Qd, Qv, sizeof(double2) * (size_t)tot)) != RPA_OK) { dev_free(Qd); return st; }
+  // index tables of the projector layout: q offsets per atom, atom and index of
+  // every projector, first projector of every atom, projectors per atom
+  int KP = 0;
+  for (int a = 0; a < natoms; ++a) KP += nproj[a];
+  std::vector<int> atom_of(KP), idx_in(KP), atom_off(natoms);
+  std::vector<int64_t> q_off(natoms);
+  int off = 0;
+  int64_t qo = 0;
+  for (int a = 0; a < natoms; ++a) {
+    atom_off[a] = off;
+    q_off[a] = qo;
+    for (int j = 0; j < nproj[a]; ++j) {
+      atom_of[off + j] = a;
+      idx_in[off + j] = j;
+    }
+    off += nproj[a];
+    qo += (int64_t)nproj[a] * nproj[a] * Q.NG;
+  }
+  const size_t meta_bytes = sizeof(int64_t) * natoms + sizeof(int) * (2 * KP + 2 * natoms);
+  std::vector<char> meta(meta_bytes);
+  char* mp = meta.data();
+  memcpy(mp, q_off.data(), sizeof(int64_t) * natoms);
+  mp += sizeof(int64_t) * natoms;
+  memcpy(mp, atom_of.data(), sizeof(int) * KP);
+  mp += sizeof(int) * KP;
+  memcpy(mp, idx_in.data(), sizeof(int) * KP);
+  mp += sizeof(int) * KP;
+  memcpy(mp, atom_off.data(), sizeof(int) * natoms);
+  mp += sizeof(int) * natoms;
+  memcpy(mp, nproj, sizeof(int) * natoms);
+  char* md = nullptr;
+  if ((st = dev_alloc(c, (void**)&md, meta_bytes)) != RPA_OK) {
+    dev_free(Qd);
+    return st;
+  }
+  CUDA_OK(c, cudaMemcpyAsync(md, meta.data(), meta_bytes, cudaMemcpyHostToDevice, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   dev_free(Q.Q);
+  dev_free(Q.paw_meta_d);
   Q.Q = Qd;
+  Q.paw_meta_d = md;
+  Q.KP = KP;
   Q.natoms = natoms;
   Q.nproj.assign(nproj, nproj + natoms);
   return RPA_OK;
@@ -1172,43 +1316,125 @@ rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* 
     if (st != RPA_OK) return st;
   }
   choose_transform_grid(c, iqs, nq);
-  double E = 0.0;
-  std::vector<double> ld(nw), tr(nw);
-  for (int i = 0; i < nq; ++i) {
-    double2* chi = nullptr;
-    rpa_status st = build_chi(c, iqs[i], nw, omega, &chi);
-    if (st != RPA_OK) return st;
-    QPt& Q = c->qpts[iqs[i]];
-    const int NG = Q.NG;
-    void *p_work, *p_ld, *p_tr, *p_flag;
-    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)nw * NG * NG, &p_work)) != RPA_OK) return st;
-    if ((st = workspace(c, "logdet", sizeof(double) * nw, &p_ld)) != RPA_OK) return st;
-    if ((st = workspace(c, "trace", sizeof(double) * nw, &p_tr)) != RPA_OK) return st;
-    if ((st = workspace(c, "flag", sizeof(int), &p_flag)) != RPA_OK) return st;
-    int64_t nl = 0;
-    {
-      StageTimer tm(c, 3, 0);
-      CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
-                            c->stream, &nl));
-      tm.add_launches(nl);
-    }
-    int flag = 0;
-    CUDA_OK(c, cudaMemcpyAsync(ld.data(), p_ld, sizeof(double) * nw, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OK(c, cudaMemcpyAsync(tr.data(), p_tr, sizeof(double) * nw, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OK(c, cudaMemcpyAsync(&flag, p_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OK(c, cudaStreamSynchronize(c->stream));
-    if (flag) return fail(c, RPA_ERR_NOT_HPD, "1 - v^1/2 chi0 v^1/2 is not positive definite at q-point %d", iqs[i]);
-    double eq = 0.0;
-    for (int j = 0; j < nw; ++j) {
-      const double e = ld[j] + tr[j];
-      if (terms) terms[(size_t)i * nw + j] = e;
-      eq += W[j] * e;
-    }
-    E += wq[i] * eq / (2.0 * M_PI);
-  }
-  *Ec = E;
+  void* p_om;
+  rpa_status st;
+  if ((st = workspace(c, "omega", sizeof(double) * nw, &p_om)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemcpyAsync(p_om, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, c->stream));
+  if ((st = energy_enqueue(c, nq, iqs, nw, (const double*)p_om)) != RPA_OK) return st;
+  if ((st = energy_collect(c, nw, wq, W, Ec, terms)) != RPA_OK) return st;
   prof_end(c);
   return RPA_OK;
+}
+
+rpa_status rpa_set_frequencies(rpa_ctx* c, int32_t nw, const double* omega) {
+  if (!c) return RPA_ERR_ARG;
+  if (nw < 1 || nw > 4096 || !omega) return fail(c, RPA_ERR_ARG, "bad frequency arguments");
+  for (int j = 0; j < nw; ++j)
+    if (!std::isfinite(omega[j])) return fail(c, RPA_ERR_ARG, "omega[%d] not finite", j);
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  double* d = nullptr;
+  rpa_status st;
+  if ((st = dev_alloc(c, (void**)&d, sizeof(double) * nw)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemcpyAsync(d, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  dev_free(c->omega_d);
+  c->omega_d = d;
+  c->nw_set = nw;
+  return RPA_OK;
+}
+
+rpa_status rpa_energy_enqueue(rpa_ctx* c, int32_t nq, const int32_t* iqs) {
+  if (!c) return RPA_ERR_ARG;
+  if (nq < 1 || nq > kMaxIndex || !iqs) return fail(c, RPA_ERR_ARG, "bad rpa_energy_enqueue arguments");
+  if (!c->omega_d) return fail(c, RPA_ERR_STATE, "rpa_set_frequencies has not been called");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  ++c->stamp;
+  for (int i = 0; i < nq; ++i) {
+    rpa_status st = check_q_ready(c, iqs[i]);
+    if (st != RPA_OK) return st;
+  }
+  choose_transform_grid(c, iqs, nq);
+  return energy_enqueue(c, nq, iqs, c->nw_set, c->omega_d);
+}
+
+struct rpa_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+};
+
+rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq, const int32_t* iqs, rpa_graph** out) {
+  if (!ctxs || n < 1 || !nq || !iqs || !out) return RPA_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || nq[i] < 1) return RPA_ERR_ARG;
+    if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->prm.device != ctxs[0]->prm.device)
+      return fail(ctxs[i], RPA_ERR_ARG, "all contexts of a graph must share one stream and device");
+    if (!ctxs[0]->prm.stream) return fail(ctxs[i], RPA_ERR_ARG, "a graph needs a caller-provided stream");
+    if (!ctxs[i]->omega_d) return fail(ctxs[i], RPA_ERR_STATE, "rpa_set_frequencies has not been called");
+  }
+  cudaStream_t s = ctxs[0]->stream;
+  if (cudaSetDevice(ctxs[0]->prm.device) != cudaSuccess) return RPA_ERR_CUDA;
+  // warm-up outside the capture: sizes every workspace and device table
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    rpa_status st = rpa_energy_enqueue(ctxs[i], nq[i], iqs + off);
+    if (st != RPA_OK) return st;
+    off += nq[i];
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ctxs[0], RPA_ERR_CUDA, "warm-up run failed");
+  std::vector<bool> prof(n);
+  for (int i = 0; i < n; ++i) {
+    prof[i] = ctxs[i]->profiling;
+    ctxs[i]->profiling = false;
+  }
+  rpa_graph* g = new rpa_graph();
+  g->stream = s;
+  g->device = ctxs[0]->prm.device;
+  rpa_status st = RPA_OK;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    st = fail(ctxs[0], RPA_ERR_CUDA, "cudaStreamBeginCapture failed");
+  } else {
+    off = 0;
+    for (int i = 0; i < n && st == RPA_OK; ++i) {
+      st = rpa_energy_enqueue(ctxs[i], nq[i], iqs + off);
+      off += nq[i];
+    }
+    const cudaError_t e = cudaStreamEndCapture(s, &g->graph);
+    if (st == RPA_OK && e != cudaSuccess) st = fail(ctxs[0], RPA_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
+    if (st == RPA_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+      st = fail(ctxs[0], RPA_ERR_CUDA, "cudaGraphInstantiate failed");
+  }
+  for (int i = 0; i < n; ++i) ctxs[i]->profiling = prof[i];
+  if (st != RPA_OK) {
+    cudaGetLastError();
+    rpa_graph_destroy(g);
+    return st;
+  }
+  *out = g;
+  return RPA_OK;
+}
+
+rpa_status rpa_graph_launch(rpa_graph* g) {
+  if (!g || !g->exec) return RPA_ERR_ARG;
+  if (cudaSetDevice(g->device) != cudaSuccess) return RPA_ERR_CUDA;
+  return cudaGraphLaunch(g->exec, g->stream) == cudaSuccess ? RPA_OK : RPA_ERR_CUDA;
+}
+
+void rpa_graph_destroy(rpa_graph* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+rpa_status rpa_energy_collect(rpa_ctx* c, const double* wq, const double* W, double* Ec, double* terms) {
+  if (!c) return RPA_ERR_ARG;
+  if (!wq || !W || !Ec) return fail(c, RPA_ERR_ARG, "bad rpa_energy_collect arguments");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  return energy_collect(c, c->nw_set, wq, W, Ec, terms);
 }
 
 rpa_status rpa_energy_backward(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* wq, int32_t nw,
