@@ -337,6 +337,86 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def run_batched(args):
+    """Batched workload: ``--instances`` (q, cell) instances of uneven sizes
+    (NG ~ U[400, 3000], n_occ ~ U[8, 120], n_unocc ~ NG, 16 frequencies, PAW),
+    evaluated (a) as plain sequential rpa_energy calls and (b) as one CUDA graph
+    over all instances, with the pair-chunk launch shape from the autotuner."""
+    import torch
+    from paper_1307_8052_gb300 import autotune as at
+    from paper_1307_8052_gb300 import binding as b
+    from paper_1307_8052_gb300 import synthetic as syn
+    from paper_1307_8052_gb300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    b.load()
+    t0 = time.perf_counter()
+    probs = [syn.config3_instance(i) for i in range(args.instances)]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    om, W = b.rpa_gauss_legendre(16, 1.0)
+    ctxs, flops, ngs = [], [], []
+    for p in probs:
+        ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, args.precision,
+                           stream=stream.cuda_stream)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_OPERAND_MB, 512)
+        ng = b.load_problem(ctx, p, paw_Q=lambda iq, gm, p=p: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))[0]
+        b.rpa_set_frequencies(ctx, om)
+        k = int(np.sum(p.sets[0].f > 0)) * int(np.sum(p.sets[1].f < 1))
+        ctxs.append(ctx)
+        ngs.append(ng)
+        flops.append(rankk_flops([ng], [k], 16))
+    total = float(sum(flops))
+    sync = stream.synchronize
+    # autotune the launch shapes on the median-size instance, share the result
+    mid = int(np.argsort(ngs)[len(ngs) // 2])
+    tune = at.autotune(ctxs[mid], [0], [1.0], om, W, reps=1, sync=sync)
+    for ctx in ctxs:
+        at.apply(ctx, tune["best"])
+
+    def sequential():
+        for ctx in ctxs:
+            b.rpa_energy(ctx, [0], [1.0], om, W)
+
+    sequential()
+    sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sequential()
+    ev1.record(stream)
+    sync()
+    t_seq = ev0.elapsed_time(ev1) / args.steps / 1e3
+    g = b.rpa_graph_create(ctxs, [[0]] * len(ctxs))
+    E = []
+    try:
+        b.rpa_graph_launch(g)
+        sync()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b.rpa_graph_launch(g)
+        ev1.record(stream)
+        sync()
+        t_graph = ev0.elapsed_time(ev1) / args.steps / 1e3
+        for ctx in ctxs:
+            E.append(b.rpa_energy_collect(ctx, [1.0], W, 1)[0])
+    finally:
+        b.rpa_graph_destroy(g)
+    for ctx in ctxs:
+        b.rpa_destroy(ctx)
+    line = {"metric": METRIC + " (batched instances)", "value": total / t_graph / 1e12, "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": t_graph * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"{len(ctxs)} (q, cell) instances, NG 400-3000, n_occ 8-120, n_unocc ~ NG, "
+                                   "16 iw, 3x13 PAW, one CUDA graph", "NG": ngs, "generation_s": gen_s},
+            "sequential": {"value": total / t_seq / 1e12, "ms_per_step": t_seq * 1e3},
+            "graph_speedup_vs_sequential": t_seq / t_graph,
+            "autotune": {"best": {str(k): v for k, v in tune["best"].items()}, "best_ms": tune["best_s"] * 1e3},
+            "E_c_sum": float(np.sum(E))}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,9 +427,13 @@ def main():
     ap.add_argument("--fp64-q", type=int, default=3, help="q-point timed in plain FP64 (-1: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sustained", action="store_true")
+    ap.add_argument("--config", choices=["bulk", "batched"], default="bulk")
+    ap.add_argument("--instances", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -228,13 +228,17 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      Eq. 10 has no aliasing for the transitions of the call
  *                      (never larger than params.grid); results equal the
  *                      plane-wave sums of Eq. 4 either way.  1: params.grid.
+ * RPA_TUNE_OPERAND_MB  device memory (MiB, >= 16) for the pair densities and
+ *                      rank-k operands of one block of occupied bands; larger
+ *                      pair sets are processed in several blocks.  Default 6144.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
   RPA_TUNE_PAIR_CHUNK = 1,
   RPA_TUNE_TC_FLUSH = 2,
   RPA_TUNE_PD_GRID = 3,
-  RPA_TUNE_COUNT = 4
+  RPA_TUNE_OPERAND_MB = 4,
+  RPA_TUNE_COUNT = 5
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

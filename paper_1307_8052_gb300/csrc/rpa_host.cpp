@@ -121,7 +121,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -377,9 +377,10 @@ struct Block {
 // plain (nL x nR) rectangle.  Rows per block bound the N and operand buffers.
 int rows_per_block(const rpa_ctx* c, int nL, int nR, int NG, int nw) {
   const int64_t NGpad = (NG + 127) / 128 * 128;
-  const int64_t budget = (int64_t)6 << 30;  // tensor-core operands: NGpad * 2P * 2 terms * 2 B * (nw + 2)
+  // tensor-core operands: NGpad * 2P * 2 terms * 2 B * (nw + 2); pair densities: P * NG * 8-16 B
+  const int64_t budget = c->tune[RPA_TUNE_OPERAND_MB] << 20;
   int64_t pmax = budget / (NGpad * 8 * (nw + 2));
-  if (c->prm.precision == RPA_FP64 || c->prm.precision == RPA_FP32) pmax = ((int64_t)2 << 30) / (16 * NG);
+  if (c->prm.precision == RPA_FP64 || c->prm.precision == RPA_FP32) pmax = budget / (16 * (int64_t)NG);
   int64_t rows = std::max<int64_t>(1, pmax / std::max(1, nR));
   return (int)std::min<int64_t>(rows, nL);
 }
@@ -1480,6 +1481,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_PD_GRID:
       if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "transform grid choice must be 0 or 1");
+      break;
+    case RPA_TUNE_OPERAND_MB:
+      if (value < 16 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "operand budget %lld MB out of range", (long long)value);
       break;
     default:
       return fail(c, RPA_ERR_ARG, "unknown tuning parameter %d", param);

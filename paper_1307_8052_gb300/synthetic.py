@@ -205,6 +205,33 @@ def config1(nocc: int = 16, nunocc: int = 1200, with_paw: bool = True) -> Proble
                    sets, qps, 16, paw)
 
 
+def config3_instance(i: int, nw: int = 16) -> Problem:
+    """One (q, cell) instance of the batched workload: the bulk box of config 1
+    (9 bohr, 40^3 grid, 20 Ha orbitals), Gamma k-point, q drawn from the
+    {0, 1/2}^3 mesh without 0, response basis size NG ~ U[400, 3000] (the
+    cutoff is set from the target count), n_occ ~ U[8, 120], n_unocc ~ NG,
+    3 PAW atoms x 13 projectors; seeds depend on the instance index."""
+    tag = 300 + i
+    rng = np.random.default_rng(seed_of(tag, 0, 9))
+    a = 9.0
+    cell = np.eye(3) * a
+    mesh = [np.array(x, dtype=np.float64) * 0.5 for x in np.ndindex(2, 2, 2)][1:]
+    q = mesh[int(rng.integers(len(mesh)))]
+    ng_target = int(rng.integers(400, 3001))
+    vol = a ** 3
+    ecut_chi = 0.5 * (6.0 * np.pi ** 2 * ng_target / vol) ** (2.0 / 3.0)
+    nocc = int(rng.integers(8, 121))
+    npw_min = min(len(wf_sphere(cell, [0, 0, 0], 20.0)), len(wf_sphere(cell, q, 20.0)))
+    nunocc = int(min(ng_target, npw_min - nocc))
+    sets = [make_orbitals(tag, 0, cell, [0.0, 0.0, 0.0], 20.0, nocc, nunocc),
+            make_orbitals(tag, 1, cell, q, 20.0, nocc, nunocc)]
+    paw = make_paw_setup(tag, [13, 13, 13])
+    for k, s in enumerate(sets):
+        s.P = make_projections(tag, k, s.C.shape[0], int(paw.nproj.sum()))
+    qp = QPoint(q, np.array([0], np.int32), np.array([1], np.int32), np.zeros((1, 3), np.int32), 1.0)
+    return Problem(f"batched-{i}", 3, cell, (40, 40, 40), 20.0, float(ecut_chi), 2.0, 1, sets, [qp], nw, paw)
+
+
 def small_problem(config_tag: int = 90, a: float = 6.0, grid=(12, 12, 12), ecut_wf: float = 4.0,
                   ecut_chi: float = 1.5, nocc: int = 3, nunocc: int = 20, mesh=(2, 1, 1),
                   nproj=(4, 5), nw: int = 8) -> Problem:
