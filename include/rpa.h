@@ -231,6 +231,8 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  * RPA_TUNE_OPERAND_MB  device memory (MiB, >= 16) for the pair densities and
  *                      rank-k operands of one block of occupied bands; larger
  *                      pair sets are processed in several blocks.  Default 6144.
+ * RPA_TUNE_TC_PIPE     tensor-core pipeline shape: 0 (default) 64-element K
+ *                      stages x 2 in shared memory; 1: 32-element stages x 4.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -238,7 +240,8 @@ typedef enum {
   RPA_TUNE_TC_FLUSH = 2,
   RPA_TUNE_PD_GRID = 3,
   RPA_TUNE_OPERAND_MB = 4,
-  RPA_TUNE_COUNT = 5
+  RPA_TUNE_TC_PIPE = 5,
+  RPA_TUNE_COUNT = 6
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

@@ -51,7 +51,7 @@ SIGNATURES = {
     "rpa_graph_launch": (_I, [_P]),
     "rpa_graph_destroy": (None, [_P]),
 }
-RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID, RPA_TUNE_OPERAND_MB = 0, 1, 2, 3, 4
+RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID, RPA_TUNE_OPERAND_MB, RPA_TUNE_TC_PIPE = range(6)
 
 
 class RpaParams(ct.Structure):

@@ -36,13 +36,16 @@ namespace tc {
 
 constexpr int BM = 128;               // tile rows (G_i)
 constexpr int BN = 128;               // tile cols (G_j)
-constexpr int BK = 64;                // bf16 K-elements per stage (128 bytes per row)
-constexpr int STAGES = 2;
-constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB
 constexpr int NUM_THREADS = 320;      // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr uint64_t TIMEOUT_NS = 4000000000ull;  // 4 s per wait
 
-template <int TERMS> struct Cfg {
+// Pipeline shapes: BK bf16 K-elements per stage (64: 128-byte rows with the
+// 128-byte swizzle; 32: 64-byte rows with the 64-byte swizzle) and STAGES
+// stages in the shared-memory ring.
+template <int TERMS, int BK_, int STAGES_> struct Cfg {
+  static constexpr int BK = BK_;
+  static constexpr int STAGES = STAGES_;
+  static constexpr int TILE_BYTES = BM * BK * 2;
   static constexpr int A_TILES = TERMS;             // A hi, (mid), lo
   static constexpr int B_TILES = 2 * TERMS;         // X hi/(mid)/lo, Z hi/(mid)/lo
   static constexpr int STAGE_BYTES = (A_TILES + B_TILES) * TILE_BYTES;
@@ -101,14 +104,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// UMMA shared-memory descriptor of a K-major tile: 8-row core groups of
+// 8 * row-bytes; layout code 2 = 128-byte swizzle (BK = 64), 4 = 64-byte (BK = 32).
+template <int BK>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+  constexpr uint32_t row_bytes = BK * 2;
+  constexpr uint64_t layout = BK == 64 ? 2 : 4;
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address (16-byte units)
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version (tcgen05)
-  d |= (uint64_t)2 << 61;                    // layout: 128-byte swizzle
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);      // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((8 * row_bytes) >> 4) << 32;   // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;                        // descriptor version (tcgen05)
+  d |= layout << 61;
   return d;
 }
 
@@ -159,11 +166,12 @@ struct Maps {
   CUtensorMap z[3];  // Z terms
 };
 
-template <int TERMS>
+template <int TERMS, int BK, int STAGES>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     herk_tc_kernel(const __grid_constant__ Maps maps, int NG, int NGpad, int nk, int fold, int flush, double2* __restrict__ chi,
                    int* __restrict__ err) {
-  using C = Cfg<TERMS>;
+  using C = Cfg<TERMS, BK, STAGES>;
+  constexpr int TILE_BYTES = C::TILE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
@@ -262,9 +270,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           uint64_t da[3], dx[3], dz[3];
 #pragma unroll
           for (int t = 0; t < TERMS; ++t) {
-            da[t] = sw128_desc(st + t * TILE_BYTES + koff);
-            dx[t] = sw128_desc(st + (TERMS + t) * TILE_BYTES + koff);
-            dz[t] = sw128_desc(st + (2 * TERMS + t) * TILE_BYTES + koff);
+            da[t] = kmajor_desc<BK>(st + t * TILE_BYTES + koff);
+            dx[t] = kmajor_desc<BK>(st + (TERMS + t) * TILE_BYTES + koff);
+            dz[t] = kmajor_desc<BK>(st + (2 * TERMS + t) * TILE_BYTES + koff);
           }
           uint32_t acc = (first && kk == 0) ? 0u : 1u;
           // hi*hi, hi*lo, lo*hi  (three terms: + hi*mid, mid*hi, mid*mid, hi*lo, lo*hi)
@@ -470,15 +478,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-static bool make_map(CUtensorMap* m, const void* base, int64_t K, int64_t rows) {
+static bool make_map(CUtensorMap* m, const void* base, int64_t K, int64_t rows, int bk) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(K * 2)};
-  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t box[2] = {(cuuint32_t)bk, BM};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -503,13 +512,29 @@ size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int terms) {
   return op * (size_t)terms * (size_t)(nw + 2);
 }
 
-cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int terms, int fold_stages, int flush_folds,
-                           double2* chi, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
+template <int BK, int STAGES>
+static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpad, int64_t Kpad, int fold64, int flush,
+                               double2* chi, int* err, cudaStream_t s) {
+  using namespace tc;
+  using C = Cfg<2, BK, STAGES>;
+  const int nk = (int)(Kpad / BK);
+  const int fold = fold64 * (64 / BK);  // the fold length is counted in 64-element units
+  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<2, BK, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       C::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  herk_tc_kernel<2, BK, STAGES><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, fold, flush, chi, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int terms, int fold_stages,
+                           int flush_folds, int pipe, double2* chi, void* scratch, size_t scratch_bytes, int* err,
+                           cudaStream_t s) {
   using namespace tc;
   if (P == 0 || NG == 0 || nw == 0) return cudaSuccess;
   if (terms != 2) return cudaErrorInvalidValue;
   if (fold_stages < 1) fold_stages = 1;
   if (flush_folds < 1) flush_folds = 1;
+  const int bk = pipe == 1 ? 32 : 64;
   const Geometry g = geometry(P, NG);
   if (scratch_bytes < herk_tc_scratch_bytes(P, NG, nw, terms)) return cudaErrorInvalidValue;
   if (g.Kpad > (int64_t)1 << 31 || (int64_t)nw * g.NGpad > (1 << 30)) return cudaErrorInvalidValue;
@@ -526,19 +551,15 @@ cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt,
   Maps maps;
   memset(&maps, 0, sizeof(maps));
   for (int t = 0; t < terms; ++t) {
-    if (!make_map(&maps.a[t], A + op_elems * nw * t, g.Kpad, (int64_t)nw * g.NGpad) ||
-        !make_map(&maps.x[t], X + op_elems * t, g.Kpad, g.NGpad) ||
-        !make_map(&maps.z[t], Z + op_elems * t, g.Kpad, g.NGpad))
+    if (!make_map(&maps.a[t], A + op_elems * nw * t, g.Kpad, (int64_t)nw * g.NGpad, bk) ||
+        !make_map(&maps.x[t], X + op_elems * t, g.Kpad, g.NGpad, bk) ||
+        !make_map(&maps.z[t], Z + op_elems * t, g.Kpad, g.NGpad, bk))
       return cudaErrorInvalidValue;
   }
   const int nt = g.NGpad / BM;
   dim3 grid(nt * (nt + 1) / 2, nw);
-  const int nk = (int)(g.Kpad / BK);
-  if ((e = cudaFuncSetAttribute(herk_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Cfg<2>::SMEM_BYTES)) != cudaSuccess)
-    return e;
-  herk_tc_kernel<2><<<grid, NUM_THREADS, Cfg<2>::SMEM_BYTES, s>>>(maps, NG, g.NGpad, nk, fold_stages, flush_folds, chi, err);
-  return cudaGetLastError();
+  if (bk == 32) return launch_gemm<32, 4>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
+  return launch_gemm<64, 2>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
 }
 
 }  // namespace rpa

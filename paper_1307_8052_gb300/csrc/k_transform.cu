@@ -161,6 +161,10 @@ __device__ inline void load_twiddle_matrix(c2<T>* tw, const c2<T>* __restrict__ 
 
 // Each thread owns one (j2, j3) line point and PP consecutive pairs, and keeps
 // all NO outputs g1 of each pair in registers while it streams j1.
+// Twiddle tables are stored with a row stride of TS = 16 outputs; a kernel
+// instance computes NO <= 16 outputs per chunk (NO = 16 for several chunks).
+constexpr int TS = 16;
+
 template <typename T, int NO, int PP>
 __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
                                                         int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
@@ -169,13 +173,13 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
                                                         c2<T>* __restrict__ T1) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
-  const int nchunk = (n1 + NO - 1) / NO;
+  const int nchunk = (n1 + TS - 1) / TS;
   const int ngrp = (np + PP - 1) / PP;
   for (int oc = 0; oc < nchunk; ++oc) {
-    const int o0 = oc * NO;
+    const int o0 = oc * TS;
     const int nout = min(NO, n1 - o0);
     if (oc) __syncthreads();
-    load_twiddle_matrix<T>(tw, twg + (int64_t)oc * N1 * NO, N1 * NO);
+    load_twiddle_matrix<T>(tw, twg + (int64_t)oc * N1 * TS, N1 * TS);
     const int64_t total = (int64_t)ngrp * N23;
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x) {
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
         c2<T> x[PP];
 #pragma unroll
         for (int q = 0; q < PP; ++q) x[q] = cj_mul<T>(un[q][(int64_t)j1 * N23], um[q][(int64_t)j1 * N23]);
-        const c2<T>* twj = tw + j1 * NO;
+        const c2<T>* twj = tw + j1 * TS;
 #pragma unroll
         for (int t = 0; t < NO; ++t) {
           const c2<T> f = twj[t];
@@ -221,15 +225,14 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
   }
 }
 
-template <typename T>
-cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                             const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
-                             cudaStream_t s) {
-  constexpr int NO = 16;
+template <typename T, int NO>
+static cudaError_t launch_stageA_no(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+                                    const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
+                                    cudaStream_t s) {
   constexpr int PP = sizeof(T) == 4 ? 2 : 1;
   const int64_t total = (int64_t)((np + PP - 1) / PP) * N23;
   if (total == 0) return cudaSuccess;
-  const int smem = N1 * NO * (int)sizeof(c2<T>);
+  const int smem = N1 * TS * (int)sizeof(c2<T>);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(pd_stageA_kernel<T, NO, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -239,20 +242,36 @@ cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int 
   return cudaGetLastError();
 }
 
+// compute width: the smallest of 8, 12, 14, 16 that holds all outputs (16 with chunks beyond)
+static inline int width_for(int n) { return n <= 8 ? 8 : n <= 12 ? 12 : n <= 14 ? 14 : 16; }
+
+template <typename T>
+cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+                             const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
+                             cudaStream_t s) {
+  switch (width_for(n1)) {
+    case 8: return launch_stageA_no<T, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+    case 12: return launch_stageA_no<T, 12>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+    case 14: return launch_stageA_no<T, 14>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+    default: return launch_stageA_no<T, 16>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+  }
+}
+
 // ---------------------------------------------------------------- pair density stage B
 // T2[pl][o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i g2 j2 / N2), g2 = g2lo + o2
+// (also used transposed by the adjoint: input axis length N2 -> output axis length n2)
 template <typename T, int NO>
 __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict__ T1, c2<T>* __restrict__ T2,
                                                         int64_t rows, int N2, int N3,
                                                         const c2<T>* __restrict__ twg, int n2) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
-  const int nchunk = (n2 + NO - 1) / NO;
+  const int nchunk = (n2 + TS - 1) / TS;
   for (int oc = 0; oc < nchunk; ++oc) {
-    const int o0 = oc * NO;
+    const int o0 = oc * TS;
     const int nout = min(NO, n2 - o0);
     if (oc) __syncthreads();
-    load_twiddle_matrix<T>(tw, twg + (int64_t)oc * N2 * NO, N2 * NO);
+    load_twiddle_matrix<T>(tw, twg + (int64_t)oc * N2 * TS, N2 * TS);
     const int64_t total = rows * N3;
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x) {
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
       for (int t = 0; t < NO; ++t) acc[t] = mk<T>(0, 0);
       for (int j2 = 0; j2 < N2; ++j2) {
         const c2<T> x = src[(int64_t)j2 * N3];
-        const c2<T>* twj = tw + j2 * NO;
+        const c2<T>* twj = tw + j2 * TS;
 #pragma unroll
         for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x, twj[t]);
       }
@@ -276,19 +295,29 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
   }
 }
 
-template <typename T>
-cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
-                             cudaStream_t s) {
-  constexpr int NO = 16;
-  const int64_t rows = (int64_t)np * n1;
-  if (rows == 0) return cudaSuccess;
-  const int smem = N2 * NO * (int)sizeof(c2<T>);
+template <typename T, int NO>
+static cudaError_t launch_stageB_no(const c2<T>* T1, c2<T>* T2, int64_t rows, int N2, int N3, const c2<T>* tw, int n2,
+                                    cudaStream_t s) {
+  const int smem = N2 * TS * (int)sizeof(c2<T>);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(pd_stageB_kernel<T, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
   pd_stageB_kernel<T, NO><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, tw, n2);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
+                             cudaStream_t s) {
+  const int64_t rows = (int64_t)np * n1;
+  if (rows == 0) return cudaSuccess;
+  switch (width_for(n2)) {
+    case 8: return launch_stageB_no<T, 8>(T1, T2, rows, N2, N3, tw, n2, s);
+    case 12: return launch_stageB_no<T, 12>(T1, T2, rows, N2, N3, tw, n2, s);
+    case 14: return launch_stageB_no<T, 14>(T1, T2, rows, N2, N3, tw, n2, s);
+    default: return launch_stageB_no<T, 16>(T1, T2, rows, N2, N3, tw, n2, s);
+  }
 }
 
 // ---------------------------------------------------------------- pair density stage C (+ PAW)

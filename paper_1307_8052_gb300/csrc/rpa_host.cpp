@@ -18,8 +18,8 @@
 
 namespace rpa {
 cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms,
-                           int fold_stages, int flush_folds, double2* chi, void* scratch, size_t scratch_bytes,
-                           int* err, cudaStream_t s);
+                           int fold_stages, int flush_folds, int pipe, double2* chi, void* scratch,
+                           size_t scratch_bytes, int* err, cudaStream_t s);
 size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
 // adjoint kernels (k_adjoint.cu)
 cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
@@ -121,7 +121,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -530,8 +530,8 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
       const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
       if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
       CUDA_OK(c, launch_herk_tc((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms,
-                                (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH], chi, scr, sb,
-                                c->dev_err, c->stream));
+                                (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH],
+                                (int)c->tune[RPA_TUNE_TC_PIPE], chi, scr, sb, c->dev_err, c->stream));
     }
   }
   return RPA_OK;
@@ -1481,6 +1481,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_PD_GRID:
       if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "transform grid choice must be 0 or 1");
+      break;
+    case RPA_TUNE_TC_PIPE:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "tensor-core pipeline shape must be 0 or 1");
       break;
     case RPA_TUNE_OPERAND_MB:
       if (value < 16 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "operand budget %lld MB out of range", (long long)value);
