@@ -199,10 +199,24 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
       for (int q = 0; q < PP; ++q)
 #pragma unroll
         for (int t = 0; t < NO; ++t) acc[q][t] = mk<T>(0, 0);
+      // the next j1 slice of both grids is loaded while the current one is used
+      c2<T> nxt_n[PP], nxt_m[PP];
+#pragma unroll
+      for (int q = 0; q < PP; ++q) {
+        nxt_n[q] = un[q][0];
+        nxt_m[q] = um[q][0];
+      }
       for (int j1 = 0; j1 < N1; ++j1) {
         c2<T> x[PP];
 #pragma unroll
-        for (int q = 0; q < PP; ++q) x[q] = cj_mul<T>(un[q][(int64_t)j1 * N23], um[q][(int64_t)j1 * N23]);
+        for (int q = 0; q < PP; ++q) x[q] = cj_mul<T>(nxt_n[q], nxt_m[q]);
+        if (j1 + 1 < N1) {
+#pragma unroll
+          for (int q = 0; q < PP; ++q) {
+            nxt_n[q] = un[q][(int64_t)(j1 + 1) * N23];
+            nxt_m[q] = um[q][(int64_t)(j1 + 1) * N23];
+          }
+        }
         const c2<T>* twj = tw + j1 * TS;
 #pragma unroll
         for (int t = 0; t < NO; ++t) {
@@ -281,8 +295,10 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
       c2<T> acc[NO];
 #pragma unroll
       for (int t = 0; t < NO; ++t) acc[t] = mk<T>(0, 0);
+      c2<T> nxt = src[0];
       for (int j2 = 0; j2 < N2; ++j2) {
-        const c2<T> x = src[(int64_t)j2 * N3];
+        const c2<T> x = nxt;
+        if (j2 + 1 < N2) nxt = src[(int64_t)(j2 + 1) * N3];
         const c2<T>* twj = tw + j2 * TS;
 #pragma unroll
         for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x, twj[t]);
@@ -328,36 +344,62 @@ __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict_
                                                         const c2<T>* __restrict__ Pm, int KP,
                                                         const int* __restrict__ Ridx, int nR, int64_t p0,
                                                         c2<T>* __restrict__ Nout) {
+  // Each thread handles one G and PG consecutive pairs: the fastest-axis DFT
+  // runs per pair, the PAW factor R_n(kp, G) is loaded once for the pairs that
+  // share the occupied band n.
+  constexpr int PG = 4;
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
   fill_twiddles<T>(tw, N3);
-  const int64_t total = (int64_t)np * NG;
+  const int ngrp = (np + PG - 1) / PG;
+  const int64_t total = (int64_t)ngrp * NG;
   const T scale = (T)inv_nr;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
        id += (int64_t)gridDim.x * blockDim.x) {
     const int ig = (int)(id % NG);
-    const int pl = (int)(id / NG);
+    const int grp = (int)(id / NG);
     const int g1 = gfft[3 * ig], g2 = gfft[3 * ig + 1], g3 = gfft[3 * ig + 2];
-    const c2<T>* src = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
     const int step = pmod(-(int64_t)g3, N3);
-    int idx = 0;
-    c2<T> acc = mk<T>(0, 0);
-    for (int j3 = 0; j3 < N3; ++j3) {
-      cmac<T>(acc, src[j3], tw[idx]);
-      idx += step;
-      if (idx >= N3) idx -= N3;
+    c2<T> acc[PG];
+    int64_t pidx[PG];
+#pragma unroll
+    for (int q = 0; q < PG; ++q) {
+      const int pl = min(grp * PG + q, np - 1);
+      pidx[q] = p0 + pl;
+      const c2<T>* src = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
+      int idx = 0;
+      c2<T> s = mk<T>(0, 0);
+      for (int j3 = 0; j3 < N3; ++j3) {
+        cmac<T>(s, src[j3], tw[idx]);
+        idx += step;
+        if (idx >= N3) idx -= N3;
+      }
+      acc[q] = mk<T>(s.x * scale, s.y * scale);
     }
-    acc.x *= scale;
-    acc.y *= scale;
-    const int64_t p = p0 + pl;
     if (KP > 0) {
-      const int64_t a = p / nR;
-      const int64_t b = p % nR;
-      const c2<T>* pm = Pm + b * KP;
-      const c2<T>* rr = R + a * (int64_t)KP * NG + ig;
-      for (int kp = 0; kp < KP; ++kp) cmac<T>(acc, pm[kp], rr[(int64_t)kp * NG]);
+      const int64_t a0 = pidx[0] / nR;
+      bool same = true;
+#pragma unroll
+      for (int q = 1; q < PG; ++q) same = same && (pidx[q] / nR == a0);
+      if (same) {
+        const c2<T>* rr = R + a0 * (int64_t)KP * NG + ig;
+        for (int kp = 0; kp < KP; ++kp) {
+          const c2<T> r = rr[(int64_t)kp * NG];
+#pragma unroll
+          for (int q = 0; q < PG; ++q) cmac<T>(acc[q], Pm[(pidx[q] % nR) * KP + kp], r);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < PG; ++q) {
+          const c2<T>* rr = R + (pidx[q] / nR) * (int64_t)KP * NG + ig;
+          const c2<T>* pm = Pm + (pidx[q] % nR) * KP;
+          for (int kp = 0; kp < KP; ++kp) cmac<T>(acc[q], pm[kp], rr[(int64_t)kp * NG]);
+        }
+      }
     }
-    Nout[p * NG + ig] = acc;
+#pragma unroll
+    for (int q = 0; q < PG; ++q)
+      if (grp * PG + q < np) Nout[pidx[q] * NG + ig] = acc[q];
   }
 }
 
@@ -365,7 +407,7 @@ template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft, int NG, int g1lo,
                              int g2lo, double inv_nr, const c2<T>* R, const c2<T>* Pm, int KP, const int* Ridx,
                              int nR, int64_t p0, c2<T>* Nout, cudaStream_t s) {
-  const int64_t total = (int64_t)np * NG;
+  const int64_t total = (int64_t)((np + 3) / 4) * NG;
   if (total == 0) return cudaSuccess;
   pd_stageC_kernel<T><<<grid_for(total, 256), 256, N3 * sizeof(c2<T>), s>>>(T2, np, n1, n2, N3, gfft, NG, g1lo, g2lo,
                                                                           inv_nr, R, Pm, KP, Ridx, nR, p0, Nout);
