@@ -233,6 +233,10 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      pair sets are processed in several blocks.  Default 6144.
  * RPA_TUNE_TC_PIPE     tensor-core pipeline shape: 0 (default) 64-element K
  *                      stages x 2 in shared memory; 1: 32-element stages x 4.
+ * RPA_TUNE_LOGDET      arithmetic of the Cholesky trailing updates in the
+ *                      RPA_FP32 and RPA_BF16X2 modes: 1 (default) float-float
+ *                      (pairs of FP32, about 44 significant bits; the matrix
+ *                      stays FP64), 0: FP64.  RPA_FP64 always uses FP64.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -241,7 +245,8 @@ typedef enum {
   RPA_TUNE_PD_GRID = 3,
   RPA_TUNE_OPERAND_MB = 4,
   RPA_TUNE_TC_PIPE = 5,
-  RPA_TUNE_COUNT = 6
+  RPA_TUNE_LOGDET = 6,
+  RPA_TUNE_COUNT = 7
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 
@@ -259,7 +264,7 @@ rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
  * `stream` (a cudaStream_t; NULL = the legacy default stream) of the current
  * device, and the call returns after that stream has finished it.
  *
- * Scratch: one process-wide static device array per device (16 MiB + 2 KiB,
+ * Scratch: one process-wide static device array per device (17 MiB + 2 KiB,
  * held until the process exits).  Limits: 1 <= nw <= 64 and
  * nw * ng * ng <= 1048576 (e.g. ng <= 256 at nw = 16); larger sizes, null or
  * host pointers return RPA_ERR_ARG without touching the GPU.  The first call on

@@ -51,7 +51,8 @@ SIGNATURES = {
     "rpa_graph_launch": (_I, [_P]),
     "rpa_graph_destroy": (None, [_P]),
 }
-RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID, RPA_TUNE_OPERAND_MB, RPA_TUNE_TC_PIPE = range(6)
+(RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID, RPA_TUNE_OPERAND_MB, RPA_TUNE_TC_PIPE,
+ RPA_TUNE_LOGDET) = range(7)
 
 
 class RpaParams(ct.Structure):

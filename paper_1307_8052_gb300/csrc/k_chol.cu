@@ -51,85 +51,185 @@ __global__ void trace_kernel(const double2* __restrict__ chi, const double* __re
   if (threadIdx.x == 0) trace[w] = red[0];
 }
 
+// ---------------------------------------------------------------- float-float trailing update
+// The trailing update dominates the factorisation (NG^3/6 complex
+// multiply-adds per frequency).  GB300 issues FP32 FMAs about 70 times as fast
+// as FP64 ones, so the mixed-precision modes evaluate it in float-float
+// arithmetic: each value is the unevaluated sum hi + lo of two FP32 numbers
+// (Dekker's exact product via FMA and Knuth's two-sum), about 44 significant
+// bits.  The matrix itself stays in FP64; only the panel sums of one update
+// are float-float.  The _rn intrinsics keep the compiler from contracting the
+// steps into FMAs, which would break the exact error terms.
+__device__ __forceinline__ float4 ff_split(double2 x) {
+  const float rh = __double2float_rn(x.x), ih = __double2float_rn(x.y);
+  return make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
+}
+
+// (sh, sl) += (xh, xl) * (yh, yl)
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = __fmaf_rn(xh, yh, -p);  // p + e == xh * yh exactly
+  e = __fmaf_rn(xh, yl, e);
+  e = __fmaf_rn(xl, yh, e);
+  const float t = __fadd_rn(sh, p);  // t + d == sh + p exactly
+  const float z = __fsub_rn(t, sh);
+  const float d = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(d, e));
+}
+
+// 1/sqrt(x) for a pivot x > 0: a single-precision estimate refined by two
+// Newton steps y <- y (3 - x y^2) / 2 in FP64 (quadratic convergence from
+// about 2^-22 to full precision).  One short dependent chain replaces a square
+// root followed by a division on the serial path of the panel factorisation.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+  y = y * fma(-hx, y * y, 1.5);
+  y = y * fma(-hx, y * y, 1.5);
+  return y;
+}
+
+// One CTA per frequency factorises the b x b diagonal block in place, adds
+// the logs of its pivots to logdet[w] (ln det A = sum_i ln L_ii^2) and writes
+// the inverse of the factor to Linv[w] (CB x CB, lower triangle, zero above).
+// Every column step is parallel over the CTA: the column of L is scaled, then
+// the Schur complement and the forward substitution for L^-1 (right-hand side
+// I) are updated together; the logs are taken once at the end.
 __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A, int NG, int k0, int b,
-                                                        double* __restrict__ logdet, int* __restrict__ flag) {
+                                                        double* __restrict__ logdet, int* __restrict__ flag,
+                                                        double2* __restrict__ Linv) {
   __shared__ double2 L[CB][CB + 1];
-  __shared__ double ld;
-  const int w = blockIdx.x;
+  __shared__ double2 X[CB][CB + 1];  // right-hand side I, then L^-1
+  __shared__ double piv_s[CB];
+  __shared__ double dinv_s;
+  const int w = blockIdx.x, tid = threadIdx.x;
   double2* Aw = A + (int64_t)w * NG * NG;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e % b;
-    if (j <= i) L[i][j] = Aw[(int64_t)(k0 + i) * NG + k0 + j];
+  for (int e = tid; e < CB * CB; e += blockDim.x) {
+    const int i = e / CB, j = e % CB;
+    L[i][j] = (i < b && j <= i) ? Aw[(int64_t)(k0 + i) * NG + k0 + j] : make_double2(0.0, 0.0);
+    X[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
-  if (threadIdx.x == 0) ld = 0.0;
   __syncthreads();
   for (int c = 0; c < b; ++c) {
-    if (threadIdx.x == 0) {
+    // one thread takes the pivot (the FP64 pipe retires only a few lanes per
+    // clock, so the other threads must not repeat the square root)
+    if (tid == 0) {
       double piv = L[c][c].x;
       if (!(piv > 0.0)) {
         atomicExch(flag, 1);
         piv = 1.0;
       }
-      ld += log(piv);
-      L[c][c] = make_double2(sqrt(piv), 0.0);
+      piv_s[c] = piv;
+      dinv_s = rsqrt_newton(piv);
     }
     __syncthreads();
-    const double dinv = 1.0 / L[c][c].x;
-    for (int i = c + 1 + threadIdx.x; i < b; i += blockDim.x) {
-      L[i][c].x *= dinv;
-      L[i][c].y *= dinv;
+    const double dinv = dinv_s, piv = piv_s[c];
+    if (tid < CB) {
+      if (tid > c && tid < b) {
+        L[tid][c].x *= dinv;
+        L[tid][c].y *= dinv;
+      } else if (tid == c) {
+        L[c][c] = make_double2(piv * dinv, 0.0);
+      }
+    } else if (tid < 2 * CB && tid - CB <= c) {
+      X[c][tid - CB].x *= dinv;
+      X[c][tid - CB].y *= dinv;
     }
     __syncthreads();
+    // The FP64 pipe retires a warp instruction in many cycles whatever its
+    // active lanes, so the useful elements are enumerated densely: first the
+    // Schur complement triangle (c < j <= i < b), then the m x (c+1) block of
+    // the forward substitution.
     const int m = b - c - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = c + 1 + e / m, j = c + 1 + e % m;
-      if (j <= i) {
+    const int ntri = m * (m + 1) / 2;
+    for (int e = tid; e < ntri + m * (c + 1); e += blockDim.x) {
+      if (e < ntri) {
+        int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while (r * (r + 1) / 2 > e) --r;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        const int i = c + 1 + r, j = c + 1 + (e - r * (r + 1) / 2);
+        // Schur complement: L_ij -= L_ic conj(L_jc)
         const double2 x = L[i][c], y = L[j][c];
-        // L_ij -= x * conj(y)
         L[i][j].x -= x.x * y.x + x.y * y.y;
         L[i][j].y -= x.y * y.x - x.x * y.y;
+      } else {
+        const int f = e - ntri;
+        const int i = c + 1 + f / (c + 1), j = f % (c + 1);
+        // forward substitution: X_ij -= L_ic X_cj
+        const double2 x = L[i][c], y = X[c][j];
+        X[i][j].x -= x.x * y.x - x.y * y.y;
+        X[i][j].y -= x.x * y.y + x.y * y.x;
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e % b;
-    if (j <= i) Aw[(int64_t)(k0 + i) * NG + k0 + j] = L[i][j];
+  if (tid < 32) {
+    double ld = tid < b ? log(piv_s[tid]) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
+    if (tid == 0) logdet[w] += ld;
   }
-  if (threadIdx.x == 0) logdet[w] += ld;
+  double2* Lw = Linv + (int64_t)w * CB * CB;
+  for (int e = tid; e < CB * CB; e += blockDim.x) {
+    const int i = e / CB, j = e % CB;
+    Lw[e] = (i < b && j <= i) ? X[i][j] : make_double2(0.0, 0.0);
+    if (i < b && j <= i) Aw[(int64_t)(k0 + i) * NG + k0 + j] = L[i][j];
+  }
 }
 
-constexpr int TR = 32;  // rows per triangular-solve CTA
+// Panel below the diagonal block: X = A_panel L_kk^-H, i.e.
+// x_rj = sum_{l <= j} a_rl conj(Linv_jl).  16 threads per row, each owning
+// columns j and b-1-j so that every thread does b+1 multiply-adds; FF selects
+// float-float arithmetic (inputs and result stay FP64).
+constexpr int TROWS = 16;  // rows per triangular-solve CTA
 
-__global__ void __launch_bounds__(TR) chol_trsm_kernel(double2* __restrict__ A, int NG, int k0, int b) {
-  __shared__ double2 Lk[CB][CB + 1];
-  __shared__ double2 X[TR][CB + 1];
+template <bool FF>
+__global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A, int NG, int k0, int b,
+                                                        const double2* __restrict__ Linv) {
+  using E = typename std::conditional<FF, float4, double2>::type;
+  __shared__ E Li[CB][CB + 1];
+  __shared__ E X[TROWS][CB + 1];
   const int w = blockIdx.y;
   double2* Aw = A + (int64_t)w * NG * NG;
-  const int i0 = k0 + b + blockIdx.x * TR;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e % b;
-    Lk[i][j] = (j <= i) ? Aw[(int64_t)(k0 + i) * NG + k0 + j] : make_double2(0.0, 0.0);
+  const double2* Lw = Linv + (int64_t)w * CB * CB;
+  const int i0 = k0 + b + blockIdx.x * TROWS;
+  for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+    const double2 v = Lw[e];
+    if constexpr (FF) Li[e / CB][e % CB] = ff_split(v); else Li[e / CB][e % CB] = v;
   }
-  for (int e = threadIdx.x; e < TR * b; e += blockDim.x) {
-    const int r = e / b, j = e % b;
-    X[r][j] = (i0 + r < NG) ? Aw[(int64_t)(i0 + r) * NG + k0 + j] : make_double2(0.0, 0.0);
+  for (int e = threadIdx.x; e < TROWS * CB; e += blockDim.x) {
+    const int r = e / CB, l = e % CB;
+    const double2 v = (i0 + r < NG && l < b) ? Aw[(int64_t)(i0 + r) * NG + k0 + l] : make_double2(0.0, 0.0);
+    if constexpr (FF) X[r][l] = ff_split(v); else X[r][l] = v;
   }
   __syncthreads();
-  const int r = threadIdx.x;
-  if (i0 + r < NG) {
-    // solve x L^H = a: x_j = (a_j - sum_{l<j} x_l conj(L_jl)) / L_jj
-    for (int j = 0; j < b; ++j) {
-      double2 s = X[r][j];
-      for (int l = 0; l < j; ++l) {
-        const double2 x = X[r][l], y = Lk[j][l];
-        s.x -= x.x * y.x + x.y * y.y;
-        s.y -= x.y * y.x - x.x * y.y;
+  const int r = threadIdx.x >> 4, t = threadIdx.x & 15;
+  const int row = i0 + r;
+  if (row >= NG) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    // t owns column t when t <= b-1-t, and column b-1-t when that lies above t
+    const int j = h == 0 ? t : b - 1 - t;
+    if (h == 0 ? 2 * t > b - 1 : j <= t) continue;
+    double2 out;
+    if constexpr (FF) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int l = 0; l <= j; ++l) {
+        const float4 a = X[r][l], y = Li[j][l];
+        ff_mac(s.x, s.y, a.x, a.y, y.x, y.y);
+        ff_mac(s.x, s.y, a.z, a.w, y.z, y.w);
+        ff_mac(s.z, s.w, a.z, a.w, y.x, y.y);
+        ff_mac(s.z, s.w, -a.x, -a.y, y.z, y.w);
       }
-      const double dinv = 1.0 / Lk[j][j].x;
-      X[r][j] = make_double2(s.x * dinv, s.y * dinv);
+      out = make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
+    } else {
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = 0; l <= j; ++l) cmac_cj<double>(s, X[r][l], Li[j][l]);
+      out = s;
     }
-    for (int j = 0; j < b; ++j) Aw[(int64_t)(i0 + r) * NG + k0 + j] = X[r][j];
+    Aw[(int64_t)row * NG + k0 + j] = out;
   }
 }
 
@@ -189,6 +289,69 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double2* __restrict__ 
     }
 }
 
+// Float-float trailing update on 32 x 32 tiles of 64 threads (4 x 4 outputs
+// each): the float-float accumulators take 167 registers a thread, and small
+// CTAs let six of them share an SM so that twelve warps hide the latency of
+// the dependent two-sum steps.
+constexpr int UTF = 32;
+
+__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b) {
+  __shared__ float4 Li[CB][UTF];
+  __shared__ float4 Lj[CB][UTF];
+  const int w = blockIdx.y;
+  double2* Aw = A + (int64_t)w * NG * NG;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int s0 = k0 + b;
+  const int r0 = s0 + ti * UTF, c0 = s0 + tj * UTF;
+  for (int e = threadIdx.x; e < b * UTF; e += blockDim.x) {
+    const int rr = e / b, l = e % b;
+    const double2 z = make_double2(0.0, 0.0);
+    Li[l][rr] = ff_split((r0 + rr < NG) ? Aw[(int64_t)(r0 + rr) * NG + k0 + l] : z);
+    Lj[l][rr] = ff_split((c0 + rr < NG) ? Aw[(int64_t)(c0 + rr) * NG + k0 + l] : z);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  // acc[r][c] = (re hi, re lo, im hi, im lo) of sum_l L_il conj(L_jl)
+  float4 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+  for (int l = 0; l < b; ++l) {
+    float4 y[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] = Lj[l][tx + 8 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 a = Li[l][ty + 8 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float4& s = acc[r][c];
+        // a * conj(y): re = ar yr + ai yi, im = ai yr - ar yi
+        ff_mac(s.x, s.y, a.x, a.y, y[c].x, y[c].y);
+        ff_mac(s.x, s.y, a.z, a.w, y[c].z, y[c].w);
+        ff_mac(s.z, s.w, a.z, a.w, y[c].x, y[c].y);
+        ff_mac(s.z, s.w, -a.x, -a.y, y[c].z, y[c].w);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int row = r0 + ty + 8 * r, col = c0 + tx + 8 * c;
+      if (row < NG && col < NG && col <= row) {
+        double2* p = Aw + (int64_t)row * NG + col;
+        double2 v = *p;
+        v.x -= (double)acc[r][c].x + (double)acc[r][c].y;
+        v.y -= (double)acc[r][c].z + (double)acc[r][c].w;
+        *p = v;
+      }
+    }
+}
+
 __global__ void add_terms_kernel(const double* __restrict__ ld, const double* __restrict__ tr, int nw,
                                  double* __restrict__ terms) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,8 +363,10 @@ static inline int gridc(int64_t n) {
   return (int)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
 }
 
+int64_t logdet_work_elems(int nw, int NG) { return (int64_t)nw * NG * NG + (int64_t)nw * CB * CB; }
+
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work, double* logdet,
-                       double* trace, int* flag, cudaStream_t s, int64_t* launches) {
+                       double* trace, int* flag, bool ff_update, cudaStream_t s, int64_t* launches) {
   cudaError_t e;
   int64_t nl = 0;
   const int upd_smem = 2 * CB * UT * (int)sizeof(double2);
@@ -210,6 +375,7 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
     return e;
   if ((e = cudaMemsetAsync(logdet, 0, sizeof(double) * nw, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return e;
+  double2* Linv = work + (int64_t)nw * NG * NG;  // [nw][CB][CB]
   const int64_t total = (int64_t)nw * NG * NG;
   chol_form_kernel<<<gridc(total), 256, 0, s>>>(chi, v, nw, NG, work);
   trace_kernel<<<nw, 256, 0, s>>>(chi, v, NG, trace);
@@ -217,13 +383,20 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int k0 = 0; k0 < NG; k0 += CB) {
     const int b = (NG - k0) < CB ? (NG - k0) : CB;
-    chol_diag_kernel<<<nw, 256, 0, s>>>(work, NG, k0, b, logdet, flag);
+    chol_diag_kernel<<<nw, 256, 0, s>>>(work, NG, k0, b, logdet, flag, Linv);
     ++nl;
     const int rest = NG - k0 - b;
     if (rest > 0) {
-      chol_trsm_kernel<<<dim3((rest + TR - 1) / TR, nw), TR, 0, s>>>(work, NG, k0, b);
-      const int nt = (rest + UT - 1) / UT;
-      chol_update_kernel<<<dim3(nt * (nt + 1) / 2, nw), 256, upd_smem, s>>>(work, NG, k0, b);
+      const dim3 tg((rest + TROWS - 1) / TROWS, nw);
+      if (ff_update) {
+        chol_trsm_kernel<true><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv);
+        const int nt = (rest + UTF - 1) / UTF;
+        chol_update_ff_kernel<<<dim3(nt * (nt + 1) / 2, nw), 64, 0, s>>>(work, NG, k0, b);
+      } else {
+        chol_trsm_kernel<false><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv);
+        const int nt = (rest + UT - 1) / UT;
+        chol_update_kernel<<<dim3(nt * (nt + 1) / 2, nw), 256, upd_smem, s>>>(work, NG, k0, b);
+      }
       nl += 2;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -234,12 +407,14 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
 
 // ---------------------------------------------------------------- allocation-free entry point
 // Scratch of rpa_logdet_noalloc: the Cholesky work matrix (up to
-// kNoAllocMaxElems complex elements) followed by the per-frequency log-det and
-// trace accumulators and the pivot flag.  It lives for the life of the process
-// on every device that loads the library (16 MiB + 2 KiB).
+// kNoAllocMaxElems complex elements), the inverses of the diagonal blocks (CB^2
+// per frequency), the per-frequency log-det and trace accumulators and the
+// pivot flag.  It lives for the life of the process on every device that loads
+// the library (17 MiB + 2 KiB).
 constexpr int64_t kNoAllocMaxElems = (int64_t)1 << 20;
 constexpr int kNoAllocMaxNw = 64;
-constexpr int64_t kNoAllocSlots = kNoAllocMaxElems + kNoAllocMaxNw + 1;  // double2 slots
+constexpr int64_t kNoAllocLinv = (int64_t)kNoAllocMaxNw * CB * CB;
+constexpr int64_t kNoAllocSlots = kNoAllocMaxElems + kNoAllocLinv + kNoAllocMaxNw + 1;  // double2 slots
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
 
 }  // namespace rpa
@@ -286,12 +461,12 @@ extern "C" rpa_status rpa_logdet_noalloc(const double* chi, const double* v, int
   }
   cudaStream_t s = (cudaStream_t)stream;
   double2* work = (double2*)base;
-  double* ld = (double*)(work + kNoAllocMaxElems);
+  double* ld = (double*)(work + kNoAllocMaxElems + kNoAllocLinv);  // past the matrix and the block inverses
   double* tr = ld + kNoAllocMaxNw;
   int* flag = (int*)(tr + kNoAllocMaxNw);
   // run_logdet clears the log-det accumulators and the flag itself; the work
   // matrix is fully rewritten from chi before it is read
-  if (run_logdet((const double2*)chi, v, nw, ng, work, ld, tr, flag, s, nullptr) != cudaSuccess) return RPA_ERR_CUDA;
+  if (run_logdet((const double2*)chi, v, nw, ng, work, ld, tr, flag, false, s, nullptr) != cudaSuccess) return RPA_ERR_CUDA;
   add_terms_kernel<<<(nw + 63) / 64, 64, 0, s>>>(ld, tr, nw, terms);
   if (cudaGetLastError() != cudaSuccess) return RPA_ERR_CUDA;
   int h_flag = 0;

@@ -121,7 +121,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 1};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -257,6 +257,9 @@ void prof_end(rpa_ctx* c) {
   }
   c->ev.clear();
 }
+
+// float-float trailing updates of the log-det in the mixed-precision modes
+bool ff_logdet(const rpa_ctx* c) { return c->prm.precision != RPA_FP64 && c->tune[RPA_TUNE_LOGDET] == 1; }
 
 int work_bytes_per_complex(const rpa_ctx* c) { return c->prm.precision == RPA_FP64 ? 16 : 8; }
 
@@ -589,11 +592,11 @@ rpa_status energy_enqueue(rpa_ctx* c, int nq, const int* iqs, int nw, const doub
     if ((st = build_chi_async(c, iqs[i], nw, omega_d, &chi)) != RPA_OK) return st;
     QPt& Q = c->qpts[iqs[i]];
     void* p_work;
-    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)nw * Q.NG * Q.NG, &p_work)) != RPA_OK) return st;
+    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw, Q.NG), &p_work)) != RPA_OK) return st;
     int64_t nl = 0;
     StageTimer tm(c, 3, 0);
     CUDA_OK(c, run_logdet(chi, Q.v_d, nw, Q.NG, (double2*)p_work, (double*)p_ld + (size_t)i * nw,
-                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, c->stream, &nl));
+                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, ff_logdet(c), c->stream, &nl));
     tm.add_launches(nl);
   }
   c->enq_iqs.assign(iqs, iqs + nq);
@@ -810,7 +813,7 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     const int NG = Q.NG;
     const size_t mat = sizeof(double2) * (size_t)nw * NG * NG;
     void *p_work, *p_ld, *p_tr, *p_flag, *p_Y, *p_W, *p_G64, *p_G32 = nullptr, *p_cw;
-    if ((st = workspace(c, "chol", mat, &p_work)) != RPA_OK) return st;
+    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw, NG), &p_work)) != RPA_OK) return st;
     if ((st = workspace(c, "logdet", sizeof(double) * nw, &p_ld)) != RPA_OK) return st;
     if ((st = workspace(c, "trace", sizeof(double) * nw, &p_tr)) != RPA_OK) return st;
     if ((st = workspace(c, "flag", sizeof(int), &p_flag)) != RPA_OK) return st;
@@ -823,7 +826,7 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     {
       StageTimer tm(c, 3, 0);
       CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
-                            c->stream, &nl));
+                            ff_logdet(c), c->stream, &nl));
       tm.add_launches(nl);
     }
     int flag = 0;
@@ -1484,6 +1487,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_TC_PIPE:
       if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "tensor-core pipeline shape must be 0 or 1");
+      break;
+    case RPA_TUNE_LOGDET:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "log-det update arithmetic must be 0 or 1");
       break;
     case RPA_TUNE_OPERAND_MB:
       if (value < 16 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "operand budget %lld MB out of range", (long long)value);

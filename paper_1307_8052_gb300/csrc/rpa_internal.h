@@ -98,9 +98,15 @@ cudaError_t launch_herk_simt_w(const c2<T>* N, int64_t P, int NG, const T* wgt, 
 // Upper triangle from lower: chi[w][i][j] = conj(chi[w][j][i]) for i < j.
 cudaError_t launch_hermitian_fill(double2* chi, int nw, int NG, cudaStream_t s);
 
-// FP64 log-det of 1 - v^1/2 chi v^1/2 by blocked Cholesky, batched over w.
-// Returns per-w e(w) = ln det + tr in eout (device), error flag in flag.
+// Complex elements of the work buffer run_logdet needs: the factor and the
+// inverses of its diagonal blocks.
+int64_t logdet_work_elems(int nw, int NG);
+
+// Log-det of 1 - v^1/2 chi v^1/2 by blocked Cholesky in FP64, batched over w:
+// per-w ln det in logdet, tr(v^1/2 chi v^1/2) in trace, pivot failure in flag.
+// ff_update evaluates the trailing updates in float-float arithmetic.
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work,
-                       double* logdet, double* trace, int* flag, cudaStream_t s, int64_t* launches);
+                       double* logdet, double* trace, int* flag, bool ff_update, cudaStream_t s,
+                       int64_t* launches);
 
 }  // namespace rpa
