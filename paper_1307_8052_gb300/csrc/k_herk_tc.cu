@@ -36,7 +36,8 @@ namespace tc {
 
 constexpr int BM = 128;               // tile rows (G_i)
 constexpr int BN = 128;               // tile cols (G_j)
-constexpr int NUM_THREADS = 320;      // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int EPI_WARPS = 16;         // epilogue warps: 4 per TMEM lane quarter
+constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr uint64_t TIMEOUT_NS = 4000000000ull;  // 4 s per wait
 
 // Pipeline shapes: BK bf16 K-elements per stage (64: 128-byte rows with the
@@ -47,7 +48,7 @@ template <int TERMS, int BK_, int STAGES_> struct Cfg {
   static constexpr int STAGES = STAGES_;
   static constexpr int TILE_BYTES = BM * BK * 2;
   static constexpr int A_TILES = TERMS;             // A hi, (mid), lo
-  static constexpr int B_TILES = 2 * TERMS;         // X hi/(mid)/lo, Z hi/(mid)/lo
+  static constexpr int B_TILES = 2 * TERMS;         // per term X then Z: one 256-row B operand
   static constexpr int STAGE_BYTES = (A_TILES + B_TILES) * TILE_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
@@ -137,19 +138,18 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], 32 * EPI_WARPS);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         for (int t = 0; t < TERMS; ++t) tma_load_2d(st + t * TILE_BYTES, &maps.a[t], &full[s], k, w * NGpad + i0);
 #pragma unroll
         for (int t = 0; t < TERMS; ++t) {
-          tma_load_2d(st + (TERMS + t) * TILE_BYTES, &maps.x[t], &full[s], k, j0);
-          tma_load_2d(st + (2 * TERMS + t) * TILE_BYTES, &maps.z[t], &full[s], k, j0);
+          tma_load_2d(st + (TERMS + 2 * t) * TILE_BYTES, &maps.x[t], &full[s], k, j0);
+          tma_load_2d(st + (TERMS + 2 * t + 1) * TILE_BYTES, &maps.z[t], &full[s], k, j0);
         }
         issued = kb + 1;
       }
@@ -244,7 +244,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      // N = 256: the B operand is X (rows 0-127, giving Re) stacked on Z
+      // (rows 128-255, giving Im), so one MMA fills both accumulators
+      constexpr uint32_t idesc = idesc_bf16(BM, 2 * BN);
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % STAGES;
         if (!mbar_wait(&full[s], (kb / STAGES) & 1, abort_flag)) {
@@ -262,33 +264,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
-        const uint32_t d_re = tmem + b * 256;
-        const uint32_t d_im = tmem + b * 256 + 128;
+        const uint32_t d = tmem + b * 256;  // Re in columns 0-127, Im in 128-255
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
-          uint64_t da[3], dx[3], dz[3];
+          uint64_t da[3], db[3];
 #pragma unroll
           for (int t = 0; t < TERMS; ++t) {
             da[t] = kmajor_desc<BK>(st + t * TILE_BYTES + koff);
-            dx[t] = kmajor_desc<BK>(st + (TERMS + t) * TILE_BYTES + koff);
-            dz[t] = kmajor_desc<BK>(st + (2 * TERMS + t) * TILE_BYTES + koff);
+            db[t] = kmajor_desc<BK>(st + (TERMS + 2 * t) * TILE_BYTES + koff);
           }
-          uint32_t acc = (first && kk == 0) ? 0u : 1u;
+          const uint32_t acc = (first && kk == 0) ? 0u : 1u;
           // hi*hi, hi*lo, lo*hi  (three terms: + hi*mid, mid*hi, mid*mid, hi*lo, lo*hi)
-          umma(d_re, da[0], dx[0], idesc, acc);
-          umma(d_im, da[0], dz[0], idesc, acc);
-          umma(d_re, da[0], dx[1], idesc, 1u);
-          umma(d_im, da[0], dz[1], idesc, 1u);
-          umma(d_re, da[1], dx[0], idesc, 1u);
-          umma(d_im, da[1], dz[0], idesc, 1u);
+          umma(d, da[0], db[0], idesc, acc);
+          umma(d, da[0], db[1], idesc, 1u);
+          umma(d, da[1], db[0], idesc, 1u);
           if (TERMS == 3) {
-            umma(d_re, da[1], dx[1], idesc, 1u);
-            umma(d_im, da[1], dz[1], idesc, 1u);
-            umma(d_re, da[0], dx[2], idesc, 1u);
-            umma(d_im, da[0], dz[2], idesc, 1u);
-            umma(d_re, da[2], dx[0], idesc, 1u);
-            umma(d_im, da[2], dz[0], idesc, 1u);
+            umma(d, da[1], db[1], idesc, 1u);
+            umma(d, da[0], db[2], idesc, 1u);
+            umma(d, da[2], db[0], idesc, 1u);
           }
         }
         umma_commit(&empty[s]);
@@ -299,26 +293,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (!mbar_wait_timer(mma_done, 0)) atomicExch(err, 5);
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 2..9)
-    // Warp w reads TMEM lane quarter w % 4 (rows 32q..32q+31) and column half
-    // h = (w - 2) / 4 of the Re and Im accumulators.  The FP32 partial of every
-    // fold is added to FP32 running sums held in registers (round to nearest)
-    // and the running sums go to the FP64 chi0 every `flush` folds, so the
-    // truncating accumulation inside the tensor core never spans more than one fold.
+    // ------------------------------------------------------------ epilogue (warps 2..17)
+    // Warp w reads TMEM lane quarter w % 4 (rows 32q..32q+31) and column
+    // slice cs = (w - 2) / 4 (32 columns) of the Re and Im accumulators; four
+    // warps per quarter drain a fold in a quarter of the time one would.  The
+    // FP32 partial of every fold is added to FP32 running sums held in
+    // registers (round to nearest) and the running sums go to the FP64 chi0
+    // every `flush` folds, so the truncating accumulation inside the tensor
+    // core never spans more than one fold.
     const int q = warp & 3;
-    const int h = (warp - 2) >> 2;
+    const int cs = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const int gi = i0 + row;
-    const int cbase = h * 64;
+    const int cbase = cs * 32;
     double2* crow = chi + ((int64_t)w * NG + gi) * NG + j0 + cbase;
     // columns of this thread that belong to the lower triangle and the sphere
-    const int ncol = (gi < NG) ? max(0, min(64, min(NG, gi + 1) - (j0 + cbase))) : 0;
-    float sre[64], sim[64];
+    const int ncol = (gi < NG) ? max(0, min(32, min(NG, gi + 1) - (j0 + cbase))) : 0;
+    float sre[32], sim[32];
 #pragma unroll
-    for (int c = 0; c < 64; ++c) sre[c] = sim[c] = 0.f;
+    for (int c = 0; c < 32; ++c) sre[c] = sim[c] = 0.f;
 #define RPA_TC_FLUSH()                                      \
   do {                                                      \
-    _Pragma("unroll") for (int c = 0; c < 64; ++c) {        \
+    _Pragma("unroll") for (int c = 0; c < 32; ++c) {        \
       if (c < ncol) {                                       \
         double2 v = crow[c];                                \
         v.x += (double)sre[c];                              \
@@ -340,21 +336,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + cbase;
-      float v[32];
-      tmem_ld32(base, v);
+      // 18 warps leave 96 registers a thread: 64 running sums and one
+      // 16-column load at a time; the buffer is released as soon as the last
+      // load has landed, before its additions
+      float v[16];
+      tmem_ld16(base, v);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) sre[c] += v[c];
-      tmem_ld32(base + 32, v);
+      for (int c = 0; c < 16; ++c) sre[c] += v[c];
+      tmem_ld16(base + 16, v);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) sre[32 + c] += v[c];
-      tmem_ld32(base + 128, v);
+      for (int c = 0; c < 16; ++c) sre[16 + c] += v[c];
+      tmem_ld16(base + 128, v);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) sim[c] += v[c];
-      tmem_ld32(base + 160, v);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) sim[32 + c] += v[c];
+      for (int c = 0; c < 16; ++c) sim[c] += v[c];
+      tmem_ld16(base + 144, v);
       tc_fence_before();
       mbar_arrive(&tempty[b]);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sim[16 + c] += v[c];
       if ((f + 1) % flush == 0) RPA_TC_FLUSH();
     }
     RPA_TC_FLUSH();

@@ -261,8 +261,6 @@ void prof_end(rpa_ctx* c) {
 // float-float trailing updates of the log-det in the mixed-precision modes
 bool ff_logdet(const rpa_ctx* c) { return c->prm.precision != RPA_FP64 && c->tune[RPA_TUNE_LOGDET] == 1; }
 
-int work_bytes_per_complex(const rpa_ctx* c) { return c->prm.precision == RPA_FP64 ? 16 : 8; }
-
 // ---- stage a1: every band of a set onto the real-space grid (Eq. 8, Table 1 step 3)
 template <typename T>
 rpa_status build_grids_T(rpa_ctx* c, OrbSet& s) {
