@@ -228,8 +228,8 @@ def run_ours(args):
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    stage_ms = np.zeros(5)
-    launches = np.zeros(5, dtype=np.int64)
+    stage_ms = np.zeros(b.RPA_NSTAGES)
+    launches = np.zeros(b.RPA_NSTAGES, dtype=np.int64)
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
@@ -313,7 +313,7 @@ def run_ours(args):
     b.rpa_destroy(ctx)
     if rank != 0:
         return
-    stage_names = ["wf_to_grid", "pair_density_paw", "rankk_update", "logdet", "other"]
+    stage_names = ["wf_to_grid", "pair_density_paw", "rankk_kernel", "logdet", "other", "rankk_operand_prep"]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",

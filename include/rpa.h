@@ -208,8 +208,10 @@ rpa_status rpa_energy_backward(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
 /* Per-stage device timings of the most recent rpa_chi0/rpa_energy call,
  * measured with CUDA events on the context's stream when enabled by
  * rpa_set_profiling(ctx, 1).  Index: 0 wavefunctions to grid, 1 pair
- * densities (+PAW), 2 rank-k update, 3 log-det, 4 other.  ms[5] total
- * milliseconds per stage, launches[5] kernel launches per stage. */
+ * densities (+PAW), 2 rank-k update kernel, 3 log-det, 4 other, 5 rank-k
+ * operand preparation (split-bfloat16 modes).  ms[RPA_NSTAGES] total
+ * milliseconds per stage, launches[RPA_NSTAGES] kernel launches per stage. */
+#define RPA_NSTAGES 6
 rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
 rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
 

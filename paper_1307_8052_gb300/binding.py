@@ -51,6 +51,7 @@ SIGNATURES = {
     "rpa_graph_launch": (_I, [_P]),
     "rpa_graph_destroy": (None, [_P]),
 }
+RPA_NSTAGES = 6  # profile stages: wf, pair densities, rank-k kernel, log-det, other, operand preparation
 (RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID, RPA_TUNE_OPERAND_MB, RPA_TUNE_TC_PIPE,
  RPA_TUNE_LOGDET) = range(7)
 
@@ -295,8 +296,8 @@ def rpa_logdet_noalloc(chi, v, terms, stream=0):
 
 
 def rpa_get_profile(ctx):
-    ms = np.zeros(5)
-    nl = np.zeros(5, dtype=np.int64)
+    ms = np.zeros(RPA_NSTAGES)
+    nl = np.zeros(RPA_NSTAGES, dtype=np.int64)
     _check(ctx, lib().rpa_get_profile(ctx, ms.ctypes.data_as(_P), nl.ctypes.data_as(_P)))
     return ms, nl
 

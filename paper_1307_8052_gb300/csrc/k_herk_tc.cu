@@ -525,34 +525,62 @@ static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpa
   return cudaGetLastError();
 }
 
-cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int terms, int fold_stages,
-                           int flush_folds, int pipe, double2* chi, void* scratch, size_t scratch_bytes, int* err,
-                           cudaStream_t s) {
+// Bounds shared by the two calls below.
+static cudaError_t check_args(int64_t P, int NG, int nw, int terms, size_t scratch_bytes) {
+  if (terms != 2) return cudaErrorInvalidValue;
+  const tc::Geometry g = tc::geometry(P, NG);
+  if (scratch_bytes < herk_tc_scratch_bytes(P, NG, nw, terms)) return cudaErrorInvalidValue;
+  if (g.Kpad > (int64_t)1 << 31 || (int64_t)nw * g.NGpad > (1 << 30)) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+// Scratch layout: X terms, Z terms, then the per-frequency A terms.
+struct Operands {
+  __nv_bfloat16 *X, *Z, *A;
+  int64_t op_elems;
+};
+static Operands operands(void* scratch, const tc::Geometry& g, int terms) {
+  Operands o;
+  o.op_elems = (int64_t)g.NGpad * g.Kpad;
+  o.X = (__nv_bfloat16*)scratch;
+  o.Z = o.X + o.op_elems * terms;
+  o.A = o.Z + o.op_elems * terms;
+  return o;
+}
+
+cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt, int nw, int terms, void* scratch,
+                            size_t scratch_bytes, cudaStream_t s) {
   using namespace tc;
   if (P == 0 || NG == 0 || nw == 0) return cudaSuccess;
-  if (terms != 2) return cudaErrorInvalidValue;
+  cudaError_t e = check_args(P, NG, nw, terms, scratch_bytes);
+  if (e != cudaSuccess) return e;
+  const Geometry g = geometry(P, NG);
+  const Operands o = operands(scratch, g, terms);
+  dim3 pg(g.NGpad / 32, (unsigned)(g.Ppad / 32));
+  prep_xz_kernel<2><<<pg, 256, 0, s>>>(N, P, NG, g.NGpad, g.Kpad, (__nv_bfloat162*)o.X, (__nv_bfloat162*)o.Z,
+                                       o.op_elems / 2);
+  prep_a_kernel<2><<<pg, 256, 0, s>>>(N, wgt, P, NG, g.NGpad, g.Kpad, nw, (__nv_bfloat162*)o.A,
+                                      o.op_elems * nw / 2);
+  return cudaGetLastError();
+}
+
+cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fold_stages, int flush_folds, int pipe,
+                        double2* chi, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
+  using namespace tc;
+  if (P == 0 || NG == 0 || nw == 0) return cudaSuccess;
+  cudaError_t e = check_args(P, NG, nw, terms, scratch_bytes);
+  if (e != cudaSuccess) return e;
   if (fold_stages < 1) fold_stages = 1;
   if (flush_folds < 1) flush_folds = 1;
   const int bk = pipe == 1 ? 32 : 64;
   const Geometry g = geometry(P, NG);
-  if (scratch_bytes < herk_tc_scratch_bytes(P, NG, nw, terms)) return cudaErrorInvalidValue;
-  if (g.Kpad > (int64_t)1 << 31 || (int64_t)nw * g.NGpad > (1 << 30)) return cudaErrorInvalidValue;
-  char* base = (char*)scratch;
-  const int64_t op_elems = (int64_t)g.NGpad * g.Kpad;  // bf16 elements per operand matrix
-  __nv_bfloat16* X = (__nv_bfloat16*)base;
-  __nv_bfloat16* Z = X + op_elems * terms;
-  __nv_bfloat16* A = Z + op_elems * terms;
-  cudaError_t e;
-  dim3 pg(g.NGpad / 32, (unsigned)(g.Ppad / 32));
-  prep_xz_kernel<2><<<pg, 256, 0, s>>>(N, P, NG, g.NGpad, g.Kpad, (__nv_bfloat162*)X, (__nv_bfloat162*)Z, op_elems / 2);
-  prep_a_kernel<2><<<pg, 256, 0, s>>>(N, wgt, P, NG, g.NGpad, g.Kpad, nw, (__nv_bfloat162*)A, op_elems * nw / 2);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const Operands o = operands(scratch, g, terms);
   Maps maps;
   memset(&maps, 0, sizeof(maps));
   for (int t = 0; t < terms; ++t) {
-    if (!make_map(&maps.a[t], A + op_elems * nw * t, g.Kpad, (int64_t)nw * g.NGpad, bk) ||
-        !make_map(&maps.x[t], X + op_elems * t, g.Kpad, g.NGpad, bk) ||
-        !make_map(&maps.z[t], Z + op_elems * t, g.Kpad, g.NGpad, bk))
+    if (!make_map(&maps.a[t], o.A + o.op_elems * nw * t, g.Kpad, (int64_t)nw * g.NGpad, bk) ||
+        !make_map(&maps.x[t], o.X + o.op_elems * t, g.Kpad, g.NGpad, bk) ||
+        !make_map(&maps.z[t], o.Z + o.op_elems * t, g.Kpad, g.NGpad, bk))
       return cudaErrorInvalidValue;
   }
   const int nt = g.NGpad / BM;

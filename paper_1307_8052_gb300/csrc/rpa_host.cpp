@@ -17,9 +17,12 @@
 #include <vector>
 
 namespace rpa {
-cudaError_t launch_herk_tc(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms,
-                           int fold_stages, int flush_folds, int pipe, double2* chi, void* scratch,
-                           size_t scratch_bytes, int* err, cudaStream_t s);
+// tensor-core rank-k update (k_herk_tc.cu): operand preparation (bf16 split of
+// the weighted and plain pair densities into scratch), then the tcgen05 kernel
+cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms,
+                            void* scratch, size_t scratch_bytes, cudaStream_t s);
+cudaError_t herk_tc_run(int64_t P, int NG, int nw, int split_terms, int fold_stages, int flush_folds, int pipe,
+                        double2* chi, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
 size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
 // adjoint kernels (k_adjoint.cu)
 cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
@@ -116,8 +119,8 @@ struct rpa_ctx {
   std::map<std::string, DevBuf> ws;
   uint64_t stamp = 0;
   bool profiling = false;
-  double prof_ms[5] = {0};
-  int64_t prof_launch[5] = {0};
+  double prof_ms[RPA_NSTAGES] = {0};
+  int64_t prof_launch[RPA_NSTAGES] = {0};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -213,7 +216,7 @@ void inv3(const double* m, double* out) {
 
 // ---- profiling helpers (CUDA events on the context stream)
 void prof_begin(rpa_ctx* c) {
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < RPA_NSTAGES; ++i) {
     c->prof_ms[i] = 0;
     c->prof_launch[i] = 0;
   }
@@ -521,18 +524,22 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
     rpa_status st = pairs_block<T>(c, Q, t, a0, std::min(nL, a0 + rows), omega_d, nw, B);
     if (st != RPA_OK) return st;
     if (B.P == 0) continue;
-    StageTimer tm(c, 2, 1);
     const int prec = c->prm.precision;
     if (prec == RPA_FP64 || prec == RPA_FP32) {
+      StageTimer tm(c, 2, 1);
       CUDA_OK(c, launch_herk_simt_w<T>(B.N, B.P, B.NG, B.w, nw, chi, c->stream));
     } else {
       const int terms = prec == RPA_BF16X3 ? 3 : 2;
       void* scr = nullptr;
       const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
       if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
-      CUDA_OK(c, launch_herk_tc((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms,
-                                (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH],
-                                (int)c->tune[RPA_TUNE_TC_PIPE], chi, scr, sb, c->dev_err, c->stream));
+      {
+        StageTimer tm(c, 5, 2);
+        CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms, scr, sb, c->stream));
+      }
+      StageTimer tm(c, 2, 1);
+      CUDA_OK(c, herk_tc_run(B.P, B.NG, nw, terms, (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH],
+                             (int)c->tune[RPA_TUNE_TC_PIPE], chi, scr, sb, c->dev_err, c->stream));
     }
   }
   return RPA_OK;
@@ -1501,7 +1508,7 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
 
 rpa_status rpa_get_profile(const rpa_ctx* c, double* ms, int64_t* launches) {
   if (!c) return RPA_ERR_ARG;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < RPA_NSTAGES; ++i) {
     if (ms) ms[i] = c->prof_ms[i];
     if (launches) launches[i] = c->prof_launch[i];
   }
