@@ -8,6 +8,13 @@
 // the panel below it by a triangular solve, and the trailing lower triangle is
 // updated with 64x64 DFMA tiles.  A pivot that is not positive (or NaN) sets a
 // device flag that the host turns into RPA_ERR_NOT_HPD; the kernels never trap.
+//
+// In the mixed-precision modes the part of the matrix that is still being
+// updated is held in float-float form (each real value the unevaluated sum of
+// two FP32 numbers, about 48 significant bits) and the trailing updates run on
+// the FP32 pipe; GB300's FP64 pipe retires only a few lanes per clock, so even
+// format conversions there would cost as much as the updates.  Factorised
+// columns are written back in FP64, so the finished factor has one format.
 #include "rpa.h"
 #include "rpa_internal.h"
 
@@ -16,50 +23,12 @@ namespace rpa {
 constexpr int CB = 32;  // panel width
 constexpr int UT = 64;  // update tile edge
 
-__global__ void chol_form_kernel(const double2* __restrict__ chi, const double* __restrict__ v, int nw, int NG,
-                                 double2* __restrict__ A) {
-  const int64_t total = (int64_t)nw * NG * NG;
-  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(id % NG);
-    const int64_t r = id / NG;
-    const int i = (int)(r % NG);
-    if (j > i) continue;
-    const double s = sqrt(v[i]) * sqrt(v[j]);
-    const double2 c = chi[id];
-    double2 a = make_double2(-s * c.x, -s * c.y);
-    if (i == j) {
-      a.x += 1.0;
-      a.y = 0.0;
-    }
-    A[id] = a;
-  }
-}
-
-__global__ void trace_kernel(const double2* __restrict__ chi, const double* __restrict__ v, int NG,
-                             double* __restrict__ trace) {
-  __shared__ double red[256];
-  const int w = blockIdx.x;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < NG; i += blockDim.x) s += v[i] * chi[((int64_t)w * NG + i) * NG + i].x;
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) trace[w] = red[0];
-}
-
-// ---------------------------------------------------------------- float-float trailing update
-// The trailing update dominates the factorisation (NG^3/6 complex
-// multiply-adds per frequency).  GB300 issues FP32 FMAs about 70 times as fast
-// as FP64 ones, so the mixed-precision modes evaluate it in float-float
-// arithmetic: each value is the unevaluated sum hi + lo of two FP32 numbers
-// (Dekker's exact product via FMA and Knuth's two-sum), about 44 significant
-// bits.  The matrix itself stays in FP64; only the panel sums of one update
-// are float-float.  The _rn intrinsics keep the compiler from contracting the
-// steps into FMAs, which would break the exact error terms.
+// ---------------------------------------------------------------- float-float arithmetic
+// A value is the unevaluated sum hi + lo of two FP32 numbers; products use
+// Dekker's exact product via FMA, sums Knuth's two-sum (about 44 significant
+// bits after a panel of multiply-adds).  A complex value is a float4
+// (re hi, re lo, im hi, im lo).  The _rn intrinsics keep the compiler from
+// contracting the steps into FMAs, which would break the exact error terms.
 __device__ __forceinline__ float4 ff_split(double2 x) {
   const float rh = __double2float_rn(x.x), ih = __double2float_rn(x.y);
   return make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
@@ -76,6 +45,65 @@ __device__ __forceinline__ void ff_mac(float& sh, float& sl, float xh, float xl,
   const float d = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
   sh = t;
   sl = __fadd_rn(sl, __fadd_rn(d, e));
+}
+
+// (h, l) <- h + l with |l| <= ulp(h) / 2 (fast two-sum; |h| >= |l| holds)
+__device__ __forceinline__ void ff_norm(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
+// (ah, al) - (bh, bl), normalised
+__device__ __forceinline__ void ff_sub(float& ah, float& al, float bh, float bl) {
+  const float t = __fsub_rn(ah, bh);
+  const float z = __fsub_rn(t, ah);
+  float d = __fadd_rn(__fsub_rn(ah, __fsub_rn(t, z)), __fsub_rn(-bh, z));  // t + d == ah - bh exactly
+  d = __fadd_rn(d, __fsub_rn(al, bl));
+  ah = t;
+  al = d;
+  ff_norm(ah, al);
+}
+
+__device__ __forceinline__ double2 ff_to_double(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+// A = 1 - v^1/2 chi v^1/2 (lower triangle), in FP64 or float-float (FF).
+template <bool FF>
+__global__ void chol_form_kernel(const double2* __restrict__ chi, const double* __restrict__ v, int nw, int NG,
+                                 double2* __restrict__ A) {
+  const int64_t total = (int64_t)nw * NG * NG;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % NG);
+    const int64_t r = id / NG;
+    const int i = (int)(r % NG);
+    if (j > i) continue;
+    const double s = sqrt(v[i]) * sqrt(v[j]);
+    const double2 c = chi[id];
+    double2 a = make_double2(-s * c.x, -s * c.y);
+    if (i == j) {
+      a.x += 1.0;
+      a.y = 0.0;
+    }
+    if constexpr (FF) reinterpret_cast<float4*>(A)[id] = ff_split(a); else A[id] = a;
+  }
+}
+
+__global__ void trace_kernel(const double2* __restrict__ chi, const double* __restrict__ v, int NG,
+                             double* __restrict__ trace) {
+  __shared__ double red[256];
+  const int w = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < NG; i += blockDim.x) s += v[i] * chi[((int64_t)w * NG + i) * NG + i].x;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) trace[w] = red[0];
 }
 
 // 1/sqrt(x) for a pivot x > 0: a single-precision estimate refined by two
@@ -97,9 +125,12 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 // Every column step is parallel over the CTA: the column of L is scaled, then
 // the Schur complement and the forward substitution for L^-1 (right-hand side
 // I) are updated together; the logs are taken once at the end.
+// FF: the block is read in float-float form and the inverse is also written
+// in float-float form to Linv_ff; the factor always goes back in FP64.
+template <bool FF>
 __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A, int NG, int k0, int b,
                                                         double* __restrict__ logdet, int* __restrict__ flag,
-                                                        double2* __restrict__ Linv) {
+                                                        double2* __restrict__ Linv, float4* __restrict__ Linv_ff) {
   __shared__ double2 L[CB][CB + 1];
   __shared__ double2 X[CB][CB + 1];  // right-hand side I, then L^-1
   __shared__ double piv_s[CB];
@@ -108,7 +139,12 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A,
   double2* Aw = A + (int64_t)w * NG * NG;
   for (int e = tid; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, j = e % CB;
-    L[i][j] = (i < b && j <= i) ? Aw[(int64_t)(k0 + i) * NG + k0 + j] : make_double2(0.0, 0.0);
+    double2 a = make_double2(0.0, 0.0);
+    if (i < b && j <= i) {
+      const int64_t o = (int64_t)(k0 + i) * NG + k0 + j;
+      if constexpr (FF) a = ff_to_double(reinterpret_cast<const float4*>(Aw)[o]); else a = Aw[o];
+    }
+    L[i][j] = a;
     X[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
@@ -174,35 +210,41 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A,
   double2* Lw = Linv + (int64_t)w * CB * CB;
   for (int e = tid; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, j = e % CB;
-    Lw[e] = (i < b && j <= i) ? X[i][j] : make_double2(0.0, 0.0);
+    const double2 x = (i < b && j <= i) ? X[i][j] : make_double2(0.0, 0.0);
+    Lw[e] = x;
+    if constexpr (FF) Linv_ff[(int64_t)w * CB * CB + e] = ff_split(x);
     if (i < b && j <= i) Aw[(int64_t)(k0 + i) * NG + k0 + j] = L[i][j];
   }
 }
 
 // Panel below the diagonal block: X = A_panel L_kk^-H, i.e.
 // x_rj = sum_{l <= j} a_rl conj(Linv_jl).  16 threads per row, each owning
-// columns j and b-1-j so that every thread does b+1 multiply-adds; FF selects
-// float-float arithmetic (inputs and result stay FP64).
+// columns j and b-1-j so that every thread does b+1 multiply-adds.  FF: the
+// panel rows and the inverse are read in float-float form, the product is
+// float-float, and the result goes to A in FP64 and to Lp ([NG][CB] per
+// frequency, float-float) for the trailing update.
 constexpr int TROWS = 16;  // rows per triangular-solve CTA
 
 template <bool FF>
 __global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A, int NG, int k0, int b,
-                                                        const double2* __restrict__ Linv) {
+                                                        const double2* __restrict__ Linv,
+                                                        const float4* __restrict__ Linv_ff, float4* __restrict__ Lp) {
   using E = typename std::conditional<FF, float4, double2>::type;
   __shared__ E Li[CB][CB + 1];
   __shared__ E X[TROWS][CB + 1];
   const int w = blockIdx.y;
   double2* Aw = A + (int64_t)w * NG * NG;
-  const double2* Lw = Linv + (int64_t)w * CB * CB;
   const int i0 = k0 + b + blockIdx.x * TROWS;
   for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-    const double2 v = Lw[e];
-    if constexpr (FF) Li[e / CB][e % CB] = ff_split(v); else Li[e / CB][e % CB] = v;
+    if constexpr (FF) Li[e / CB][e % CB] = Linv_ff[(int64_t)w * CB * CB + e];
+    else Li[e / CB][e % CB] = Linv[(int64_t)w * CB * CB + e];
   }
   for (int e = threadIdx.x; e < TROWS * CB; e += blockDim.x) {
     const int r = e / CB, l = e % CB;
-    const double2 v = (i0 + r < NG && l < b) ? Aw[(int64_t)(i0 + r) * NG + k0 + l] : make_double2(0.0, 0.0);
-    if constexpr (FF) X[r][l] = ff_split(v); else X[r][l] = v;
+    const bool in = i0 + r < NG && l < b;
+    const int64_t o = (int64_t)(i0 + r) * NG + k0 + l;
+    if constexpr (FF) X[r][l] = in ? reinterpret_cast<const float4*>(Aw)[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+    else X[r][l] = in ? Aw[o] : make_double2(0.0, 0.0);
   }
   __syncthreads();
   const int r = threadIdx.x >> 4, t = threadIdx.x & 15;
@@ -213,7 +255,6 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A,
     // t owns column t when t <= b-1-t, and column b-1-t when that lies above t
     const int j = h == 0 ? t : b - 1 - t;
     if (h == 0 ? 2 * t > b - 1 : j <= t) continue;
-    double2 out;
     if constexpr (FF) {
       float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int l = 0; l <= j; ++l) {
@@ -223,13 +264,15 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A,
         ff_mac(s.z, s.w, a.z, a.w, y.x, y.y);
         ff_mac(s.z, s.w, -a.x, -a.y, y.z, y.w);
       }
-      out = make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
+      ff_norm(s.x, s.y);
+      ff_norm(s.z, s.w);
+      Aw[(int64_t)row * NG + k0 + j] = ff_to_double(s);
+      Lp[((int64_t)w * NG + row) * CB + j] = s;
     } else {
       double2 s = make_double2(0.0, 0.0);
       for (int l = 0; l <= j; ++l) cmac_cj<double>(s, X[r][l], Li[j][l]);
-      out = s;
+      Aw[(int64_t)row * NG + k0 + j] = s;
     }
-    Aw[(int64_t)row * NG + k0 + j] = out;
   }
 }
 
@@ -290,25 +333,28 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double2* __restrict__ 
 }
 
 // Float-float trailing update on 32 x 32 tiles of 64 threads (4 x 4 outputs
-// each): the float-float accumulators take 167 registers a thread, and small
-// CTAs let six of them share an SM so that twelve warps hide the latency of
-// the dependent two-sum steps.
+// each): the panel comes from Lp and the trailing matrix is float-float, so
+// the kernel issues no FP64 instruction.  The accumulators take 167 registers
+// a thread; small CTAs let six of them share an SM so that twelve warps hide
+// the latency of the dependent two-sum steps.
 constexpr int UTF = 32;
 
-__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b) {
+__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b,
+                                                               const float4* __restrict__ Lp) {
   __shared__ float4 Li[CB][UTF];
   __shared__ float4 Lj[CB][UTF];
   const int w = blockIdx.y;
-  double2* Aw = A + (int64_t)w * NG * NG;
+  float4* Aw = reinterpret_cast<float4*>(A) + (int64_t)w * NG * NG;
+  const float4* Pw = Lp + (int64_t)w * NG * CB;
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
   const int s0 = k0 + b;
   const int r0 = s0 + ti * UTF, c0 = s0 + tj * UTF;
   for (int e = threadIdx.x; e < b * UTF; e += blockDim.x) {
     const int rr = e / b, l = e % b;
-    const double2 z = make_double2(0.0, 0.0);
-    Li[l][rr] = ff_split((r0 + rr < NG) ? Aw[(int64_t)(r0 + rr) * NG + k0 + l] : z);
-    Lj[l][rr] = ff_split((c0 + rr < NG) ? Aw[(int64_t)(c0 + rr) * NG + k0 + l] : z);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    Li[l][rr] = (r0 + rr < NG) ? Pw[(int64_t)(r0 + rr) * CB + l] : z;
+    Lj[l][rr] = (c0 + rr < NG) ? Pw[(int64_t)(c0 + rr) * CB + l] : z;
   }
   __syncthreads();
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
@@ -343,10 +389,10 @@ __global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restri
     for (int c = 0; c < 4; ++c) {
       const int row = r0 + ty + 8 * r, col = c0 + tx + 8 * c;
       if (row < NG && col < NG && col <= row) {
-        double2* p = Aw + (int64_t)row * NG + col;
-        double2 v = *p;
-        v.x -= (double)acc[r][c].x + (double)acc[r][c].y;
-        v.y -= (double)acc[r][c].z + (double)acc[r][c].w;
+        float4* p = Aw + (int64_t)row * NG + col;
+        float4 v = *p;
+        ff_sub(v.x, v.y, acc[r][c].x, acc[r][c].y);
+        ff_sub(v.z, v.w, acc[r][c].z, acc[r][c].w);
         *p = v;
       }
     }
@@ -363,7 +409,12 @@ static inline int gridc(int64_t n) {
   return (int)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
 }
 
-int64_t logdet_work_elems(int nw, int NG) { return (int64_t)nw * NG * NG + (int64_t)nw * CB * CB; }
+// work layout (complex slots of 16 bytes): the matrix [nw][NG][NG], the
+// inverses of the diagonal blocks in FP64 and in float-float [nw][CB][CB]
+// each, and the float-float panel [nw][NG][CB]
+int64_t logdet_work_elems(int nw, int NG) {
+  return (int64_t)nw * NG * NG + 2 * (int64_t)nw * CB * CB + (int64_t)nw * NG * CB;
+}
 
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work, double* logdet,
                        double* trace, int* flag, bool ff_update, cudaStream_t s, int64_t* launches) {
@@ -375,30 +426,37 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
     return e;
   if ((e = cudaMemsetAsync(logdet, 0, sizeof(double) * nw, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return e;
-  double2* Linv = work + (int64_t)nw * NG * NG;  // [nw][CB][CB]
+  double2* Linv = work + (int64_t)nw * NG * NG;                                     // [nw][CB][CB]
+  float4* Linv_ff = reinterpret_cast<float4*>(Linv + (int64_t)nw * CB * CB);        // [nw][CB][CB]
+  float4* Lp = Linv_ff + (int64_t)nw * CB * CB;                                     // [nw][NG][CB]
   const int64_t total = (int64_t)nw * NG * NG;
-  chol_form_kernel<<<gridc(total), 256, 0, s>>>(chi, v, nw, NG, work);
+  if (ff_update)
+    chol_form_kernel<true><<<gridc(total), 256, 0, s>>>(chi, v, nw, NG, work);
+  else
+    chol_form_kernel<false><<<gridc(total), 256, 0, s>>>(chi, v, nw, NG, work);
   trace_kernel<<<nw, 256, 0, s>>>(chi, v, NG, trace);
   nl += 2;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int k0 = 0; k0 < NG; k0 += CB) {
     const int b = (NG - k0) < CB ? (NG - k0) : CB;
-    chol_diag_kernel<<<nw, 256, 0, s>>>(work, NG, k0, b, logdet, flag, Linv);
-    ++nl;
     const int rest = NG - k0 - b;
-    if (rest > 0) {
-      const dim3 tg((rest + TROWS - 1) / TROWS, nw);
-      if (ff_update) {
-        chol_trsm_kernel<true><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv);
+    const dim3 tg((rest + TROWS - 1) / TROWS, nw);
+    if (ff_update) {
+      chol_diag_kernel<true><<<nw, 256, 0, s>>>(work, NG, k0, b, logdet, flag, Linv, Linv_ff);
+      if (rest > 0) {
+        chol_trsm_kernel<true><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv, Linv_ff, Lp);
         const int nt = (rest + UTF - 1) / UTF;
-        chol_update_ff_kernel<<<dim3(nt * (nt + 1) / 2, nw), 64, 0, s>>>(work, NG, k0, b);
-      } else {
-        chol_trsm_kernel<false><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv);
+        chol_update_ff_kernel<<<dim3(nt * (nt + 1) / 2, nw), 64, 0, s>>>(work, NG, k0, b, Lp);
+      }
+    } else {
+      chol_diag_kernel<false><<<nw, 256, 0, s>>>(work, NG, k0, b, logdet, flag, Linv, nullptr);
+      if (rest > 0) {
+        chol_trsm_kernel<false><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv, nullptr, nullptr);
         const int nt = (rest + UT - 1) / UT;
         chol_update_kernel<<<dim3(nt * (nt + 1) / 2, nw), 256, upd_smem, s>>>(work, NG, k0, b);
       }
-      nl += 2;
     }
+    nl += rest > 0 ? 3 : 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (launches) *launches += nl;
