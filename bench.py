@@ -102,6 +102,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def herk_traffic():
+    """DRAM bytes per launch of the rank-k kernel from the committed ncu summary,
+    or None when the kernel source has changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "herk_tc_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, d["source"]), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if h != d.get("source_sha256"):
+        return None
+    return float(d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"])
+
+
 def rankk_flops(ngs, ks, nw):
     return float(sum(4.0 * ng * (ng + 1) * k * nw for ng, k in zip(ngs, ks)))
 
@@ -175,6 +192,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     from paper_1307_8052_gb300 import binding as b
+    from paper_1307_8052_gb300 import shard
     from paper_1307_8052_gb300 import synthetic as syn
     from paper_1307_8052_gb300.build import build
 
@@ -217,11 +235,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(x, device="cuda")
 
     for _ in range(args.warmup):
         b.rpa_energy(ctx, iqs, wq, om, W)
@@ -331,7 +345,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3},
         "gpu_launches": int(launches.sum()),
         "roofline": {"bound": bound, "kernel": "rank-k update (Eq. 17)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": herk_traffic() if bound == "tensor" else None,
+                     "traffic_note": "ncu DRAM read+write bytes of one launch of the profiling case (one k-block, "
+                                     "NG 1180); null once the kernel source differs from the captured one",
                      "peak_source": peak_kind if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x max clock"},
         "clocks": clk.summary(),
         "cpu_baseline": base,

@@ -68,7 +68,7 @@ def g_sphere(cell, q_red, ecut: float) -> np.ndarray:
 
 
 def coulomb(cell, q_red, gmiller) -> np.ndarray:
-    """v_G(q) = 4 pi / |q+G|^2 (Sec. 2.3, text after Eq. 11); zero where q+G = 0."""
+    """v_G(q) = 4 pi / |q+G|^2 (Sec. 2.2, text after Eq. 11); zero where q+G = 0."""
     B = reciprocal(cell)
     qg = np.asarray(gmiller, dtype=np.float64) + np.asarray(q_red, dtype=np.float64)
     c = qg @ B

@@ -68,6 +68,21 @@ def test_config0_chi_and_energy(precision):
         b.rpa_destroy(ctx)
 
 
+def test_config0_matches_stored_terms():
+    """The FP64 path against the stored oracle terms of tests/golden/."""
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config0_terms.txt")) as f:
+        rows = [[float(x) for x in ln.split()] for ln in f if ln.strip() and not ln.startswith("#")]
+    t = np.array(rows)
+    p = syn.config0()
+    ctx = _ctx(p, "fp64")
+    try:
+        _, terms = b.rpa_energy(ctx, [0], [1.0], t[:, 1], t[:, 2])
+    finally:
+        b.rpa_destroy(ctx)
+    assert np.max(np.abs(terms[0] - t[:, 3])) <= TOL["fp64"]["term"] * np.max(np.abs(t[:, 3]))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
 def test_small_mesh_umklapp_paw_all_q(precision):
     """2x1x1 mesh (umklapp at q = 1/2), ragged Miller boxes, two PAW atoms."""
