@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "chi0 TFLOP/s and s per q (all iw), mixed vs FP64 on 1 GB300; E_c rel. error"
 WORKLOAD = "bulk 9 bohr box, 40^3 grid, 2x2x2 k, 8 q, 16 occ + 1200 empty bands, NG~1200, 16 iw, 3x13 PAW projectors"
+WORKLOAD_SLAB = ("slab 9.4x8.1x40 bohr, 48x40x200 grid, 4x2x1 k, 120 occ + 3000 empty bands, NG~3000, 16 iw, "
+                 "16x18 + 2x8 PAW projectors")
 CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
                 "clocks_event_reasons.sw_power_cap")
@@ -123,9 +125,17 @@ def rankk_flops(ngs, ks, nw):
     return float(sum(4.0 * ng * (ng + 1) * k * nw for ng, k in zip(ngs, ks)))
 
 
-def make_workload():
+def make_workload(config="bulk"):
     from paper_1307_8052_gb300 import synthetic as syn
-    return syn.config1()
+    return syn.config2() if config == "slab" else syn.config1()
+
+
+def workload_qpoints(args, p):
+    """q-points of one step: all 8 for the bulk workload; for the slab the
+    ``--slab-q`` q-points from (0, 1/2, 0) on (8 transitions each)."""
+    if args.config == "slab":
+        return list(range(1, 1 + args.slab_q))
+    return list(range(len(p.qpoints)))
 
 
 def pairs_per_q(p):
@@ -138,23 +148,23 @@ def pairs_per_q(p):
     return out
 
 
-def cpu_sample(p, steps=1, warmup=0):
-    """Time the oracle on a bounded sample of the workload: chi0 of q-point 3 from
-    the first transition with 4 occupied x 100 empty bands (all G, all iw)."""
+def cpu_sample(p, steps=1, warmup=0, iq=3, nocc=4):
+    """Time the oracle on a bounded sample of the workload: chi0 of q-point iq from
+    the first transition with nocc occupied x 100 empty bands (all G, all iw)."""
     import oracle as o
     from paper_1307_8052_gb300 import synthetic as syn
-    iq = 3
     qp = p.qpoints[iq]
+    no = int(np.sum(p.sets[0].f > 0))
     sets = []
     for s in p.sets:
-        keep = np.r_[np.arange(12, 16), np.arange(16, 116)]
+        keep = np.r_[np.arange(no - nocc, no), np.arange(no, no + 100)]
         sets.append(syn.OrbitalSet(s.k_red, s.miller, s.C[keep], s.eps[keep], s.f[keep], s.P[keep]))
     sub = syn.Problem(p.name, p.config, p.cell, p.grid, p.ecut_wf, p.ecut_chi, p.spin_factor, p.nk_bz, sets,
                       [syn.QPoint(qp.q_red, qp.k_of[:1], qp.kq_of[:1], qp.G0[:1], 1.0)], p.nw, p.paw)
     gm = o.g_sphere(p.cell, qp.q_red, p.ecut_chi)
     Q = syn.paw_Q(p.paw, p.cell, qp.q_red, gm)
     om, _ = o.frequency_grid(p.nw)
-    flops = rankk_flops([len(gm)], [4 * 100], p.nw)
+    flops = rankk_flops([len(gm)], [nocc * 100], p.nw)
     times = []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
@@ -168,8 +178,14 @@ def cpu_sample(p, steps=1, warmup=0):
         cores = os.cpu_count()
     t = float(np.mean(times))
     return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": int(cores), "kind": "oracle",
-            "sample": "chi0 of q=(0,1/2,1/2), first k-transition, 4 occupied x 100 empty bands, all G and iw "
-                      f"({flops / 1e12:.4f} TFLOP algorithmic, {t:.2f} s per sample)"}, times
+            "sample": f"chi0 of q={tuple(float(x) for x in qp.q_red)}, first k-transition, {nocc} occupied x 100 "
+                      f"empty bands, all G and iw ({flops / 1e12:.4f} TFLOP algorithmic, {t:.2f} s per sample)"}, times
+
+
+def cpu_sample_for(args, p, steps=1, warmup=0):
+    if args.config == "slab":
+        return cpu_sample(p, steps, warmup, iq=1, nocc=2)
+    return cpu_sample(p, steps, warmup)
 
 
 def run_reference(args):
@@ -177,13 +193,13 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = make_workload()
-    base, times = cpu_sample(p, steps=args.steps, warmup=args.warmup)
+    p = make_workload(args.config)
+    base, times = cpu_sample_for(args, p, steps=args.steps, warmup=args.warmup)
     t = float(np.mean(times))
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": base["sample"]},
+            "config": {"workload": WORKLOAD_SLAB if args.config == "slab" else WORKLOAD, "sample": base["sample"]},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -211,17 +227,19 @@ def run_ours(args):
     b.load()
     stream = torch.cuda.current_stream()
 
-    p = make_workload()
-    nq = len(p.qpoints)
+    p = make_workload(args.config)
+    iqs = workload_qpoints(args, p)
+    nq = len(iqs)
     om, W = b.rpa_gauss_legendre(p.nw, 1.0)
-    wq = [qp.weight for qp in p.qpoints]
-    iqs = list(range(nq))
-    Kq = pairs_per_q(p)
+    wq = [p.qpoints[i].weight for i in iqs]
+    Kall = pairs_per_q(p)
+    Kq = [Kall[i] for i in iqs]
 
     def make_ctx(precision):
         ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, precision, device=local,
                            stream=stream.cuda_stream)
-        ngs = b.load_problem(ctx, p, paw_Q=lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))
+        ngs = b.load_problem(ctx, p, qs=iqs,
+                             paw_Q=lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))
         return ctx, ngs
 
     ctx, ngs = make_ctx(args.precision)
@@ -261,11 +279,11 @@ def run_ours(args):
     pinned = []
     for s in p.sets:
         pinned.append((torch.from_numpy(s.C).pin_memory(), torch.from_numpy(s.P).pin_memory()))
-    Qpin = []
+    Qpin = {}
     for iq in iqs:
         gm = b.rpa_gvectors(ctx, iq)
-        Qpin.append(torch.from_numpy(syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm)).pin_memory())
-    h2d = sum(c.numel() * 16 + pp.numel() * 16 for c, pp in pinned) + sum(q.numel() * 16 for q in Qpin)
+        Qpin[iq] = torch.from_numpy(syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm)).pin_memory()
+    h2d = sum(c.numel() * 16 + pp.numel() * 16 for c, pp in pinned) + sum(q.numel() * 16 for q in Qpin.values())
     h2d += sum(s.miller.nbytes + s.eps.nbytes + s.f.nbytes for s in p.sets)
     d2h = 8 * (1 + nq * p.nw)
 
@@ -291,8 +309,9 @@ def run_ours(args):
 
     # plain FP64 form on one q-point for the mixed-vs-FP64 statement
     fp64 = None
-    if args.fp64_q >= 0:
+    if args.fp64_q >= 0 and args.config == "bulk":
         iq = args.fp64_q
+        pos = iqs.index(iq)
         ctx64, ngs64 = make_ctx("fp64")
         b.rpa_set_profiling(ctx64, True)
         barrier()
@@ -304,7 +323,7 @@ def run_ours(args):
         ms64, _ = b.rpa_get_profile(ctx64)
         b.rpa_destroy(ctx64)
         Emix, tmix = b.rpa_energy(ctx, [iq], [1.0], om, W)
-        f64 = rankk_flops([ngs64[iq]], [Kq[iq]], p.nw)
+        f64 = rankk_flops([ngs64[pos]], [Kq[pos]], p.nw)
         fp64 = {"q": iq, "s_per_q": s64, "chi0_tflops": f64 / s64 / 1e12,
                 "rankk_ms": ms64[2], "logdet_ms": ms64[3],
                 "speedup_mixed_vs_fp64": s64 / (t_step / nq),
@@ -323,7 +342,7 @@ def run_ours(args):
     achieved = flops / (herk_ms / 1e3) / 1e12
     base = None
     if rank == 0 and not args.no_cpu:
-        base, _ = cpu_sample(p, steps=1, warmup=0)
+        base, _ = cpu_sample_for(args, p, steps=1, warmup=0)
     b.rpa_destroy(ctx)
     if rank != 0:
         return
@@ -334,8 +353,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x2": "bf16x2->f32",
                                        "bf16x3": "bf16x3->f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "q_points": nq, "NG": ngs,
-                   "pairs_per_q": Kq, "nw": p.nw, "l2": "inputs larger than L2 (grids 5 GB, N 185 MB per k)",
+        "config": {"workload": WORKLOAD_SLAB if args.config == "slab" else WORKLOAD, "precision": args.precision,
+                   "q_points": nq, "NG": ngs,
+                   "pairs_per_q": Kq, "nw": p.nw, "l2": "inputs larger than L2 (grids >= 1.4 GB, rank-k operands >= 3 GB per block)",
                    "parallelism": f"replicas x{world}"},
         "s_per_q": t_step / nq,
         "E_c": E,
@@ -346,13 +366,75 @@ def run_ours(args):
         "gpu_launches": int(launches.sum()),
         "roofline": {"bound": bound, "kernel": "rank-k update (Eq. 17)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": herk_traffic() if bound == "tensor" else None,
+                     "traffic": herk_traffic() if (bound == "tensor" and args.config == "bulk") else None,
                      "traffic_note": "ncu DRAM read+write bytes of one launch of the profiling case (one k-block, "
                                      "NG 1180); null once the kernel source differs from the captured one",
                      "peak_source": peak_kind if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x max clock"},
         "clocks": clk.summary(),
         "cpu_baseline": base,
     }
+    print(json.dumps(line))
+
+
+def run_backward(args):
+    """Gradient workload: the bulk geometry at one q = (1/2, 0, 0) with all 8
+    k-points and 16 occupied + 1200 empty bands per set; one step is
+    rpa_energy_backward for dE_c/dchi0, dE_c/dC and dE_c/dP of every set (the
+    forward pass included), outputs in device memory."""
+    import torch
+    from paper_1307_8052_gb300 import binding as b
+    from paper_1307_8052_gb300 import synthetic as syn
+    from paper_1307_8052_gb300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    b.load()
+    stream = torch.cuda.current_stream()
+    p = syn.config1()
+    iq = [i for i, qp in enumerate(p.qpoints) if np.allclose(qp.q_red, [0.5, 0.0, 0.0])][0]
+    om, W = b.rpa_gauss_legendre(p.nw, 1.0)
+    ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, args.precision,
+                       stream=stream.cuda_stream)
+    ng = b.load_problem(ctx, p, qs=[iq], paw_Q=lambda i, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[i].q_red, gm))[0]
+    K = pairs_per_q(p)[iq]
+    dev = torch.device("cuda")
+    dC = [torch.zeros(s.C.shape, dtype=torch.complex128, device=dev) for s in p.sets]
+    dP = [torch.zeros(s.P.shape, dtype=torch.complex128, device=dev) for s in p.sets]
+    dchi = [torch.zeros((p.nw, ng, ng), dtype=torch.complex128, device=dev)]
+    sets = list(range(len(p.sets)))
+    wq = [p.qpoints[iq].weight]
+
+    def step():
+        return b.rpa_energy_backward(ctx, [iq], wq, om, W, 1.0, sets, dC, dP, dchi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    b.rpa_set_profiling(ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_ms = np.zeros(b.RPA_NSTAGES)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            E = step()
+            stage_ms += b.rpa_get_profile(ctx)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / args.steps / 1e3
+    b.rpa_destroy(ctx)
+    f_fwd = rankk_flops([ng], [K], p.nw)
+    f_bwd = 8.0 * ng * ng * K * p.nw  # N-bar = 2 sum_w w Gamma_w n: one complex NG x NG by NG x K product per w
+    stage_names = ["wf_to_grid", "pair_density_paw", "rankk_kernel", "logdet", "other_and_adjoint",
+                   "rankk_operand_prep"]
+    line = {"metric": "E_c gradient (dE/dchi0, dE/dC, dE/dP incl. forward) TFLOP/s on 1 GB300",
+            "value": (f_fwd + f_bwd) / t / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "gradient: bulk 9 bohr box, 40^3 grid, q=(1/2,0,0), 8 k, 16 occ + 1200 empty "
+                                   "bands, NG %d, 16 iw, 3x13 PAW" % ng, "pairs": K,
+                       "flops": {"forward_rankk": f_fwd, "adjoint_nbar": f_bwd}},
+            "E_c_q": E, "stage_ms_per_step": {n: float(m / args.steps) for n, m in zip(stage_names, stage_ms)},
+            "clocks": clk.summary()}
     print(json.dumps(line))
 
 
@@ -447,13 +529,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sustained", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--config", choices=["bulk", "batched"], default="bulk")
+    ap.add_argument("--config", choices=["bulk", "slab", "batched", "backward"], default="bulk")
+    ap.add_argument("--slab-q", type=int, default=1, help="q-points per step of the slab workload")
     ap.add_argument("--instances", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batched":
         run_batched(args)
+    elif args.config == "backward":
+        run_backward(args)
     else:
         run_ours(args)
 

@@ -205,6 +205,35 @@ def config1(nocc: int = 16, nunocc: int = 1200, with_paw: bool = True) -> Proble
                    sets, qps, 16, paw)
 
 
+def config2(nocc: int = 120, nunocc: int = 3000, kidx=None, with_paw: bool = True) -> Problem:
+    """Surface slab: 9.4 x 8.1 x 40 bohr cell, 48 x 40 x 200 grid, 20 Ha orbitals
+    (13039 plane waves at Gamma), Gamma-centred 4 x 2 x 1 in-plane k-mesh whose
+    8 points are also the 8 q-points (k+q stays on the mesh, with umklapp),
+    7.55 Ha response cutoff (NG 2988-3058), 16 frequencies, 16 PAW atoms x 18
+    projectors + 2 x 8.  ``kidx`` keeps a subset of the k-points (the q-points
+    then pair only kept k with kept k+q)."""
+    cell = np.diag([9.4, 8.1, 40.0])
+    kmesh = [np.array([i / 4.0, j / 2.0, 0.0]) for i in range(4) for j in range(2)]
+    keep = list(range(len(kmesh))) if kidx is None else list(kidx)
+    sets = [make_orbitals(2, i, cell, kmesh[i], 20.0, nocc, nunocc) for i in keep]
+    paw = None
+    if with_paw:
+        paw = make_paw_setup(2, [18] * 16 + [8] * 2)
+        for s_, i in zip(sets, keep):
+            s_.P = make_projections(2, i, s_.C.shape[0], int(paw.nproj.sum()))
+    qps = []
+    pos = {i: n for n, i in enumerate(keep)}
+    for qp in mesh_qpoints(kmesh, kmesh):
+        sel = [t for t in range(len(qp.k_of)) if int(qp.k_of[t]) in pos and int(qp.kq_of[t]) in pos]
+        if not sel:
+            continue
+        qps.append(QPoint(qp.q_red, np.array([pos[int(qp.k_of[t])] for t in sel], np.int32),
+                          np.array([pos[int(qp.kq_of[t])] for t in sel], np.int32),
+                          qp.G0[sel].reshape(-1, 3), qp.weight))
+    return Problem("config2-slab-48x40x200", 2, cell, (48, 40, 200), 20.0, 7.55, 2.0, 8,
+                   sets, qps, 16, paw)
+
+
 def config3_instance(i: int, nw: int = 16) -> Problem:
     """One (q, cell) instance of the batched workload: the bulk box of config 1
     (9 bohr, 40^3 grid, 20 Ha orbitals), Gamma k-point, q drawn from the

@@ -121,3 +121,44 @@ def test_backward_central_differences_fp64():
             assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (which, fd, an)
     finally:
         b.rpa_destroy(ctx)
+
+
+def test_config4_geometry_central_differences_fp64():
+    """Gradient workload geometry (bulk box, 40^3 grid, all 8 k-points, q = (1/2, 0, 0),
+    3 x 13 projectors, NG ~ 1200, 16 frequencies) on a band subset (16 occupied +
+    100 empty per set): directional derivatives of the FP64 energy along random
+    directions of C and P against the fourth-order central difference
+    [8(E(h) - E(-h)) - (E(2h) - E(-2h))] / 12h with h = 1e-5 (truncation O(h^4);
+    at this size the second-order quotient with h = 1e-6 is itself only good
+    to ~1.5e-6)."""
+    full = syn.config1(nocc=16, nunocc=100)
+    iq = [i for i, qp in enumerate(full.qpoints) if np.allclose(qp.q_red, [0.5, 0.0, 0.0])][0]
+    p = syn.Problem(full.name, 4, full.cell, full.grid, full.ecut_wf, full.ecut_chi, full.spin_factor,
+                    full.nk_bz, full.sets, [full.qpoints[iq]], 16, full.paw)
+    om, W = o.frequency_grid(p.nw)
+    ctx = _ctx(p, "fp64")
+    try:
+        E0, dC, dP, dchi = _grad(ctx, p, om, W, [0])
+        assert dchi[0].shape[1] > 1000
+        rng = np.random.default_rng(4)
+        h = 1e-5
+        for trial, (s, which) in enumerate([(0, "C"), (3, "C"), (6, "C"), (1, "P"), (5, "P")]):
+            base = getattr(p.sets[s], which).copy()
+            d = rng.standard_normal(base.shape) + 1j * rng.standard_normal(base.shape)
+            vals = []
+            for sign in (1, -1, 2, -2):
+                new = base + sign * h * d
+                if which == "C":
+                    b.rpa_set_orbitals(ctx, s, p.sets[s].k_red, p.sets[s].miller, new, p.sets[s].eps, p.sets[s].f)
+                    b.rpa_set_paw(ctx, s, p.paw.nproj, p.sets[s].P)
+                else:
+                    b.rpa_set_paw(ctx, s, p.paw.nproj, new)
+                vals.append(b.rpa_energy(ctx, [0], [p.qpoints[0].weight], om, W)[0])
+            b.rpa_set_orbitals(ctx, s, p.sets[s].k_red, p.sets[s].miller, p.sets[s].C, p.sets[s].eps, p.sets[s].f)
+            b.rpa_set_paw(ctx, s, p.paw.nproj, p.sets[s].P)
+            fd = (8.0 * (vals[0] - vals[1]) - (vals[2] - vals[3])) / (12.0 * h)
+            g = dC[s] if which == "C" else dP[s]
+            an = float(np.sum(np.conj(g) * d).real)
+            assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (which, s, fd, an)
+    finally:
+        b.rpa_destroy(ctx)

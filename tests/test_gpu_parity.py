@@ -194,6 +194,30 @@ def test_config1_full_size_sampled_bf16x2():
     assert np.all(np.einsum("wii->wi", chi).real <= 0)
 
 
+@pytest.fixture(scope="module")
+def slab_case():
+    """Slab geometry (9.4 x 8.1 x 40 bohr, 48 x 40 x 200 grid, 13039 plane waves,
+    NG = 3058, 16 x 18 + 2 x 8 projectors) on a band subset: k = Gamma and
+    (0, 1/2, 0), q = (0, 1/2, 0) with one umklapp transition, 8 frequencies."""
+    p = syn.config2(nocc=3, nunocc=40, kidx=[0, 1])
+    iq = 1
+    assert np.abs(p.qpoints[iq].G0).sum() > 0
+    om, _ = o.frequency_grid(8)
+    return p, iq, om, o.chi0(p, iq, om, _oracle_Q(p, iq))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x2"])
+def test_config2_slab_geometry(slab_case, precision):
+    p, iq, om, ref = slab_case
+    ctx = _ctx(p, precision, iqs=[iq])
+    try:
+        chi = b.rpa_chi0(ctx, iq, om)
+    finally:
+        b.rpa_destroy(ctx)
+    assert chi.shape == ref.shape and ref.shape[1] > 3000
+    assert _rel(chi, ref) < TOL[precision]["chi"]
+
+
 def test_tuning_knobs_change_rounding_only():
     p = syn.small_problem(config_tag=95)
     om, _ = o.frequency_grid(4)
