@@ -165,7 +165,32 @@ __device__ inline void load_twiddle_matrix(c2<T>* tw, const c2<T>* __restrict__ 
 // instance computes NO <= 16 outputs per chunk (NO = 16 for several chunks).
 constexpr int TS = 16;
 
-template <typename T, int NO, int PP>
+// Per-thread cp.async ring: the transform kernels stream one grid line per
+// thread, so each thread prefetches its own next PF-1 slices into private
+// shared-memory slots (no block barrier needed) and the loads of several
+// iterations are in flight at once.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(c2<T>* dst_smem, const c2<T>* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(c2<T>) == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// byte offset of the ring after a twiddle table of n entries
+template <typename T>
+__host__ __device__ constexpr int ring_offset(int n) {
+  return (int)(((size_t)n * TS * sizeof(c2<T>) + 15) / 16 * 16);
+}
+constexpr int RING_PF = 4;       // stages of the ring
+constexpr int RING_THREADS = 256;
+
+template <typename T, int NO, int PP, int PF>
 __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
                                                         int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
                                                         const int* __restrict__ Ridx, int nR, int64_t p0, int np,
@@ -199,30 +224,65 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
       for (int q = 0; q < PP; ++q)
 #pragma unroll
         for (int t = 0; t < NO; ++t) acc[q][t] = mk<T>(0, 0);
-      // the next j1 slice of both grids is loaded while the current one is used
-      c2<T> nxt_n[PP], nxt_m[PP];
-#pragma unroll
-      for (int q = 0; q < PP; ++q) {
-        nxt_n[q] = un[q][0];
-        nxt_m[q] = um[q][0];
-      }
-      for (int j1 = 0; j1 < N1; ++j1) {
-        c2<T> x[PP];
-#pragma unroll
-        for (int q = 0; q < PP; ++q) x[q] = cj_mul<T>(nxt_n[q], nxt_m[q]);
-        if (j1 + 1 < N1) {
+      if constexpr (PF > 1) {
+        // slot (stage st, value v) of this thread: ring[(st * 2 PP + v) * 256 + tid]
+        c2<T>* my = reinterpret_cast<c2<T>*>(smem_raw + ring_offset<T>(N1)) + threadIdx.x;
+        auto issue = [&](int j) {
+          const int st = j % PF;
 #pragma unroll
           for (int q = 0; q < PP; ++q) {
-            nxt_n[q] = un[q][(int64_t)(j1 + 1) * N23];
-            nxt_m[q] = um[q][(int64_t)(j1 + 1) * N23];
+            cp_async_elem<T>(my + (st * 2 * PP + 2 * q) * RING_THREADS, un[q] + (int64_t)j * N23);
+            cp_async_elem<T>(my + (st * 2 * PP + 2 * q + 1) * RING_THREADS, um[q] + (int64_t)j * N23);
+          }
+        };
+#pragma unroll
+        for (int j = 0; j < PF - 1; ++j) {
+          if (j < N1) issue(j);
+          cp_async_commit();
+        }
+        for (int j1 = 0; j1 < N1; ++j1) {
+          if (j1 + PF - 1 < N1) issue(j1 + PF - 1);
+          cp_async_commit();
+          cp_async_wait<PF - 1>();  // the group of slice j1 has landed
+          const int st = j1 % PF;
+          c2<T> x[PP];
+#pragma unroll
+          for (int q = 0; q < PP; ++q)
+            x[q] = cj_mul<T>(my[(st * 2 * PP + 2 * q) * RING_THREADS], my[(st * 2 * PP + 2 * q + 1) * RING_THREADS]);
+          const c2<T>* twj = tw + j1 * TS;
+#pragma unroll
+          for (int t = 0; t < NO; ++t) {
+            const c2<T> f = twj[t];
+#pragma unroll
+            for (int q = 0; q < PP; ++q) cmac<T>(acc[q][t], x[q], f);
           }
         }
-        const c2<T>* twj = tw + j1 * TS;
+      } else {
+        // the next j1 slice of both grids is loaded while the current one is used
+        c2<T> nxt_n[PP], nxt_m[PP];
 #pragma unroll
-        for (int t = 0; t < NO; ++t) {
-          const c2<T> f = twj[t];
+        for (int q = 0; q < PP; ++q) {
+          nxt_n[q] = un[q][0];
+          nxt_m[q] = um[q][0];
+        }
+        for (int j1 = 0; j1 < N1; ++j1) {
+          c2<T> x[PP];
 #pragma unroll
-          for (int q = 0; q < PP; ++q) cmac<T>(acc[q][t], x[q], f);
+          for (int q = 0; q < PP; ++q) x[q] = cj_mul<T>(nxt_n[q], nxt_m[q]);
+          if (j1 + 1 < N1) {
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+              nxt_n[q] = un[q][(int64_t)(j1 + 1) * N23];
+              nxt_m[q] = um[q][(int64_t)(j1 + 1) * N23];
+            }
+          }
+          const c2<T>* twj = tw + j1 * TS;
+#pragma unroll
+          for (int t = 0; t < NO; ++t) {
+            const c2<T> f = twj[t];
+#pragma unroll
+            for (int q = 0; q < PP; ++q) cmac<T>(acc[q][t], x[q], f);
+          }
         }
       }
 #pragma unroll
@@ -239,21 +299,34 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
   }
 }
 
-template <typename T, int NO>
-static cudaError_t launch_stageA_no(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+template <typename T, int NO, int PF>
+static cudaError_t launch_stageA_pf(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
                                     const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
                                     cudaStream_t s) {
   constexpr int PP = sizeof(T) == 4 ? 2 : 1;
   const int64_t total = (int64_t)((np + PP - 1) / PP) * N23;
   if (total == 0) return cudaSuccess;
-  const int smem = N1 * TS * (int)sizeof(c2<T>);
+  const int smem = PF > 1 ? ring_offset<T>(N1) + PF * 2 * PP * RING_THREADS * (int)sizeof(c2<T>)
+                          : N1 * TS * (int)sizeof(c2<T>);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(pd_stageA_kernel<T, NO, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(pd_stageA_kernel<T, NO, PP, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  pd_stageA_kernel<T, NO, PP><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np,
-                                                                     tw, n1, T1);
+  pd_stageA_kernel<T, NO, PP, PF><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0,
+                                                                         np, tw, n1, T1);
   return cudaGetLastError();
+}
+
+// the ring needs PF * 2 PP * 256 slots next to the twiddle table; very long
+// axes (table beyond 160 KB) fall back to one-slice register prefetch
+template <typename T, int NO>
+static cudaError_t launch_stageA_no(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+                                    const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
+                                    cudaStream_t s) {
+  if (ring_offset<T>(N1) <= 160 * 1024)
+    return launch_stageA_pf<T, NO, RING_PF>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+  return launch_stageA_pf<T, NO, 1>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
 }
 
 // compute width: the smallest of 8, 12, 14, 16 that holds all outputs (16 with chunks beyond)
@@ -274,7 +347,7 @@ cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int 
 // ---------------------------------------------------------------- pair density stage B
 // T2[pl][o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i g2 j2 / N2), g2 = g2lo + o2
 // (also used transposed by the adjoint: input axis length N2 -> output axis length n2)
-template <typename T, int NO>
+template <typename T, int NO, int PF>
 __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict__ T1, c2<T>* __restrict__ T2,
                                                         int64_t rows, int N2, int N3,
                                                         const c2<T>* __restrict__ twg, int n2) {
@@ -295,13 +368,32 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
       c2<T> acc[NO];
 #pragma unroll
       for (int t = 0; t < NO; ++t) acc[t] = mk<T>(0, 0);
-      c2<T> nxt = src[0];
-      for (int j2 = 0; j2 < N2; ++j2) {
-        const c2<T> x = nxt;
-        if (j2 + 1 < N2) nxt = src[(int64_t)(j2 + 1) * N3];
-        const c2<T>* twj = tw + j2 * TS;
+      if constexpr (PF > 1) {
+        c2<T>* my = reinterpret_cast<c2<T>*>(smem_raw + ring_offset<T>(N2)) + threadIdx.x;
 #pragma unroll
-        for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x, twj[t]);
+        for (int j = 0; j < PF - 1; ++j) {
+          if (j < N2) cp_async_elem<T>(my + j * RING_THREADS, src + (int64_t)j * N3);
+          cp_async_commit();
+        }
+        for (int j2 = 0; j2 < N2; ++j2) {
+          const int jn = j2 + PF - 1;
+          if (jn < N2) cp_async_elem<T>(my + (jn % PF) * RING_THREADS, src + (int64_t)jn * N3);
+          cp_async_commit();
+          cp_async_wait<PF - 1>();  // the group of slice j2 has landed
+          const c2<T> x = my[(j2 % PF) * RING_THREADS];
+          const c2<T>* twj = tw + j2 * TS;
+#pragma unroll
+          for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x, twj[t]);
+        }
+      } else {
+        c2<T> nxt = src[0];
+        for (int j2 = 0; j2 < N2; ++j2) {
+          const c2<T> x = nxt;
+          if (j2 + 1 < N2) nxt = src[(int64_t)(j2 + 1) * N3];
+          const c2<T>* twj = tw + j2 * TS;
+#pragma unroll
+          for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x, twj[t]);
+        }
       }
       c2<T>* dst = T2 + (r * n2 + o0) * N3 + j3;
 #pragma unroll
@@ -311,16 +403,23 @@ __global__ void __launch_bounds__(256) pd_stageB_kernel(const c2<T>* __restrict_
   }
 }
 
+template <typename T, int NO, int PF>
+static cudaError_t launch_stageB_pf(const c2<T>* T1, c2<T>* T2, int64_t rows, int N2, int N3, const c2<T>* tw, int n2,
+                                    cudaStream_t s) {
+  const int smem = PF > 1 ? ring_offset<T>(N2) + PF * RING_THREADS * (int)sizeof(c2<T>) : N2 * TS * (int)sizeof(c2<T>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pd_stageB_kernel<T, NO, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  pd_stageB_kernel<T, NO, PF><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, tw, n2);
+  return cudaGetLastError();
+}
+
 template <typename T, int NO>
 static cudaError_t launch_stageB_no(const c2<T>* T1, c2<T>* T2, int64_t rows, int N2, int N3, const c2<T>* tw, int n2,
                                     cudaStream_t s) {
-  const int smem = N2 * TS * (int)sizeof(c2<T>);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(pd_stageB_kernel<T, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  pd_stageB_kernel<T, NO><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, tw, n2);
-  return cudaGetLastError();
+  if (ring_offset<T>(N2) <= 160 * 1024) return launch_stageB_pf<T, NO, RING_PF>(T1, T2, rows, N2, N3, tw, n2, s);
+  return launch_stageB_pf<T, NO, 1>(T1, T2, rows, N2, N3, tw, n2, s);
 }
 
 template <typename T>
