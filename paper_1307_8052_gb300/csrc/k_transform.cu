@@ -461,20 +461,25 @@ __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict_
     const int step = pmod(-(int64_t)g3, N3);
     c2<T> acc[PG];
     int64_t pidx[PG];
+    const c2<T>* src[PG];
 #pragma unroll
     for (int q = 0; q < PG; ++q) {
       const int pl = min(grp * PG + q, np - 1);
       pidx[q] = p0 + pl;
-      const c2<T>* src = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
-      int idx = 0;
-      c2<T> s = mk<T>(0, 0);
-      for (int j3 = 0; j3 < N3; ++j3) {
-        cmac<T>(s, src[j3], tw[idx]);
-        idx += step;
-        if (idx >= N3) idx -= N3;
-      }
-      acc[q] = mk<T>(s.x * scale, s.y * scale);
+      src[q] = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
+      acc[q] = mk<T>(0, 0);
     }
+    // the PG pairs advance together: four independent loads per step
+    int idx = 0;
+    for (int j3 = 0; j3 < N3; ++j3) {
+      const c2<T> f = tw[idx];
+#pragma unroll
+      for (int q = 0; q < PG; ++q) cmac<T>(acc[q], src[q][j3], f);
+      idx += step;
+      if (idx >= N3) idx -= N3;
+    }
+#pragma unroll
+    for (int q = 0; q < PG; ++q) acc[q] = mk<T>(acc[q].x * scale, acc[q].y * scale);
     if (KP > 0) {
       const int64_t a0 = pidx[0] / nR;
       bool same = true;
