@@ -524,7 +524,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16x2"], default="bf16x2")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16x2", "bf16x3"], default="bf16x2")
     ap.add_argument("--fp64-q", type=int, default=3, help="q-point timed in plain FP64 (-1: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sustained", action="store_true")

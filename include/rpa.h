@@ -60,7 +60,8 @@ typedef enum {
  * RPA_BF16X2 : pair densities in FP32; rank-k update on the tensor cores with
  *              each operand split into two bfloat16 terms (hi + lo, three
  *              products), FP32 accumulation in tensor memory, FP64 chi0.
- * RPA_BF16X3 : as BF16X2 with three bfloat16 terms (six products).
+ * RPA_BF16X3 : as BF16X2 with three bfloat16 terms (hi + mid + lo, about
+ *              24 bits per operand) and six products (hh, hm, mh, mm, hl, lh).
  * In every mode the PAW projection products, the log-det and the frequency
  * quadrature run in FP64. */
 typedef enum {

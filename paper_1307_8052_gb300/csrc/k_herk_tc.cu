@@ -511,23 +511,25 @@ size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int terms) {
   return op * (size_t)terms * (size_t)(nw + 2);
 }
 
-template <int BK, int STAGES>
+template <int TERMS, int BK, int STAGES>
 static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpad, int64_t Kpad, int fold64, int flush,
                                double2* chi, int* err, cudaStream_t s) {
   using namespace tc;
-  using C = Cfg<2, BK, STAGES>;
+  using C = Cfg<TERMS, BK, STAGES>;
+  static_assert(C::SMEM_BYTES <= 227 * 1024, "shared-memory ring too large");
   const int nk = (int)(Kpad / BK);
   const int fold = fold64 * (64 / BK);  // the fold length is counted in 64-element units
-  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<2, BK, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       C::SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<TERMS, BK, STAGES>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  herk_tc_kernel<2, BK, STAGES><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, fold, flush, chi, err);
+  herk_tc_kernel<TERMS, BK, STAGES><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, fold, flush, chi,
+                                                                            err);
   return cudaGetLastError();
 }
 
 // Bounds shared by the two calls below.
 static cudaError_t check_args(int64_t P, int NG, int nw, int terms, size_t scratch_bytes) {
-  if (terms != 2) return cudaErrorInvalidValue;
+  if (terms != 2 && terms != 3) return cudaErrorInvalidValue;
   const tc::Geometry g = tc::geometry(P, NG);
   if (scratch_bytes < herk_tc_scratch_bytes(P, NG, nw, terms)) return cudaErrorInvalidValue;
   if (g.Kpad > (int64_t)1 << 31 || (int64_t)nw * g.NGpad > (1 << 30)) return cudaErrorInvalidValue;
@@ -557,10 +559,17 @@ cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt
   const Geometry g = geometry(P, NG);
   const Operands o = operands(scratch, g, terms);
   dim3 pg(g.NGpad / 32, (unsigned)(g.Ppad / 32));
-  prep_xz_kernel<2><<<pg, 256, 0, s>>>(N, P, NG, g.NGpad, g.Kpad, (__nv_bfloat162*)o.X, (__nv_bfloat162*)o.Z,
-                                       o.op_elems / 2);
-  prep_a_kernel<2><<<pg, 256, 0, s>>>(N, wgt, P, NG, g.NGpad, g.Kpad, nw, (__nv_bfloat162*)o.A,
-                                      o.op_elems * nw / 2);
+  if (terms == 3) {
+    prep_xz_kernel<3><<<pg, 256, 0, s>>>(N, P, NG, g.NGpad, g.Kpad, (__nv_bfloat162*)o.X, (__nv_bfloat162*)o.Z,
+                                         o.op_elems / 2);
+    prep_a_kernel<3><<<pg, 256, 0, s>>>(N, wgt, P, NG, g.NGpad, g.Kpad, nw, (__nv_bfloat162*)o.A,
+                                        o.op_elems * nw / 2);
+  } else {
+    prep_xz_kernel<2><<<pg, 256, 0, s>>>(N, P, NG, g.NGpad, g.Kpad, (__nv_bfloat162*)o.X, (__nv_bfloat162*)o.Z,
+                                         o.op_elems / 2);
+    prep_a_kernel<2><<<pg, 256, 0, s>>>(N, wgt, P, NG, g.NGpad, g.Kpad, nw, (__nv_bfloat162*)o.A,
+                                        o.op_elems * nw / 2);
+  }
   return cudaGetLastError();
 }
 
@@ -572,7 +581,9 @@ cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fold_stages, i
   if (e != cudaSuccess) return e;
   if (fold_stages < 1) fold_stages = 1;
   if (flush_folds < 1) flush_folds = 1;
-  const int bk = pipe == 1 ? 32 : 64;
+  // three terms: 9 tiles a stage, so 32-element stages x 3 (217 KB); two
+  // terms: 64-element stages x 2 (default) or 32-element stages x 4
+  const int bk = (terms == 3 || pipe == 1) ? 32 : 64;
   const Geometry g = geometry(P, NG);
   const Operands o = operands(scratch, g, terms);
   Maps maps;
@@ -585,8 +596,10 @@ cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fold_stages, i
   }
   const int nt = g.NGpad / BM;
   dim3 grid(nt * (nt + 1) / 2, nw);
-  if (bk == 32) return launch_gemm<32, 4>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
-  return launch_gemm<64, 2>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
+  if (terms == 3)
+    return launch_gemm<3, 32, 3>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
+  if (bk == 32) return launch_gemm<2, 32, 4>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
+  return launch_gemm<2, 64, 2>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
 }
 
 }  // namespace rpa

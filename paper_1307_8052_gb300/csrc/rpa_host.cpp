@@ -381,9 +381,10 @@ struct Block {
 // plain (nL x nR) rectangle.  Rows per block bound the N and operand buffers.
 int rows_per_block(const rpa_ctx* c, int nL, int nR, int NG, int nw) {
   const int64_t NGpad = (NG + 127) / 128 * 128;
-  // tensor-core operands: NGpad * 2P * 2 terms * 2 B * (nw + 2); pair densities: P * NG * 8-16 B
+  // tensor-core operands: NGpad * 2P * terms * 2 B * (nw + 2); pair densities: P * NG * 8-16 B
   const int64_t budget = c->tune[RPA_TUNE_OPERAND_MB] << 20;
-  int64_t pmax = budget / (NGpad * 8 * (nw + 2));
+  const int64_t terms = c->prm.precision == RPA_BF16X3 ? 3 : 2;
+  int64_t pmax = budget / (NGpad * 4 * terms * (nw + 2));
   if (c->prm.precision == RPA_FP64 || c->prm.precision == RPA_FP32) pmax = budget / (16 * (int64_t)NG);
   int64_t rows = std::max<int64_t>(1, pmax / std::max(1, nR));
   return (int)std::min<int64_t>(rows, nL);
@@ -919,7 +920,7 @@ rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
   for (int i = 0; i < 3; ++i)
     if (p->grid[i] < 2 || p->grid[i] > kMaxGrid) return RPA_ERR_ARG;
   if (!(p->ecut_chi > 0.0) || !(p->spin_factor > 0.0) || p->nk_bz < 1) return RPA_ERR_ARG;
-  if (p->precision < RPA_FP64 || p->precision > RPA_BF16X2) return RPA_ERR_ARG;
+  if (p->precision < RPA_FP64 || p->precision > RPA_BF16X3) return RPA_ERR_ARG;
   const double* a = p->cell;
   const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
                      a[2] * (a[3] * a[7] - a[4] * a[6]);

@@ -48,7 +48,7 @@ def _rel(a, r):
     return np.abs(a - r).max() / max(np.abs(r).max(), 1e-300)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-5), ("bf16x2", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-5), ("bf16x2", 1e-4), ("bf16x3", 2e-5)])
 def test_backward_matches_oracle_gradient(precision, tol):
     p = _problem()
     om, W = o.frequency_grid(p.nw)

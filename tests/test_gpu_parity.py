@@ -20,6 +20,7 @@ TOL = {
     "fp64": dict(chi=1e-11, ec=1e-10, term=1e-10),
     "fp32": dict(chi=4e-6, ec=1e-6, term=1e-6),
     "bf16x2": dict(chi=2e-5, ec=1e-6, term=5e-6),
+    "bf16x3": dict(chi=4e-6, ec=1e-6, term=1e-6),
 }
 
 
@@ -49,7 +50,7 @@ def _rel(a, b_):
     return np.abs(a - b_).max() / np.abs(b_).max()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2", "bf16x3"])
 def test_config0_chi_and_energy(precision):
     p = syn.config0()
     om, W = o.frequency_grid(p.nw)
@@ -83,7 +84,7 @@ def test_config0_matches_stored_terms():
     assert np.max(np.abs(terms[0] - t[:, 3])) <= TOL["fp64"]["term"] * np.max(np.abs(t[:, 3]))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2", "bf16x3"])
 def test_small_mesh_umklapp_paw_all_q(precision):
     """2x1x1 mesh (umklapp at q = 1/2), ragged Miller boxes, two PAW atoms."""
     p = syn.small_problem()
@@ -130,7 +131,7 @@ def test_device_pointers_match_host():
         b.rpa_destroy(ctx_d)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x2", "bf16x3"])
 def test_config1_geometry_two_transitions(precision):
     """Full config-1 geometry (9 bohr box, 40^3 grid, 20 Ha orbitals, NG ~ 1200,
     3 x 13 projectors) with a band subset and two transitions of q = (0, 1/2, 1/2),
@@ -228,6 +229,11 @@ def test_tuning_knobs_change_rounding_only():
         b.rpa_set_tuning(ctx, b.RPA_TUNE_PAIR_CHUNK, 7)
         c = b.rpa_chi0(ctx, 1, om)
         assert _rel(c, a) < TOL["bf16x2"]["chi"]
+        # 32-element K stages x 4 with the 64-byte swizzle
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FOLD, 1)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PIPE, 1)
+        d = b.rpa_chi0(ctx, 1, om)
+        assert _rel(d, a) < TOL["bf16x2"]["chi"]
         with pytest.raises(b.RpaError) as e:
             b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FOLD, 0)
         assert e.value.status == b.RPA_ERR_ARG
