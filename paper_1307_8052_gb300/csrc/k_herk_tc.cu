@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 
 namespace rpa {
@@ -166,10 +167,23 @@ struct Maps {
   CUtensorMap z[3];  // Z terms
 };
 
-template <int TERMS, int BK, int STAGES>
+// Extra arguments of the weighted-product variant (GEMM = true): the adjoint
+// of the rank-k update, out[p][g] = 2 sum_w wgt[w][p] sum_k N[p][k] conj(Gam_w[k][g])
+// (Eq. 17 transposed).  A holds the pair densities (rows p, shared by all w),
+// X / Z the per-frequency Gam (rows w * NGpad + g); K runs over w and k, and
+// the weight of row p is applied to every fold as it leaves tensor memory.
+struct GemmArgs {
+  int64_t P;          // rows (pairs)
+  int nkw;            // K stages per frequency
+  int ngt;            // column tiles (NGpad / BN)
+  const float* wgt;   // [nw][P]
+  float2* out;        // [P][NG]
+};
+
+template <int TERMS, int BK, int STAGES, bool GEMM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     herk_tc_kernel(const __grid_constant__ Maps maps, int NG, int NGpad, int nk, int fold, int flush, double2* __restrict__ chi,
-                   int* __restrict__ err) {
+                   int* __restrict__ err, const GemmArgs ga) {
   using C = Cfg<TERMS, BK, STAGES>;
   constexpr int TILE_BYTES = C::TILE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -185,7 +199,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int w = blockIdx.y;
   int ti, tj;
-  tri_tile(blockIdx.x, ti, tj);
+  if constexpr (GEMM) {
+    ti = blockIdx.x / ga.ngt;  // row tile of pairs
+    tj = blockIdx.x % ga.ngt;
+  } else {
+    tri_tile(blockIdx.x, ti, tj);
+  }
   const int i0 = ti * BM, j0 = tj * BN;
   const int nfold = (nk + fold - 1) / fold;
 
@@ -225,13 +244,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         mbar_expect_tx(&full[s], C::STAGE_BYTES);
         unsigned char* st = smem + s * C::STAGE_BYTES;
-        const int k = kb * BK;
+        // HERK: A rows w * NGpad + i0 (weighted per frequency), X / Z rows j0;
+        // GEMM: A rows i0 (pairs), X / Z rows wk * NGpad + j0 of frequency wk
+        const int wk = GEMM ? kb / ga.nkw : 0;
+        const int k = GEMM ? (kb - wk * ga.nkw) * BK : kb * BK;
+        const int arow = GEMM ? i0 : w * NGpad + i0;
+        const int brow = GEMM ? wk * NGpad + j0 : j0;
 #pragma unroll
-        for (int t = 0; t < TERMS; ++t) tma_load_2d(st + t * TILE_BYTES, &maps.a[t], &full[s], k, w * NGpad + i0);
+        for (int t = 0; t < TERMS; ++t) tma_load_2d(st + t * TILE_BYTES, &maps.a[t], &full[s], k, arow);
 #pragma unroll
         for (int t = 0; t < TERMS; ++t) {
-          tma_load_2d(st + (TERMS + 2 * t) * TILE_BYTES, &maps.x[t], &full[s], k, j0);
-          tma_load_2d(st + (TERMS + 2 * t + 1) * TILE_BYTES, &maps.z[t], &full[s], k, j0);
+          tma_load_2d(st + (TERMS + 2 * t) * TILE_BYTES, &maps.x[t], &full[s], k, brow);
+          tma_load_2d(st + (TERMS + 2 * t + 1) * TILE_BYTES, &maps.z[t], &full[s], k, brow);
         }
         issued = kb + 1;
       }
@@ -306,9 +330,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int row = q * 32 + lane;
     const int gi = i0 + row;
     const int cbase = cs * 32;
-    double2* crow = chi + ((int64_t)w * NG + gi) * NG + j0 + cbase;
-    // columns of this thread that belong to the lower triangle and the sphere
-    const int ncol = (gi < NG) ? max(0, min(32, min(NG, gi + 1) - (j0 + cbase))) : 0;
+    double2* crow = GEMM ? nullptr : chi + ((int64_t)w * NG + gi) * NG + j0 + cbase;
+    // HERK: columns of this thread in the lower triangle and the sphere;
+    // GEMM: columns inside the sphere of a row inside the pair range
+    int ncol;
+    if constexpr (GEMM)
+      ncol = (gi < ga.P) ? max(0, min(32, NG - (j0 + cbase))) : 0;
+    else
+      ncol = (gi < NG) ? max(0, min(32, min(NG, gi + 1) - (j0 + cbase))) : 0;
+    float wrow = 0.f;  // GEMM: 2 wgt[w][p] of the current frequency
+    int wcur = -1;
     float sre[32], sim[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) sre[c] = sim[c] = 0.f;
@@ -325,6 +356,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       sim[c] = 0.f;                                         \
     }                                                       \
   } while (0)
+    if constexpr (GEMM) flush = 1 << 30;  // one write at the end
     for (int f = 0; f < nfold; ++f) {
       const int b = f & 1;
       // the warp decides together: tcgen05.ld below is warp-collective
@@ -336,27 +368,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + cbase;
+      float sc = 1.f;
+      if constexpr (GEMM) {
+        const int wf = (f * fold) / ga.nkw;  // folds never straddle frequencies (fold divides nkw)
+        if (wf != wcur) {
+          wcur = wf;
+          wrow = gi < ga.P ? 2.f * ga.wgt[(int64_t)wf * ga.P + gi] : 0.f;
+        }
+        sc = wrow;
+      }
       // 18 warps leave 96 registers a thread: 64 running sums and one
       // 16-column load at a time; the buffer is released as soon as the last
       // load has landed, before its additions
       float v[16];
       tmem_ld16(base, v);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) sre[c] += v[c];
+      for (int c = 0; c < 16; ++c) sre[c] = fmaf(sc, v[c], sre[c]);
       tmem_ld16(base + 16, v);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) sre[16 + c] += v[c];
+      for (int c = 0; c < 16; ++c) sre[16 + c] = fmaf(sc, v[c], sre[16 + c]);
       tmem_ld16(base + 128, v);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) sim[c] += v[c];
+      for (int c = 0; c < 16; ++c) sim[c] = fmaf(sc, v[c], sim[c]);
       tmem_ld16(base + 144, v);
       tc_fence_before();
       mbar_arrive(&tempty[b]);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) sim[16 + c] += v[c];
+      for (int c = 0; c < 16; ++c) sim[16 + c] = fmaf(sc, v[c], sim[16 + c]);
       if ((f + 1) % flush == 0) RPA_TC_FLUSH();
     }
-    RPA_TC_FLUSH();
+    if constexpr (GEMM) {
+      float2* orow = ga.out + (int64_t)gi * NG + j0 + cbase;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < ncol) orow[c] = make_float2(sre[c], sim[c]);
+    } else {
+      RPA_TC_FLUSH();
+    }
 #undef RPA_TC_FLUSH
   }
   tc_fence_before();
@@ -464,6 +512,34 @@ __global__ void __launch_bounds__(256) prep_a_kernel(const float2* __restrict__ 
   }
 }
 
+// A[t][p][2k+c] = split((Re, Im) N[p][k]) for the adjoint product: rows padded
+// to Prows, K to KN = 2 * round32(NG), zero padding.
+template <int TERMS>
+__global__ void __launch_bounds__(256) prep_n_kernel(const float2* __restrict__ N, int64_t P, int NG, int64_t Prows,
+                                                     int KN, __nv_bfloat162* __restrict__ A, int64_t term_stride) {
+  const int kh = KN / 2;
+  const int64_t total = Prows * kh;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(id % kh);
+    const int64_t p = id / kh;
+    const float2 v = (p < P && k < NG) ? N[p * NG + k] : make_float2(0.f, 0.f);
+    __nv_bfloat16 rh, rm, rl, ih, im, il;
+    if (TERMS == 2) {
+      split2(v.x, rh, rl);
+      split2(v.y, ih, il);
+      A[id] = __halves2bfloat162(rh, ih);
+      A[id + term_stride] = __halves2bfloat162(rl, il);
+    } else {
+      split3(v.x, rh, rm, rl);
+      split3(v.y, ih, im, il);
+      A[id] = __halves2bfloat162(rh, ih);
+      A[id + term_stride] = __halves2bfloat162(rm, im);
+      A[id + 2 * term_stride] = __halves2bfloat162(rl, il);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -519,11 +595,11 @@ static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpa
   static_assert(C::SMEM_BYTES <= 227 * 1024, "shared-memory ring too large");
   const int nk = (int)(Kpad / BK);
   const int fold = fold64 * (64 / BK);  // the fold length is counted in 64-element units
-  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<TERMS, BK, STAGES>,
+  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<TERMS, BK, STAGES, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  herk_tc_kernel<TERMS, BK, STAGES><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, fold, flush, chi,
-                                                                            err);
+  herk_tc_kernel<TERMS, BK, STAGES, false><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, fold, flush,
+                                                                                   chi, err, GemmArgs{});
   return cudaGetLastError();
 }
 
@@ -600,6 +676,99 @@ cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fold_stages, i
     return launch_gemm<3, 32, 3>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
   if (bk == 32) return launch_gemm<2, 32, 4>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
   return launch_gemm<2, 64, 2>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, s);
+}
+
+// ---------------------------------------------------------------- adjoint product on the tensor cores
+// out[p][g] = 2 sum_w wgt[w][p] sum_k N[p][k] conj(Gam_w[k][g]) for Hermitian
+// Gam_w (the adjoint of the rank-k update).  Gam is split once per q-point into
+// X / Z operands [terms][nw * NGpad][KN]; the pair densities of each block into
+// A [terms][Prows][KN].
+static int64_t nbar_kn(int NG) { return 2 * (((int64_t)NG + 31) / 32 * 32); }
+static int64_t nbar_prows(int64_t P) { return (P + tc::BM - 1) / tc::BM * tc::BM; }
+
+size_t nbar_tc_gam_bytes(int NG, int nw, int terms) {
+  const int64_t NGpad = (NG + tc::BM - 1) / tc::BM * tc::BM;
+  return (size_t)2 * terms * nw * NGpad * nbar_kn(NG) * 2;
+}
+size_t nbar_tc_a_bytes(int64_t P, int NG, int terms) { return (size_t)terms * nbar_prows(P) * nbar_kn(NG) * 2; }
+
+cudaError_t nbar_tc_prepare_gam(const float2* Gam, int NG, int nw, int terms, void* gbuf, cudaStream_t s) {
+  if (terms != 2 && terms != 3) return cudaErrorInvalidValue;
+  const int NGpad = (NG + tc::BM - 1) / tc::BM * tc::BM;
+  const int64_t KN = nbar_kn(NG);
+  const int64_t op = (int64_t)nw * NGpad * KN / 2;  // bf16 pairs per term of X (or Z)
+  __nv_bfloat162* X = (__nv_bfloat162*)gbuf;
+  __nv_bfloat162* Z = X + op * terms;
+  dim3 pg(NGpad / 32, (unsigned)(KN / 2 / 32));
+  for (int w = 0; w < nw; ++w) {
+    const float2* Gw = Gam + (int64_t)w * NG * NG;
+    const int64_t off = (int64_t)w * NGpad * KN / 2;
+    // rows k of Gam play the role of pairs: X[g][2k] = (Re, Im) Gam[k][g], Z = (-Im, Re)
+    if (terms == 3)
+      tc::prep_xz_kernel<3><<<pg, 256, 0, s>>>(Gw, NG, NG, NGpad, KN, X + off, Z + off, op);
+    else
+      tc::prep_xz_kernel<2><<<pg, 256, 0, s>>>(Gw, NG, NG, NGpad, KN, X + off, Z + off, op);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t nbar_tc_run(const float2* N, const float* wgt, int64_t P, int NG, int nw, int terms, const void* gbuf,
+                        void* abuf, size_t abytes, float2* out, int* err, cudaStream_t s) {
+  using namespace tc;
+  if (P == 0 || NG == 0 || nw == 0) return cudaSuccess;
+  if ((terms != 2 && terms != 3) || abytes < nbar_tc_a_bytes(P, NG, terms)) return cudaErrorInvalidValue;
+  const int NGpad = (NG + BM - 1) / BM * BM;
+  const int64_t KN = nbar_kn(NG), Prows = nbar_prows(P);
+  if (Prows > (1 << 30) || (int64_t)nw * NGpad > (1 << 30)) return cudaErrorInvalidValue;
+  const int64_t aterm = Prows * KN / 2;
+  {
+    const int64_t total = Prows * KN / 2;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    if (terms == 3)
+      prep_n_kernel<3><<<blocks, 256, 0, s>>>(N, P, NG, Prows, (int)KN, (__nv_bfloat162*)abuf, aterm);
+    else
+      prep_n_kernel<2><<<blocks, 256, 0, s>>>(N, P, NG, Prows, (int)KN, (__nv_bfloat162*)abuf, aterm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int bk = terms == 3 ? 32 : 64;
+  const int64_t gop = (int64_t)nw * NGpad * KN;  // bf16 elements per term of X
+  const __nv_bfloat16* X = (const __nv_bfloat16*)gbuf;
+  const __nv_bfloat16* Z = X + gop * terms;
+  const __nv_bfloat16* A = (const __nv_bfloat16*)abuf;
+  Maps maps;
+  memset(&maps, 0, sizeof(maps));
+  for (int t = 0; t < terms; ++t) {
+    if (!make_map(&maps.a[t], A + Prows * KN * t, KN, Prows, bk) ||
+        !make_map(&maps.x[t], X + gop * t, KN, (int64_t)nw * NGpad, bk) ||
+        !make_map(&maps.z[t], Z + gop * t, KN, (int64_t)nw * NGpad, bk))
+      return cudaErrorInvalidValue;
+  }
+  GemmArgs ga;
+  ga.P = P;
+  ga.nkw = (int)(KN / bk);
+  ga.ngt = NGpad / BN;
+  ga.wgt = wgt;
+  ga.out = out;
+  const int nk = ga.nkw * nw;
+  const dim3 grid((unsigned)((Prows / BM) * ga.ngt), 1);
+  cudaError_t e;
+  if (terms == 3) {
+    using C = Cfg<3, 32, 3>;
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<3, 32, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  C::SMEM_BYTES)) != cudaSuccess)
+      return e;
+    herk_tc_kernel<3, 32, 3, true><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+                                                                           ga);
+  } else {
+    using C = Cfg<2, 64, 2>;
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<2, 64, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  C::SMEM_BYTES)) != cudaSuccess)
+      return e;
+    herk_tc_kernel<2, 64, 2, true><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+                                                                           ga);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace rpa

@@ -24,6 +24,12 @@ cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt
 cudaError_t herk_tc_run(int64_t P, int NG, int nw, int split_terms, int fold_stages, int flush_folds, int pipe,
                         double2* chi, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
 size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
+// adjoint product 2 sum_w w N conj(Gam_w) on the tensor cores (k_herk_tc.cu)
+size_t nbar_tc_gam_bytes(int NG, int nw, int terms);
+size_t nbar_tc_a_bytes(int64_t P, int NG, int terms);
+cudaError_t nbar_tc_prepare_gam(const float2* Gam, int NG, int nw, int terms, void* gbuf, cudaStream_t s);
+cudaError_t nbar_tc_run(const float2* N, const float* wgt, int64_t P, int NG, int nw, int terms, const void* gbuf,
+                        void* abuf, size_t abytes, float2* out, int* err, cudaStream_t s);
 // adjoint kernels (k_adjoint.cu)
 cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
                       double2* G64, float2* G32, cudaStream_t s, int64_t* launches);
@@ -679,7 +685,7 @@ struct AdjState {
 
 template <typename T>
 rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* omega_d, int nw,
-                          const c2<T>* Gam, AdjState& A) {
+                          const c2<T>* Gam, const void* gam_tc, AdjState& A) {
   Block<T> B;
   rpa_status st = pairs_block<T>(c, Q, t, a0, a1, omega_d, nw, B);
   if (st != RPA_OK || B.P == 0) return st;
@@ -692,8 +698,19 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
   if ((st = workspace(c, "Nbar", sizeof(c2<T>) * (size_t)B.P * NG, &p_nbar)) != RPA_OK) return st;
   c2<T>* Nbar = (c2<T>*)p_nbar;
   StageTimer tm(c, 4, 0);
-  CUDA_OK(c, launch_nbar<T>(B.N, B.P, NG, B.w, Gam, nw, Nbar, c->stream));
-  tm.add_launches(1);
+  if (gam_tc && sizeof(T) == 4) {
+    // split-bfloat16 modes: the product on the tensor cores
+    const int terms = c->prm.precision == RPA_BF16X3 ? 3 : 2;
+    void* p_a;
+    const size_t ab = nbar_tc_a_bytes(B.P, NG, terms);
+    if ((st = workspace(c, "nbar_a", ab, &p_a)) != RPA_OK) return st;
+    CUDA_OK(c, nbar_tc_run((const float2*)B.N, (const float*)B.w, B.P, NG, nw, terms, gam_tc, p_a, ab,
+                           (float2*)Nbar, c->dev_err, c->stream));
+    tm.add_launches(2);
+  } else {
+    CUDA_OK(c, launch_nbar<T>(B.N, B.P, NG, B.w, Gam, nw, Nbar, c->stream));
+    tm.add_launches(1);
+  }
   if (B.KP > 0) {
     if ((st = workspace(c, "paw_y", sizeof(c2<T>) * (size_t)nL * B.KP * NG, &p_y)) != RPA_OK) return st;
     CUDA_OK(c, launch_paw_adjoint<T>(Nbar, B.R, B.Pm, nL, nR, NG, B.KP, Q.Q, B.atom_of, B.idx_in, B.atom_off,
@@ -863,13 +880,20 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     const void* omega_d = nullptr;
     if ((st = workspace(c, "omega", sizeof(double) * nw, (void**)&omega_d)) != RPA_OK) return st;
     const c2<T>* Gam = sizeof(T) == 8 ? (const c2<T>*)p_G64 : (const c2<T>*)p_G32;
+    void* gam_tc = nullptr;
+    if (c->prm.precision == RPA_BF16X2 || c->prm.precision == RPA_BF16X3) {
+      const int terms = c->prm.precision == RPA_BF16X3 ? 3 : 2;
+      if ((st = workspace(c, "nbar_gam", nbar_tc_gam_bytes(NG, nw, terms), &gam_tc)) != RPA_OK) return st;
+      StageTimer tm(c, 4, nw);
+      CUDA_OK(c, nbar_tc_prepare_gam((const float2*)p_G32, NG, nw, terms, gam_tc, c->stream));
+    }
     for (size_t t = 0; t < Q.k_of.size(); ++t)
     {
       const int nL = (int)c->sets[Q.k_of[t]].L.size(), nR = (int)c->sets[Q.kq_of[t]].R.size();
       const int rows = rows_per_block(c, nL, nR, NG, nw);
       for (int a0 = 0; a0 < nL; a0 += rows)
         if ((st = backward_block<T>(c, Q, (int)t, a0, std::min(nL, a0 + rows), (const double*)omega_d, nw, Gam,
-                                    A)) != RPA_OK)
+                                    gam_tc, A)) != RPA_OK)
           return st;
     }
   }
