@@ -28,8 +28,12 @@ Readings of the paper that the oracle fixes (all listed in the design notes):
   (f_n - f_m) * 2 (e_n - e_m) / (w^2 + (e_n - e_m)^2).
 * The Gauss-Legendre nodes of Sec. 2.1 are mapped to [0, inf) by
   w = w0 (1+x)/(1-x); the nodes are an input of the energy.
-* At q = 0 the G = 0 element of the Coulomb kernel is set to zero (the
-  optical-limit head of Eq. 11 is a separate feature).
+* At q = 0 the G = 0 element of the Coulomb kernel is set to zero, unless the
+  optical limit is requested: then the G = 0 pair density is the q -> 0 limit
+  of Eq. 12 per unit |q| along a direction q^, -i q^.<psi_n|grad|psi_m> /
+  (e_m - e_n), with the gradient of Eq. 13 (plane-wave part evaluated exactly
+  in the plane-wave basis, PAW part from the input matrices q^.Q_grad of
+  Eq. 14), and v_0 = 4 pi (the |q|^2 of v and of |n(0)|^2 cancel).
 * The plane-wave normalisation is sum_Q |C(Q)|^2 = 1, so the pair density is
   n(G) = sum_Q conj(C_nk(Q)) C_m,k+q(Q+G) and n_nn(0) = 1 at q = 0.
 """
@@ -67,8 +71,9 @@ def g_sphere(cell, q_red, ecut: float) -> np.ndarray:
     return np.array(out, dtype=np.int64).reshape(-1, 3)
 
 
-def coulomb(cell, q_red, gmiller) -> np.ndarray:
-    """v_G(q) = 4 pi / |q+G|^2 (Sec. 2.2, text after Eq. 11); zero where q+G = 0."""
+def coulomb(cell, q_red, gmiller, optical: bool = False) -> np.ndarray:
+    """v_G(q) = 4 pi / |q+G|^2 (Sec. 2.2, text after Eq. 11); zero where q+G = 0,
+    or 4 pi there in the optical limit (v_0 |n_0|^2 with both |q|^2 factored out)."""
     B = reciprocal(cell)
     qg = np.asarray(gmiller, dtype=np.float64) + np.asarray(q_red, dtype=np.float64)
     c = qg @ B
@@ -76,6 +81,8 @@ def coulomb(cell, q_red, gmiller) -> np.ndarray:
     v = np.zeros(len(q2))
     nz = np.any(qg != 0.0, axis=1)
     v[nz] = 4.0 * np.pi / q2[nz]
+    if optical:
+        v[~nz] = 4.0 * np.pi
     return v
 
 
@@ -191,6 +198,38 @@ def _selection(f_k, f_kp):
     return nsel, msel
 
 
+# ---------------------------------------------------------------------------
+# optical limit q -> 0 (Eqs. 12-14)
+# ---------------------------------------------------------------------------
+def nabla_matrix(oset, cell, qdir, nsel, msel, paw_nproj=None, Qnabla=None) -> np.ndarray:
+    """q^.<psi_n|grad|psi_m> of Eq. 13 for n in nsel, m in msel of one orbital set.
+
+    Plane-wave part: <psi_n|grad|psi_m> = i sum_Q conj(C_n(Q)) (k+Q) C_m(Q) for
+    psi = Omega^-1/2 sum_Q C(Q) e^{i(k+Q).r} (exact in the basis).  PAW part:
+    sum_a sum_ij conj(P_ni) P_mj q^.Q_grad^a_ij, with ``Qnabla[a]`` shaped
+    (3, ni, ni) (Eq. 14's matrices, an input).  ``qdir`` is normalised here."""
+    qhat = np.asarray(qdir, dtype=np.float64)
+    qhat = qhat / np.linalg.norm(qhat)
+    B = reciprocal(cell)
+    kQ = (np.asarray(oset.k_red, dtype=np.float64)[None, :] + np.asarray(oset.miller, dtype=np.float64)) @ B
+    s = kQ @ qhat
+    C = np.asarray(oset.C)
+    D = 1j * (np.conj(C[nsel]) * s[None, :]) @ C[msel].T
+    if paw_nproj is not None and Qnabla is not None and len(paw_nproj):
+        P = np.asarray(oset.P)
+        off = 0
+        for a, ni in enumerate(paw_nproj):
+            Qa = np.einsum("d,dij->ij", qhat, np.asarray(Qnabla[a]))
+            D = D + np.conj(P[nsel][:, off:off + ni]) @ Qa @ P[msel][:, off:off + ni].T
+            off += ni
+    return D
+
+
+def optical_head(D, eps_n, eps_m) -> np.ndarray:
+    """n_{q->0}(G = 0) per unit |q| (Eq. 12): -i q^.<psi_n|grad|psi_m> / (e_m - e_n)."""
+    return -1j * D / (np.asarray(eps_m)[None, :] - np.asarray(eps_n)[:, None])
+
+
 def pair_block(sets, paw_nproj, Qflat, gmiller, ik, ikp, G0):
     """Full pair density n_nm(G) (pseudo part + PAW term) for one (k, k+q) block."""
     sk, skp = sets[ik], sets[ikp]
@@ -205,12 +244,15 @@ def pair_block(sets, paw_nproj, Qflat, gmiller, ik, ikp, G0):
 # chi0 (Eq. 3 / Eqs. 15-17: explicit sum over k and band pairs)
 # ---------------------------------------------------------------------------
 
-def chi0(problem, iq: int, omega, Qflat=None, pair_filter=None) -> np.ndarray:
+def chi0(problem, iq: int, omega, Qflat=None, pair_filter=None, optical=None) -> np.ndarray:
     """chi0_GG'(q, i w_j) = sum_k sum_{f_n > f_m} w_nm(w_j) n_nm(G) conj(n_nm(G')).
 
     ``problem`` is any object with the attributes of ``synthetic.Problem``.
     ``pair_filter(ik, nsel, msel) -> (nsel', msel')`` restricts the band
-    pairs (used for partial sums).  Returns (nw, NG, NG) complex128."""
+    pairs (used for partial sums).  ``optical = (qdir, Qnabla)`` replaces the
+    G = 0 pair densities of a q = 0 point by the optical limit of Eq. 12
+    (``Qnabla`` per atom (3, ni, ni), or None without PAW).  Returns
+    (nw, NG, NG) complex128."""
     qp = problem.qpoints[iq]
     gm = g_sphere(problem.cell, qp.q_red, problem.ecut_chi)
     ng = len(gm)
@@ -220,6 +262,13 @@ def chi0(problem, iq: int, omega, Qflat=None, pair_filter=None) -> np.ndarray:
     for t in range(len(qp.k_of)):
         ik, ikp, G0 = int(qp.k_of[t]), int(qp.kq_of[t]), qp.G0[t]
         n, nsel, msel = pair_block(problem.sets, nproj, Qflat, gm, ik, ikp, G0)
+        if optical is not None:
+            if np.any(np.asarray(qp.q_red) != 0) or ik != ikp or np.any(np.asarray(G0) != 0):
+                raise ValueError("the optical limit needs q = 0 and k -> k transitions")
+            ig0 = int(np.flatnonzero(np.all(np.asarray(gm) == 0, axis=1))[0])
+            sk = problem.sets[ik]
+            D = nabla_matrix(sk, problem.cell, optical[0], nsel, msel, nproj, optical[1])
+            n[ig0] = optical_head(D, sk.eps[nsel], sk.eps[msel])
         if pair_filter is not None:
             a, b = pair_filter(t, nsel, msel)
             n = n[:, a][:, :, b]
@@ -286,19 +335,21 @@ def ec_terms(chi, v) -> np.ndarray:
     return out
 
 
-def energy(problem, omega, W, Qs=None, iqs=None):
+def energy(problem, omega, W, Qs=None, iqs=None, optical=None):
     """E_c = sum_q w_q sum_j W_j / (2 pi) e_q(w_j) (Eq. 2 with the IBZ weights of Sec. 2.1).
 
-    ``Qs[iq]`` holds the flattened augmentation functions for q-point iq.
-    Returns (E_c, terms[nq, nw])."""
+    ``Qs[iq]`` holds the flattened augmentation functions for q-point iq;
+    ``optical[iq] = (qdir, Qnabla)`` switches on the optical limit of a q = 0
+    point.  Returns (E_c, terms[nq, nw])."""
     iqs = range(len(problem.qpoints)) if iqs is None else iqs
     terms = []
     E = 0.0
     for iq in iqs:
         qp = problem.qpoints[iq]
-        chi = chi0(problem, iq, omega, None if Qs is None else Qs[iq])
+        opt = None if optical is None else optical.get(iq)
+        chi = chi0(problem, iq, omega, None if Qs is None else Qs[iq], optical=opt)
         gm = g_sphere(problem.cell, qp.q_red, problem.ecut_chi)
-        v = coulomb(problem.cell, qp.q_red, gm)
+        v = coulomb(problem.cell, qp.q_red, gm, optical=opt is not None)
         e = ec_terms(chi, v)
         terms.append(e)
         E += qp.weight * float(np.sum(np.asarray(W) * e)) / TWO_PI
