@@ -140,6 +140,23 @@ rpa_status rpa_gvectors(const rpa_ctx* ctx, int32_t iq, int32_t* ng,
 rpa_status rpa_set_paw_Q(rpa_ctx* ctx, int32_t iq, int32_t natoms,
                          const int32_t* nproj, const double* Q);
 
+/* Optical limit q -> 0 at q-point iq (Eqs. 12-14).  iq must have q = 0 and
+ * only k -> k transitions without umklapp.  The G = 0 pair density of every
+ * pair becomes its q -> 0 limit per unit |q| along the direction qdir[3]
+ * (Cartesian, normalised by the library),
+ *   n_nm(0) = -i q^.<psi_n|grad|psi_m> / (e_m - e_n),
+ *   <psi_n|grad|psi_m> = i sum_Q conj(C_n(Q)) (k+Q) C_m(Q)
+ *                        + sum_a sum_ij conj(P_ni) P_mj Qgrad^a_ij      (Eq. 13),
+ * with Qgrad^a_ij = <phi_i|grad|phi_j> - <phi~_i|grad|phi~_j> of Eq. 14 given
+ * atom after atom as [3][ni][ni] complex blocks (x, y, z), host memory; pass
+ * natoms = 0 and Qgrad = NULL without PAW.  v_0 becomes 4 pi (the |q|^2 of v
+ * and of |n_0|^2 cancel), so chi0 and E_c of iq include the head and wings.
+ * qdir = NULL switches the limit off again (n(0) and v_0 = 0 of q = 0).  The
+ * setting lasts until rpa_set_qpoint replaces iq.  rpa_energy_backward
+ * returns RPA_ERR_STATE for a q-point with the optical limit. */
+rpa_status rpa_set_optical(rpa_ctx* ctx, int32_t iq, const double* qdir, int32_t natoms,
+                           const int32_t* nproj, const double* Qgrad);
+
 /* chi0_GG'(q, i omega_j) of q-point iq (Eq. 3 summed as Eq. 17) for nw
  * frequencies omega[nw] (host).  Pairs (n at k, m at k+q) with f_n > f_m
  * enter with the real time-reversal-combined weight

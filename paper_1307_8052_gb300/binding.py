@@ -37,6 +37,7 @@ SIGNATURES = {
     "rpa_set_qpoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P]),
     "rpa_gvectors": (_I, [_P, _I, _P, _P]),
     "rpa_set_paw_Q": (_I, [_P, _I, _I, _P, _P]),
+    "rpa_set_optical": (_I, [_P, _I, _P, _I, _P, _P]),
     "rpa_chi0": (_I, [_P, _I, _I, _P, _P]),
     "rpa_energy": (_I, [_P, _I, _P, _P, _I, _P, _P, _P, _P]),
     "rpa_set_profiling": (_I, [_P, _I]),
@@ -183,6 +184,23 @@ def rpa_set_paw_Q(ctx, iq, nproj, Q):
     nproj = np.asarray(nproj, dtype=np.int32)
     _check(ctx, lib().rpa_set_paw_Q(ctx, int(iq), len(nproj), _ptr(nproj, np.int32, keep),
                                     _ptr(Q, np.complex128, keep)))
+
+
+def rpa_set_optical(ctx, iq, qdir, nproj=None, Qgrad=None):
+    """Optical limit at q = 0 point iq along ``qdir`` (Cartesian); ``Qgrad[a]``
+    complex (3, ni, ni) per atom, or None without PAW; ``qdir=None`` switches it off."""
+    keep = []
+    if qdir is None:
+        _check(ctx, lib().rpa_set_optical(ctx, int(iq), None, 0, None, None))
+        return
+    qd = np.ascontiguousarray(qdir, dtype=np.float64)
+    if Qgrad is None or nproj is None or len(nproj) == 0:
+        _check(ctx, lib().rpa_set_optical(ctx, int(iq), _ptr(qd, np.float64, keep), 0, None, None))
+        return
+    nproj = np.asarray(nproj, dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(q, dtype=np.complex128).reshape(-1) for q in Qgrad]))
+    _check(ctx, lib().rpa_set_optical(ctx, int(iq), _ptr(qd, np.float64, keep), len(nproj),
+                                      _ptr(nproj, np.int32, keep), _ptr(flat, np.complex128, keep)))
 
 
 def rpa_chi0(ctx, iq, omega, out=None):

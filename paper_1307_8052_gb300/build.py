@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librpa_gb300.so")
-SOURCES = ["rpa_host.cpp", "k_transform.cu", "k_herk.cu", "k_herk_tc.cu", "k_chol.cu", "k_adjoint.cu"]
+SOURCES = ["rpa_host.cpp", "k_transform.cu", "k_herk.cu", "k_herk_tc.cu", "k_chol.cu", "k_adjoint.cu", "k_optical.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,133 @@
+// Optical limit q -> 0 (Eqs. 12-14): the G = 0 pair density of a q = 0 point
+// per unit |q| along q^,
+//   n_nm(0) = -i q^.<psi_n|grad|psi_m> / (e_m - e_n),
+//   q^.<psi_n|grad|psi_m> = i sum_Q conj(C_n(Q)) q^.(k+Q) C_m(Q)
+//                           + sum_ij conj(P_ni) (q^.Q_grad)_ij P_mj,
+// written into the G = 0 column of a block of pair densities.  The plane-wave
+// part is exact in the basis (the spectral gradient); q^.Q_grad (Eq. 14) is an
+// input contracted with q^ on the host.  FP64 throughout: the head enters the
+// log-det with the largest Coulomb weight.
+#include "rpa.h"
+#include "rpa_internal.h"
+
+#include <algorithm>
+
+namespace rpa {
+
+constexpr int OT = 64;  // output tile edge (pairs)
+constexpr int OK = 16;  // K chunk
+
+// Y[b][i] = sum_j Qn[i][j] P[R[b]][j]
+__global__ void optical_paw_y_kernel(const double2* __restrict__ P, int KP, const double2* __restrict__ Qn,
+                                     const int* __restrict__ R, int nR, double2* __restrict__ Y) {
+  const int64_t total = (int64_t)nR * KP;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(id % KP);
+    const int b = (int)(id / KP);
+    const double2* pm = P + (int64_t)R[b] * KP;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < KP; ++j) cmac<double>(acc, Qn[(int64_t)i * KP + j], pm[j]);
+    Y[id] = acc;
+  }
+}
+
+// D[a][b] = sum_k A_k(n_a) B_k(m_b) over K = npw (+ KP), 4 x 4 outputs a thread;
+// then N[(a nR + b) NG + ig0] = -i D / (e_m - e_n).
+template <typename T>
+__global__ void __launch_bounds__(256) optical_head_kernel(const double2* __restrict__ C, int npw,
+                                                           const double* __restrict__ s,
+                                                           const double2* __restrict__ P, int KP,
+                                                           const double2* __restrict__ Y, const int* __restrict__ L,
+                                                           int nL, const int* __restrict__ R, int nR,
+                                                           const double* __restrict__ eps, int NG, int ig0,
+                                                           c2<T>* __restrict__ N) {
+  __shared__ double2 As[OK][OT];
+  __shared__ double2 Bs[OK][OT];
+  const int a0 = blockIdx.y * OT, b0 = blockIdx.x * OT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
+  const int K = npw + (P ? KP : 0);
+  for (int k0 = 0; k0 < K; k0 += OK) {
+#pragma unroll
+    for (int q = 0; q < (OK * OT) / 256; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int kk = e / OT, r = e % OT;
+      const int k = k0 + kk;
+      double2 av = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      if (k < K) {
+        if (a0 + r < nL) {
+          const int n = L[a0 + r];
+          if (k < npw) {
+            // i s(Q) conj(C_n(Q))
+            const double2 cn = C[(int64_t)n * npw + k];
+            av = make_double2(s[k] * cn.y, s[k] * cn.x);
+          } else {
+            const double2 pn = P[(int64_t)n * KP + (k - npw)];
+            av = make_double2(pn.x, -pn.y);
+          }
+        }
+        if (b0 + r < nR) {
+          const int m = R[b0 + r];
+          bv = k < npw ? C[(int64_t)m * npw + k] : Y[(int64_t)(b0 + r) * KP + (k - npw)];
+        }
+      }
+      As[kk][r] = av;
+      Bs[kk][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < OK; ++kk) {
+      double2 av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac<double>(acc[r][c], av[r], bv[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int a = a0 + ty + 16 * r, b = b0 + tx + 16 * c;
+      if (a < nL && b < nR) {
+        const double de = eps[R[b]] - eps[L[a]];
+        // -i D / de
+        const double2 d = acc[r][c];
+        N[((int64_t)a * nR + b) * NG + ig0] = mk<T>((T)(d.y / de), (T)(-d.x / de));
+      }
+    }
+}
+
+template <typename T>
+cudaError_t launch_optical_head(const double2* C, int npw, const double* s, const double2* P, int KP,
+                                const double2* Qn, double2* Y, const int* L, int nL, const int* R, int nR,
+                                const double* eps, int NG, int ig0, c2<T>* N, cudaStream_t st) {
+  if (nL == 0 || nR == 0) return cudaSuccess;
+  if (P) {
+    const int64_t total = (int64_t)nR * KP;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    optical_paw_y_kernel<<<blocks, 256, 0, st>>>(P, KP, Qn, R, nR, Y);
+  }
+  dim3 grid((nR + OT - 1) / OT, (nL + OT - 1) / OT);
+  optical_head_kernel<T><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, eps, NG, ig0, N);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_optical_head<float>(const double2*, int, const double*, const double2*, int,
+                                                const double2*, double2*, const int*, int, const int*, int,
+                                                const double*, int, int, float2*, cudaStream_t);
+template cudaError_t launch_optical_head<double>(const double2*, int, const double*, const double2*, int,
+                                                 const double2*, double2*, const int*, int, const int*, int,
+                                                 const double*, int, int, double2*, cudaStream_t);
+
+}  // namespace rpa

@@ -109,7 +109,14 @@ struct QPt {
   int* gfft_d = nullptr;    // [nk][NG][3] transform indices g = G + G0 of every transition
   char* paw_meta_d = nullptr;  // PAW index tables (q offsets, atom of projector, ...)
   int KP = 0;
+  // optical limit (Eqs. 12-14), q = 0 only
+  bool optical = false;
+  int ig0 = -1;                 // index of G = 0 in the sphere
+  double2* Qn_d = nullptr;      // q^.Qgrad as a dense block-diagonal [KPo][KPo], or null
+  int KPo = 0;
+  std::map<int, double*> s_d;   // per orbital set: q^.(k+Q) of its plane waves
 };
+
 
 }  // namespace
 
@@ -172,6 +179,14 @@ rpa_status dev_alloc(rpa_ctx* c, void** p, size_t bytes) {
 
 void dev_free(void* p) {
   if (p) cudaFree(p);
+}
+void free_optical(QPt& Q) {
+  dev_free(Q.Qn_d);
+  Q.Qn_d = nullptr;
+  for (auto& kv : Q.s_d) dev_free(kv.second);
+  Q.s_d.clear();
+  Q.optical = false;
+  Q.KPo = 0;
 }
 
 rpa_status workspace(rpa_ctx* c, const char* name, size_t bytes, void** out) {
@@ -509,6 +524,18 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
                                      1.0 / (double)Nr, Rp, Pm, KP, skp.R_d, nR, p0, (c2<T>*)p_N, c->stream));
       tm.add_launches(3);
     }
+  }
+  if (Q.optical) {
+    // optical limit: the G = 0 column from q^.<psi_n|grad|psi_m> (Eqs. 12-13)
+    const bool pawo = Q.Qn_d && sk.P;
+    if (pawo && sk.KP != Q.KPo)
+      return fail(c, RPA_ERR_ARG, "projector count of set %d does not match the optical Qgrad", Q.k_of[t]);
+    void* p_y = nullptr;
+    if (pawo && (st = workspace(c, "optical_y", sizeof(double2) * (size_t)nR * Q.KPo, &p_y)) != RPA_OK) return st;
+    StageTimer tm(c, 1, pawo ? 2 : 1);
+    CUDA_OK(c, launch_optical_head<T>(sk.C, sk.npw, Q.s_d[Q.k_of[t]], pawo ? sk.P : nullptr, Q.KPo, Q.Qn_d,
+                                      (double2*)p_y, Lsub, nL, skp.R_d, nR, sk.eps_d, NG, Q.ig0, (c2<T>*)p_N,
+                                      c->stream));
   }
   B.w = (T*)p_w;
   B.N = (c2<T>*)p_N;
@@ -996,6 +1023,7 @@ void rpa_destroy(rpa_ctx* c) {
     dev_free(kv.second.gfft_d);
     dev_free(kv.second.paw_meta_d);
     dev_free(kv.second.Q);
+    free_optical(kv.second);
   }
   for (auto& kv : c->ws) dev_free(kv.second.p);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -1233,6 +1261,7 @@ rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t
     dev_free(it->second.Q);
     dev_free(it->second.gfft_d);
     dev_free(it->second.paw_meta_d);
+    free_optical(it->second);
   }
   c->qpts[iq] = Q;
   if (ng_out) *ng_out = Q.NG;
@@ -1245,6 +1274,89 @@ rpa_status rpa_gvectors(const rpa_ctx* c, int32_t iq, int32_t* ng, int32_t* mill
   if (it == c->qpts.end() || !it->second.valid) return RPA_ERR_STATE;
   *ng = it->second.NG;
   if (miller_out) memcpy(miller_out, it->second.gm.data(), sizeof(int32_t) * it->second.gm.size());
+  return RPA_OK;
+}
+
+rpa_status rpa_set_optical(rpa_ctx* c, int32_t iq, const double* qdir, int32_t natoms, const int32_t* nproj,
+                           const double* Qg) {
+  if (!c) return RPA_ERR_ARG;
+  auto it = c->qpts.find(iq);
+  if (it == c->qpts.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "q-point %d not set", iq);
+  QPt& Q = it->second;
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));  // earlier work may still read the old tables
+  free_optical(Q);
+  int ig0 = -1;
+  for (int i = 0; i < Q.NG; ++i)
+    if (Q.gm[3 * i] == 0 && Q.gm[3 * i + 1] == 0 && Q.gm[3 * i + 2] == 0) ig0 = i;
+  if (!qdir) {
+    if (ig0 >= 0 && Q.q[0] == 0.0 && Q.q[1] == 0.0 && Q.q[2] == 0.0) {
+      Q.v[ig0] = 0.0;
+      CUDA_OK(c, cudaMemcpy(Q.v_d + ig0, &Q.v[ig0], sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return RPA_OK;
+  }
+  if (Q.q[0] != 0.0 || Q.q[1] != 0.0 || Q.q[2] != 0.0 || ig0 < 0)
+    return fail(c, RPA_ERR_ARG, "the optical limit needs q = 0");
+  for (size_t t = 0; t < Q.k_of.size(); ++t)
+    if (Q.k_of[t] != Q.kq_of[t] || Q.G0[3 * t] || Q.G0[3 * t + 1] || Q.G0[3 * t + 2])
+      return fail(c, RPA_ERR_ARG, "the optical limit needs k -> k transitions without umklapp");
+  const double nrm = std::sqrt(qdir[0] * qdir[0] + qdir[1] * qdir[1] + qdir[2] * qdir[2]);
+  if (!(nrm > 0.0) || !std::isfinite(nrm)) return fail(c, RPA_ERR_ARG, "qdir must be a nonzero vector");
+  const double qh[3] = {qdir[0] / nrm, qdir[1] / nrm, qdir[2] / nrm};
+  if (natoms < 0 || natoms > 100000 || (natoms > 0 && (!nproj || !Qg)))
+    return fail(c, RPA_ERR_ARG, "bad optical PAW arguments");
+  rpa_status st;
+  if (natoms > 0) {
+    int KP = 0;
+    for (int a = 0; a < natoms; ++a) {
+      if (nproj[a] < 1 || nproj[a] > 64) return fail(c, RPA_ERR_ARG, "nproj[%d] outside [1,64]", a);
+      KP += nproj[a];
+    }
+    if (is_device_ptr(Qg)) return fail(c, RPA_ERR_ARG, "Qgrad must be host memory");
+    std::vector<double2> Qn((size_t)KP * KP, make_double2(0.0, 0.0));
+    size_t src = 0;
+    int off = 0;
+    for (int a = 0; a < natoms; ++a) {
+      const int ni = nproj[a];
+      for (int i = 0; i < ni; ++i)
+        for (int j = 0; j < ni; ++j) {
+          double2 v = make_double2(0.0, 0.0);
+          for (int d = 0; d < 3; ++d) {
+            const size_t e = src + ((size_t)d * ni + i) * ni + j;
+            v.x += qh[d] * Qg[2 * e];
+            v.y += qh[d] * Qg[2 * e + 1];
+          }
+          Qn[(size_t)(off + i) * KP + off + j] = v;
+        }
+      src += (size_t)3 * ni * ni;
+      off += ni;
+    }
+    if ((st = dev_alloc(c, (void**)&Q.Qn_d, sizeof(double2) * Qn.size())) != RPA_OK) return st;
+    CUDA_OK(c, cudaMemcpy(Q.Qn_d, Qn.data(), sizeof(double2) * Qn.size(), cudaMemcpyHostToDevice));
+    Q.KPo = KP;
+  }
+  // q^.(k+Q) of every plane wave of every set used by iq (Cartesian, B rows)
+  const double* B = c->B;
+  for (int id : Q.k_of) {
+    if (Q.s_d.count(id)) continue;
+    const OrbSet& os = c->sets[id];
+    std::vector<double> sv(os.npw);
+    for (int g = 0; g < os.npw; ++g) {
+      const double r[3] = {os.k[0] + os.miller[3 * g], os.k[1] + os.miller[3 * g + 1], os.k[2] + os.miller[3 * g + 2]};
+      double acc = 0.0;
+      for (int d = 0; d < 3; ++d) acc += qh[d] * (r[0] * B[d] + r[1] * B[3 + d] + r[2] * B[6 + d]);
+      sv[g] = acc;
+    }
+    double* sd = nullptr;
+    if ((st = dev_alloc(c, (void**)&sd, sizeof(double) * os.npw)) != RPA_OK) return st;
+    Q.s_d[id] = sd;
+    CUDA_OK(c, cudaMemcpy(sd, sv.data(), sizeof(double) * os.npw, cudaMemcpyHostToDevice));
+  }
+  Q.ig0 = ig0;
+  Q.v[ig0] = 4.0 * M_PI;
+  CUDA_OK(c, cudaMemcpy(Q.v_d + ig0, &Q.v[ig0], sizeof(double), cudaMemcpyHostToDevice));
+  Q.optical = true;
   return RPA_OK;
 }
 
@@ -1484,6 +1596,8 @@ rpa_status rpa_energy_backward(rpa_ctx* c, int32_t nq, const int32_t* iqs, const
   for (int i = 0; i < nq; ++i) {
     rpa_status st = check_q_ready(c, iqs[i]);
     if (st != RPA_OK) return st;
+    if (c->qpts[iqs[i]].optical)
+      return fail(c, RPA_ERR_STATE, "q-point %d uses the optical limit; its gradient is not available", iqs[i]);
   }
   choose_transform_grid(c, iqs, nq);
   rpa_status st;

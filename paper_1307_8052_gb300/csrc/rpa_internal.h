@@ -98,6 +98,14 @@ cudaError_t launch_herk_simt_w(const c2<T>* N, int64_t P, int NG, const T* wgt, 
 // Upper triangle from lower: chi[w][i][j] = conj(chi[w][j][i]) for i < j.
 cudaError_t launch_hermitian_fill(double2* chi, int nw, int NG, cudaStream_t s);
 
+// Optical limit (k_optical.cu): G = 0 column of a block of pair densities at
+// q = 0 from q^.<psi_n|grad|psi_m> (plane-wave part with s[Q] = q^.(k+Q),
+// PAW part from the dense q^.Q_grad matrix Qn [KP][KP]; Y is scratch [nR][KP]).
+template <typename T>
+cudaError_t launch_optical_head(const double2* C, int npw, const double* s, const double2* P, int KP,
+                                const double2* Qn, double2* Y, const int* L, int nL, const int* R, int nR,
+                                const double* eps, int NG, int ig0, c2<T>* N, cudaStream_t st);
+
 // Complex elements of the work buffer run_logdet needs: the factor and the
 // inverses of its diagonal blocks.
 int64_t logdet_work_elems(int nw, int NG);

@@ -139,6 +139,17 @@ def make_paw_setup(config: int, nproj) -> PawSetup:
     return PawSetup(nproj, cs, R)
 
 
+def paw_Qnabla(paw: PawSetup, config: int) -> list:
+    """Synthetic q -> 0 PAW gradient matrices of Eq. 14, one complex (3, ni, ni)
+    block per atom, anti-Hermitian in (i, j) like <phi_i|grad|phi_j> - <phi~_i|grad|phi~_j>."""
+    rng = np.random.default_rng(seed_of(config, 0, 3))
+    out = []
+    for ni in paw.nproj:
+        A = 0.2 * (rng.standard_normal((3, ni, ni)) + 1j * rng.standard_normal((3, ni, ni)))
+        out.append(A - np.conj(np.transpose(A, (0, 2, 1))))
+    return out
+
+
 def paw_Q(paw: PawSetup, cell, q_red, gmiller) -> np.ndarray:
     """Synthetic augmentation Q^a_ij(q+G) = c_ij exp(-0.3|q+G|^2) exp(-i (q+G).R_a).
 
