@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "chi0 TFLOP/s and s per q (all iw), mixed vs FP64 on 1 GB300; E_c rel. error"
 WORKLOAD = "bulk 9 bohr box, 40^3 grid, 2x2x2 k, 8 q, 16 occ + 1200 empty bands, NG~1200, 16 iw, 3x13 PAW projectors"
+OPTICAL_QDIR = (1.0, 1.0, 1.0)
 WORKLOAD_SLAB = ("slab 9.4x8.1x40 bohr, 48x40x200 grid, 4x2x1 k, 120 occ + 3000 empty bands, NG~3000, 16 iw, "
                  "16x18 + 2x8 PAW projectors")
 CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -241,11 +242,16 @@ def run_ours(args):
     Kall = pairs_per_q(p)
     Kq = [Kall[i] for i in iqs]
 
+    # q = 0 of the bulk mesh carries the optical-limit head and wings (Eqs. 12-14)
+    optical_q = [i for i in iqs if np.all(p.qpoints[i].q_red == 0)] if args.config == "bulk" else []
+
     def make_ctx(precision):
         ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, precision, device=local,
                            stream=stream.cuda_stream)
         ngs = b.load_problem(ctx, p, qs=iqs,
                              paw_Q=lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))
+        for iq in optical_q:
+            b.rpa_set_optical(ctx, iq, OPTICAL_QDIR, p.paw.nproj, syn.paw_Qnabla(p.paw, p.config))
         return ctx, ngs
 
     ctx, ngs = make_ctx(args.precision)
@@ -363,6 +369,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_SLAB if args.config == "slab" else WORKLOAD, "precision": args.precision,
                    "q_points": nq, "NG": ngs,
+                   "optical_limit": (f"q=0 head and wings along {OPTICAL_QDIR}" if optical_q else None),
                    "pairs_per_q": Kq, "nw": p.nw, "l2": "inputs larger than L2 (grids >= 1.4 GB, rank-k operands >= 3 GB per block)",
                    "parallelism": f"replicas x{world}"},
         "s_per_q": t_step / nq,
