@@ -245,6 +245,39 @@ def config2(nocc: int = 120, nunocc: int = 3000, kidx=None, with_paw: bool = Tru
                    sets, qps, 16, paw)
 
 
+def spin_metal_problem(config_tag: int = 80, a: float = 6.0, grid=(12, 12, 12), ecut_wf: float = 4.0,
+                       ecut_chi: float = 1.5, nb: int = 14, mesh=(2, 1, 1), nproj=(4, 5), nw: int = 8,
+                       kT: float = 0.05) -> Problem:
+    """Spin-polarised metal: one orbital set per (k, spin) (set 2k + spin),
+    Fermi-Dirac occupations f = 1 / (1 + exp((e - mu_s) / kT)) with the chemical
+    potential of spin s on band nb/2 - 1 + s of the first k-point, so both
+    channels have partially occupied bands, spin factor 1, transitions
+    k -> k+q within each spin channel."""
+    cell = np.diag([a, a * 1.1, a * 0.9])
+    kmesh = [np.array([i / mesh[0], j / mesh[1], l / mesh[2]]) for i in range(mesh[0])
+             for j in range(mesh[1]) for l in range(mesh[2])]
+    paw = make_paw_setup(config_tag, list(nproj)) if nproj else None
+    sets = []
+    mu = [None, None]
+    for i, k in enumerate(kmesh):
+        for sp in (0, 1):
+            st = make_orbitals(config_tag, 2 * i + sp, cell, k, ecut_wf, nb // 2, nb - nb // 2)
+            if mu[sp] is None:
+                mu[sp] = float(st.eps[nb // 2 - 1 + sp])
+            st.f = 1.0 / (1.0 + np.exp((st.eps - mu[sp]) / kT))
+            if paw is not None:
+                st.P = make_projections(config_tag, 2 * i + sp, st.C.shape[0], int(paw.nproj.sum()))
+            sets.append(st)
+    qps = []
+    for qp in mesh_qpoints(kmesh, kmesh):
+        k_of = np.concatenate([2 * qp.k_of, 2 * qp.k_of + 1]).astype(np.int32)
+        kq_of = np.concatenate([2 * qp.kq_of, 2 * qp.kq_of + 1]).astype(np.int32)
+        G0 = np.concatenate([qp.G0, qp.G0]).astype(np.int32)
+        qps.append(QPoint(qp.q_red, k_of, kq_of, G0, qp.weight))
+    return Problem(f"spin-metal-{config_tag}", config_tag, cell, tuple(grid), ecut_wf, ecut_chi, 1.0,
+                   len(kmesh), sets, qps, nw, paw)
+
+
 def config3_instance(i: int, nw: int = 16) -> Problem:
     """One (q, cell) instance of the batched workload: the bulk box of config 1
     (9 bohr, 40^3 grid, 20 Ha orbitals), Gamma k-point, q drawn from the

@@ -342,3 +342,33 @@ def test_gradient_matches_central_differences():
         g = gC[s] if which == "C" else gP[s]
         an = float(np.sum(np.conj(g) * d).real)
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (which, fd, an)
+
+
+def test_spin_channels_add_up():
+    """Spin polarisation (NEXT-2): chi0 is the sum over spin channels with
+    spin factor 1, so two identical channels at s = 1 equal one channel at s = 2,
+    and the channels of a polarised metal add up."""
+    p = syn.spin_metal_problem(nw=4)
+    om, _ = o.frequency_grid(4)
+    iq = 1
+    qp = p.qpoints[iq]
+    Q = syn.paw_Q(p.paw, p.cell, qp.q_red, o.g_sphere(p.cell, qp.q_red, p.ecut_chi))
+    nt = len(qp.k_of) // 2
+    # partially occupied bands in both channels
+    assert any(0.05 < f < 0.95 for s_ in p.sets[0::2] for f in s_.f)
+    assert any(0.05 < f < 0.95 for s_ in p.sets[1::2] for f in s_.f)
+    full = o.chi0(p, iq, om, Q)
+    up = o.chi0(p, iq, om, Q, pair_filter=lambda t, n, m: (np.arange(len(n)) if t < nt else np.arange(0),
+                                                            np.arange(len(m))))
+    dn = o.chi0(p, iq, om, Q, pair_filter=lambda t, n, m: (np.arange(len(n)) if t >= nt else np.arange(0),
+                                                            np.arange(len(m))))
+    assert np.abs(up + dn - full).max() <= 1e-14 * np.abs(full).max()
+    # identical channels at s = 1 == one channel at s = 2
+    import dataclasses
+    same = dataclasses.replace(p, sets=[p.sets[2 * (i // 2)] for i in range(len(p.sets))])
+    paired = dataclasses.replace(p, spin_factor=2.0, sets=p.sets[0::2], qpoints=[
+        syn.QPoint(q.q_red, q.k_of[:len(q.k_of) // 2] // 2, q.kq_of[:len(q.kq_of) // 2] // 2,
+                   q.G0[:len(q.G0) // 2], q.weight) for q in p.qpoints])
+    a = o.chi0(same, iq, om, Q)
+    b = o.chi0(paired, iq, om, Q)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
