@@ -199,6 +199,36 @@ def _selection(f_k, f_kp):
 
 
 # ---------------------------------------------------------------------------
+# IBZ -> BZ symmetry (Eq. 9; Table 1 steps 4 and 7)
+# ---------------------------------------------------------------------------
+def rotate_set(oset, M, time_reversal=False, paw_nproj=None, atom_map=None, D=None):
+    """Orbital set at k' = M k from the set at k (Eq. 9: psi'(r) = psi(T^-1 r)).
+
+    In the plane-wave basis the rotated orbital has the same coefficients on
+    the rotated reciprocal vectors: C'(M Q) = C(Q), with M the integer matrix of
+    the operation on reduced reciprocal coordinates.  Time reversal adds
+    psi -> conj(psi): k', Q' -> -k', -Q' and C' = conj(C).  Projections (step 7):
+    P'[n, a, i] = sum_j D[a][i, j] P[n, atom_map[a], j] (conjugated under time
+    reversal); D and atom_map describe the projectors and are inputs."""
+    import dataclasses
+    M = np.asarray(M, dtype=np.int64).reshape(3, 3)
+    sg = -1 if time_reversal else 1
+    k = sg * (M @ np.asarray(oset.k_red, dtype=np.float64))
+    mil = (sg * (np.asarray(oset.miller, dtype=np.int64) @ M.T)).astype(np.int32)
+    C = np.conj(oset.C) if time_reversal else np.array(oset.C, copy=True)
+    P = None
+    if oset.P is not None and paw_nproj is not None:
+        off = np.concatenate([[0], np.cumsum(paw_nproj)])
+        P = np.zeros_like(oset.P)
+        for a, ni in enumerate(paw_nproj):
+            src = atom_map[a]
+            P[:, off[a]:off[a] + ni] = oset.P[:, off[src]:off[src] + paw_nproj[src]] @ np.asarray(D[a]).T
+        if time_reversal:
+            P = np.conj(P)
+    return dataclasses.replace(oset, k_red=k, miller=mil, C=C, P=P)
+
+
+# ---------------------------------------------------------------------------
 # optical limit q -> 0 (Eqs. 12-14)
 # ---------------------------------------------------------------------------
 def nabla_matrix(oset, cell, qdir, nsel, msel, paw_nproj=None, Qnabla=None) -> np.ndarray:

@@ -1,0 +1,91 @@
+"""Pins of the oracle's IBZ -> BZ rotation (Eq. 9; steps 4 and 7) against
+things that do not use it: orbitals diagonalised directly at the rotated
+k-point of a symmetric model crystal, and group properties of the projector
+rotation."""
+import dataclasses
+
+import numpy as np
+
+import oracle as o
+from paper_1307_8052_gb300 import synthetic as syn
+
+
+def _model_sets(cell, kpts, V, ecut=2.0, nocc=3, nb=10):
+    """Eigenstates of H = -grad^2/2 + V on a shared plane-wave list."""
+    B = o.reciprocal(cell)
+    miller = syn.wf_sphere(cell, [0, 0, 0], ecut + 0.8)
+    out = []
+    for k in kpts:
+        kq = (np.asarray(k)[None, :] + miller) @ B
+        H = np.diag(0.5 * np.einsum("ij,ij->i", kq, kq)).astype(np.complex128)
+        for i in range(len(miller)):
+            for j in range(len(miller)):
+                H[i, j] += V(tuple(miller[i] - miller[j]))
+        e, U = np.linalg.eigh(H)
+        f = np.r_[np.ones(nocc), np.zeros(nb - nocc)]
+        out.append(syn.OrbitalSet(np.asarray(k, float), miller, U.T[:nb].copy(), e[:nb], f, None))
+    return out
+
+
+def _cubic_potential():
+    # V(G) invariant under the 90-degree rotation about z and under G -> -G with a real potential
+    def V(G):
+        if G == (0, 0, 0):
+            return 0.0
+        g = np.array(G, float)
+        return 0.3 * np.exp(-0.3 * g @ g) * (1.0 + 0.2 * np.cos(g[0] * g[1]) + 0.1 * g[2] ** 2)
+    return V
+
+
+def test_rotated_orbitals_give_the_chi0_of_the_rotated_k_point():
+    cell = np.eye(3) * 5.0
+    V = _cubic_potential()
+    k = np.array([0.5, 0.0, 0.0])
+    M = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]])  # 90 degrees about z (reduced = Cartesian here)
+    kr = M @ k
+    direct = _model_sets(cell, [k, kr], V)
+    rot = o.rotate_set(direct[0], M)
+    assert np.allclose(rot.k_red, kr)
+    om, _ = o.frequency_grid(3)
+    q = np.zeros(3)
+
+    def chi(sets):
+        qp = syn.QPoint(q, np.array([0]), np.array([0]), np.zeros((1, 3), np.int32), 1.0)
+        prob = syn.Problem("sym", 0, cell, (20, 20, 20), 2.8, 1.2, 2.0, 1, sets, [qp], 3)
+        return o.chi0(prob, 0, om)
+
+    a = chi([rot])
+    b = chi([direct[1]])
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    assert np.abs(b).max() > 1e-4
+    # time reversal: the set at -k is the conjugate (real potential)
+    tr = o.rotate_set(direct[0], np.eye(3, dtype=int), time_reversal=True)
+    neg = _model_sets(cell, [-k], V)[0]
+    assert np.abs(chi([tr]) - chi([neg])).max() <= 1e-10 * np.abs(b).max()
+    # a wrong rotation (transpose) breaks it
+    wrong = o.rotate_set(direct[0], M.T)
+    assert np.abs(chi([wrong]) - b).max() > 1e-3 * np.abs(b).max()
+
+
+def test_projector_rotation_composes_and_identity_is_a_no_op():
+    s = syn.make_orbitals(4, 0, np.eye(3) * 6.0, [0.1, 0.2, 0.0], 3.0, 3, 5)
+    nproj = [3, 3, 2]
+    rng = np.random.default_rng(2)
+    s = dataclasses.replace(s, P=rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8)))
+    eye = [np.eye(n) for n in nproj]
+    same = o.rotate_set(s, np.eye(3, dtype=int), False, nproj, [0, 1, 2], eye)
+    assert np.array_equal(same.P, s.P) and np.array_equal(same.miller, s.miller)
+
+    def unit(n):
+        q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        return q
+
+    D1 = [unit(n) for n in nproj]
+    D2 = [unit(n) for n in nproj]
+    amap1, amap2 = [1, 0, 2], [1, 0, 2]
+    twice = o.rotate_set(o.rotate_set(s, np.eye(3, dtype=int), False, nproj, amap1, D1),
+                         np.eye(3, dtype=int), False, nproj, amap2, D2)
+    # composition: target a takes source amap1[amap2[a]] with D2[a] D1[amap2[a]]
+    comp = [D2[a] @ D1[amap2[a]] for a in range(3)]
+    once = o.rotate_set(s, np.eye(3, dtype=int), False, nproj, [amap1[amap2[a]] for a in range(3)], comp)
+    assert np.allclose(twice.P, once.P, atol=1e-13)
