@@ -109,6 +109,23 @@ rpa_status rpa_set_orbitals(rpa_ctx* ctx, int32_t kidx, const double k_red[3],
                             int32_t nbands, int32_t npw, const int32_t* miller,
                             const double* C, const double* eps, const double* f);
 
+/* IBZ -> BZ symmetry (Eq. 9; Table 1 steps 4 and 7): orbital set kidx becomes
+ * the set src transformed by a crystal symmetry {T|tau},
+ * psi'(r) = psi(T^-1 (r - tau)), with optional time reversal psi -> conj(psi).
+ * M[9] (row-major, integers) is T on reduced reciprocal coordinates: k' = M k,
+ * and every plane wave Q -> M Q keeps its coefficient times
+ * exp(-2 pi i (M (k+Q)).tau), tau[3] the fractional translation in reduced
+ * real-space coordinates (NULL = 0).  time_reversal != 0 then negates k' and
+ * Q' and conjugates the coefficients.  M must be unimodular and keep the
+ * reciprocal metric (M^T B B^T M = B B^T), else RPA_ERR_ARG.  Eigenvalues and
+ * occupations are copied.  If src has projections, natoms must equal its
+ * atom count and P'[n][a][i] = sum_j D^a_ij P[n][atom_map[a]][j] (conjugated
+ * under time reversal), D atom after atom [ni][ni] complex, host or device
+ * (lattice-vector phases of the projectors belong in D).  kidx != src; the
+ * source is not modified. */
+rpa_status rpa_set_orbitals_sym(rpa_ctx* ctx, int32_t kidx, int32_t src, const int32_t* M, const double* tau,
+                                int32_t time_reversal, int32_t natoms, const int32_t* atom_map, const double* D);
+
 /* PAW projections of set kidx (Eq. 6; Table 1 step 7):
  * P[nbands][sum_a nproj[a]] (complex) with P_ni = <p~^a_i | psi~_nk>, atoms
  * in order.  nproj[a] in [1, 64].  P host or device. */

@@ -201,21 +201,29 @@ def _selection(f_k, f_kp):
 # ---------------------------------------------------------------------------
 # IBZ -> BZ symmetry (Eq. 9; Table 1 steps 4 and 7)
 # ---------------------------------------------------------------------------
-def rotate_set(oset, M, time_reversal=False, paw_nproj=None, atom_map=None, D=None):
-    """Orbital set at k' = M k from the set at k (Eq. 9: psi'(r) = psi(T^-1 r)).
+def rotate_set(oset, M, time_reversal=False, paw_nproj=None, atom_map=None, D=None, tau=None):
+    """Orbital set at k' = M k from the set at k (Eq. 9: psi'(r) = psi(T^-1 (r - tau))).
 
-    In the plane-wave basis the rotated orbital has the same coefficients on
-    the rotated reciprocal vectors: C'(M Q) = C(Q), with M the integer matrix of
-    the operation on reduced reciprocal coordinates.  Time reversal adds
-    psi -> conj(psi): k', Q' -> -k', -Q' and C' = conj(C).  Projections (step 7):
+    In the plane-wave basis the rotated orbital has the coefficients
+    C'(M Q) = C(Q) exp(-2 pi i (M (k+Q)).tau) on the rotated reciprocal vectors,
+    with M the integer matrix of the operation on reduced reciprocal
+    coordinates and tau the fractional translation in reduced real-space
+    coordinates (zero by default).  Time reversal adds psi -> conj(psi):
+    k', Q' -> -k', -Q' and C' -> conj(C').  Projections (step 7):
     P'[n, a, i] = sum_j D[a][i, j] P[n, atom_map[a], j] (conjugated under time
     reversal); D and atom_map describe the projectors and are inputs."""
     import dataclasses
     M = np.asarray(M, dtype=np.int64).reshape(3, 3)
     sg = -1 if time_reversal else 1
-    k = sg * (M @ np.asarray(oset.k_red, dtype=np.float64))
-    mil = (sg * (np.asarray(oset.miller, dtype=np.int64) @ M.T)).astype(np.int32)
-    C = np.conj(oset.C) if time_reversal else np.array(oset.C, copy=True)
+    kr = M @ np.asarray(oset.k_red, dtype=np.float64)
+    Qr = np.asarray(oset.miller, dtype=np.int64) @ M.T
+    k = sg * kr
+    mil = (sg * Qr).astype(np.int32)
+    C = np.array(oset.C, copy=True)
+    if tau is not None:
+        C = C * np.exp(-2j * np.pi * ((kr[None, :] + Qr) @ np.asarray(tau, dtype=np.float64)))[None, :]
+    if time_reversal:
+        C = np.conj(C)
     P = None
     if oset.P is not None and paw_nproj is not None:
         off = np.concatenate([[0], np.cumsum(paw_nproj)])

@@ -38,6 +38,7 @@ SIGNATURES = {
     "rpa_gvectors": (_I, [_P, _I, _P, _P]),
     "rpa_set_paw_Q": (_I, [_P, _I, _I, _P, _P]),
     "rpa_set_optical": (_I, [_P, _I, _P, _I, _P, _P]),
+    "rpa_set_orbitals_sym": (_I, [_P, _I, _I, _P, _P, _I, _I, _P, _P]),
     "rpa_chi0": (_I, [_P, _I, _I, _P, _P]),
     "rpa_energy": (_I, [_P, _I, _P, _P, _I, _P, _P, _P, _P]),
     "rpa_set_profiling": (_I, [_P, _I]),
@@ -184,6 +185,25 @@ def rpa_set_paw_Q(ctx, iq, nproj, Q):
     nproj = np.asarray(nproj, dtype=np.int32)
     _check(ctx, lib().rpa_set_paw_Q(ctx, int(iq), len(nproj), _ptr(nproj, np.int32, keep),
                                     _ptr(Q, np.complex128, keep)))
+
+
+def rpa_set_orbitals_sym(ctx, kidx, src, M, time_reversal=False, atom_map=None, D=None, tau=None):
+    """Set kidx = set src under the operation {M|tau} (M: 3x3 integers on reduced
+    reciprocal coordinates, tau: reduced fractional translation or None),
+    optionally time-reversed; ``D[a]`` (ni, ni) complex rotates the projections
+    of atom ``atom_map[a]`` onto atom a."""
+    keep = []
+    Mi = np.ascontiguousarray(np.asarray(M, dtype=np.int32).reshape(9))
+    tp = None if tau is None else _ptr(np.ascontiguousarray(tau, dtype=np.float64), np.float64, keep)
+    if D is None:
+        _check(ctx, lib().rpa_set_orbitals_sym(ctx, int(kidx), int(src), _ptr(Mi, np.int32, keep), tp,
+                                               int(bool(time_reversal)), 0, None, None))
+        return
+    am = np.ascontiguousarray(atom_map, dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(d, dtype=np.complex128).reshape(-1) for d in D]))
+    _check(ctx, lib().rpa_set_orbitals_sym(ctx, int(kidx), int(src), _ptr(Mi, np.int32, keep), tp,
+                                           int(bool(time_reversal)), len(am), _ptr(am, np.int32, keep),
+                                           _ptr(flat, np.complex128, keep)))
 
 
 def rpa_set_optical(ctx, iq, qdir, nproj=None, Qgrad=None):

@@ -131,3 +131,71 @@ template cudaError_t launch_optical_head<double>(const double2*, int, const doub
                                                  const double*, int, int, double2*, cudaStream_t);
 
 }  // namespace rpa
+
+// ---------------------------------------------------------------- IBZ -> BZ symmetry (Eq. 9, steps 4 and 7)
+namespace rpa {
+
+__global__ void conj_kernel(double2* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i].y = -x[i].y;
+}
+
+// out[n][off[a] + i] = sum_j D[doff[a] + i ni + j] P[n][off[src[a]] + j], conjugated if tr
+__global__ void rotate_P_kernel(const double2* __restrict__ P, int nb, int KP, int natoms, const int* __restrict__ meta,
+                                const double2* __restrict__ D, int tr, double2* __restrict__ out) {
+  // meta: off[natoms], src[natoms], ni[natoms], doff[natoms], atom_of[KP], idx_in[KP]
+  const int* off = meta;
+  const int* src = off + natoms;
+  const int* nis = src + natoms;
+  const int* doff = nis + natoms;
+  const int* atom_of = doff + natoms;
+  const int* idx_in = atom_of + KP;
+  const int64_t total = (int64_t)nb * KP;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(id % KP);
+    const int64_t n = id / KP;
+    const int a = atom_of[k], i = idx_in[k], ni = nis[a];
+    const double2* ps = P + n * KP + off[src[a]];
+    const double2* d = D + doff[a] + (int64_t)i * ni;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < ni; ++j) cmac<double>(acc, d[j], ps[j]);
+    if (tr) acc.y = -acc.y;
+    out[id] = acc;
+  }
+}
+
+// C[n][q] *= ph[q] for nb bands of npw plane waves
+__global__ void phase_kernel(double2* __restrict__ C, int64_t nb, int npw, const double2* __restrict__ ph) {
+  const int64_t total = nb * npw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = C[i], b = ph[i % npw];
+    C[i] = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  }
+}
+
+cudaError_t launch_phase(double2* C, int64_t nb, int npw, const double2* ph, cudaStream_t s) {
+  const int64_t n = nb * npw;
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  phase_kernel<<<blocks, 256, 0, s>>>(C, nb, npw, ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conj(double2* x, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  conj_kernel<<<blocks, 256, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_P(const double2* P, int nb, int KP, int natoms, const int* meta, const double2* D, int tr,
+                            double2* out, cudaStream_t s) {
+  const int64_t total = (int64_t)nb * KP;
+  if (total == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  rotate_P_kernel<<<blocks, 256, 0, s>>>(P, nb, KP, natoms, meta, D, tr, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rpa

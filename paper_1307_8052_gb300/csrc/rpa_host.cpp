@@ -1151,6 +1151,123 @@ rpa_status rpa_set_orbitals(rpa_ctx* c, int32_t kidx, const double k_red[3], int
   return RPA_OK;
 }
 
+rpa_status rpa_set_orbitals_sym(rpa_ctx* c, int32_t kidx, int32_t src, const int32_t* M, const double* tau,
+                                int32_t time_reversal, int32_t natoms, const int32_t* atom_map, const double* D) {
+  if (!c) return RPA_ERR_ARG;
+  if (kidx == src) return fail(c, RPA_ERR_ARG, "target and source set must differ");
+  auto it = c->sets.find(src);
+  if (it == c->sets.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "orbital set %d not set", src);
+  if (!M) return fail(c, RPA_ERR_ARG, "null rotation");
+  // M acts on reduced reciprocal coordinates; it must be unimodular and keep
+  // lengths: M^T G M = G with the metric G = B B^T of the reciprocal rows
+  const int64_t det = (int64_t)M[0] * (M[4] * M[8] - M[5] * M[7]) - (int64_t)M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                      (int64_t)M[2] * (M[3] * M[7] - M[4] * M[6]);
+  if (det != 1 && det != -1) return fail(c, RPA_ERR_ARG, "rotation matrix is not unimodular");
+  double G[9], scale = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int d = 0; d < 3; ++d) acc += c->B[3 * i + d] * c->B[3 * j + d];
+      G[3 * i + j] = acc;
+      scale = std::max(scale, std::fabs(acc));
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += M[3 * a + i] * G[3 * a + b] * M[3 * b + j];
+      if (std::fabs(acc - G[3 * i + j]) > 1e-9 * scale)
+        return fail(c, RPA_ERR_ARG, "rotation does not preserve the reciprocal metric");
+    }
+  if (tau && !(std::isfinite(tau[0]) && std::isfinite(tau[1]) && std::isfinite(tau[2])))
+    return fail(c, RPA_ERR_ARG, "tau not finite");
+  const OrbSet& so = it->second;
+  const int sg = time_reversal ? -1 : 1;
+  double kr[3], k[3];
+  for (int i = 0; i < 3; ++i) {
+    kr[i] = M[3 * i] * so.k[0] + M[3 * i + 1] * so.k[1] + M[3 * i + 2] * so.k[2];
+    k[i] = sg * kr[i];
+  }
+  std::vector<int> mil(so.miller.size());
+  std::vector<double2> ph(tau ? so.npw : 0);
+  for (int q = 0; q < so.npw; ++q) {
+    int Qr[3];
+    for (int i = 0; i < 3; ++i) {
+      Qr[i] = M[3 * i] * so.miller[3 * q] + M[3 * i + 1] * so.miller[3 * q + 1] + M[3 * i + 2] * so.miller[3 * q + 2];
+      mil[3 * q + i] = sg * Qr[i];
+    }
+    if (tau) {
+      // exp(-2 pi i (M (k+Q)).tau), before time reversal
+      const double x = (kr[0] + Qr[0]) * tau[0] + (kr[1] + Qr[1]) * tau[1] + (kr[2] + Qr[2]) * tau[2];
+      const double fr = x - std::nearbyint(x);  // the phase depends on x mod 1
+      ph[q] = make_double2(std::cos(2.0 * M_PI * fr), -std::sin(2.0 * M_PI * fr));
+    }
+  }
+  // the source's projections, copied before the new set may replace anything
+  const bool paw = so.P && natoms > 0;
+  if (so.P && natoms > 0 && natoms != so.natoms)
+    return fail(c, RPA_ERR_ARG, "natoms %d does not match the source set's %d", natoms, so.natoms);
+  if (paw && (!atom_map || !D)) return fail(c, RPA_ERR_ARG, "atom_map and D are needed for the projections");
+  std::vector<int> nproj = so.nproj;
+  const int KP = so.KP, nb = so.nb;
+  std::vector<int> meta;
+  int64_t dtot = 0;
+  if (paw) {
+    std::vector<int> off(natoms), srcv(natoms), doff(natoms), atom_of(KP), idx_in(KP);
+    int o = 0;
+    for (int a = 0; a < natoms; ++a) {
+      off[a] = o;
+      for (int j = 0; j < nproj[a]; ++j) {
+        atom_of[o + j] = a;
+        idx_in[o + j] = j;
+      }
+      o += nproj[a];
+    }
+    for (int a = 0; a < natoms; ++a) {
+      if (atom_map[a] < 0 || atom_map[a] >= natoms || nproj[atom_map[a]] != nproj[a])
+        return fail(c, RPA_ERR_ARG, "atom_map[%d] = %d invalid", a, atom_map[a]);
+      srcv[a] = atom_map[a];
+      doff[a] = (int)dtot;
+      dtot += (int64_t)nproj[a] * nproj[a];
+    }
+    meta.insert(meta.end(), off.begin(), off.end());
+    meta.insert(meta.end(), srcv.begin(), srcv.end());
+    meta.insert(meta.end(), nproj.begin(), nproj.end());
+    meta.insert(meta.end(), doff.begin(), doff.end());
+    meta.insert(meta.end(), atom_of.begin(), atom_of.end());
+    meta.insert(meta.end(), idx_in.begin(), idx_in.end());
+  }
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  rpa_status st;
+  void *p_meta = nullptr, *p_D = nullptr, *p_P = nullptr;
+  if (paw) {
+    if ((st = workspace(c, "sym_meta", sizeof(int) * meta.size(), &p_meta)) != RPA_OK) return st;
+    if ((st = workspace(c, "sym_D", sizeof(double2) * (size_t)dtot, &p_D)) != RPA_OK) return st;
+    if ((st = workspace(c, "sym_P", sizeof(double2) * (size_t)nb * KP, &p_P)) != RPA_OK) return st;
+    CUDA_OK(c, cudaMemcpyAsync(p_meta, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice, c->stream));
+    if ((st = copy_in(c, p_D, D, sizeof(double2) * (size_t)dtot)) != RPA_OK) return st;
+    CUDA_OK(c, launch_rotate_P(so.P, nb, KP, natoms, (const int*)p_meta, (const double2*)p_D, time_reversal ? 1 : 0,
+                               (double2*)p_P, c->stream));
+  }
+  // the coefficients travel unchanged to the rotated plane waves (device to device)
+  const std::vector<double> eps = so.eps, f = so.f;
+  const double2* Csrc = so.C;
+  const int npw = so.npw;
+  if ((st = rpa_set_orbitals(c, kidx, k, nb, npw, mil.data(), (const double*)Csrc, eps.data(), f.data())) != RPA_OK)
+    return st;
+  OrbSet& sn = c->sets[kidx];
+  if (tau) {
+    void* p_ph;
+    if ((st = workspace(c, "sym_phase", sizeof(double2) * (size_t)npw, &p_ph)) != RPA_OK) return st;
+    CUDA_OK(c, cudaMemcpyAsync(p_ph, ph.data(), sizeof(double2) * (size_t)npw, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(c, launch_phase(sn.C, nb, npw, (const double2*)p_ph, c->stream));
+  }
+  if (time_reversal) CUDA_OK(c, launch_conj(sn.C, (int64_t)nb * npw, c->stream));
+  if (paw && (st = rpa_set_paw(c, kidx, natoms, nproj.data(), (const double*)p_P)) != RPA_OK) return st;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return RPA_OK;
+}
+
 rpa_status rpa_set_paw(rpa_ctx* c, int32_t kidx, int32_t natoms, const int32_t* nproj, const double* P) {
   if (!c) return RPA_ERR_ARG;
   auto it = c->sets.find(kidx);

@@ -106,6 +106,14 @@ cudaError_t launch_optical_head(const double2* C, int npw, const double* s, cons
                                 const double2* Qn, double2* Y, const int* L, int nL, const int* R, int nR,
                                 const double* eps, int NG, int ig0, c2<T>* N, cudaStream_t st);
 
+// IBZ -> BZ symmetry (k_optical.cu): conjugation of coefficients, and rotation
+// of projections out[n][a][i] = sum_j D^a_ij P[n][src(a)][j] (conjugated if tr);
+// meta = off[natoms], src[natoms], ni[natoms], doff[natoms], atom_of[KP], idx_in[KP].
+cudaError_t launch_conj(double2* x, int64_t n, cudaStream_t s);
+cudaError_t launch_phase(double2* C, int64_t nb, int npw, const double2* ph, cudaStream_t s);
+cudaError_t launch_rotate_P(const double2* P, int nb, int KP, int natoms, const int* meta, const double2* D, int tr,
+                            double2* out, cudaStream_t s);
+
 // Complex elements of the work buffer run_logdet needs: the factor and the
 // inverses of its diagonal blocks.
 int64_t logdet_work_elems(int nw, int NG);

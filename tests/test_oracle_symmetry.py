@@ -89,3 +89,20 @@ def test_projector_rotation_composes_and_identity_is_a_no_op():
     comp = [D2[a] @ D1[amap2[a]] for a in range(3)]
     once = o.rotate_set(s, np.eye(3, dtype=int), False, nproj, [amap1[amap2[a]] for a in range(3)], comp)
     assert np.allclose(twice.P, once.P, atol=1e-13)
+
+
+def test_fractional_translation_multiplies_chi0_by_the_phase():
+    """Translating every orbital by tau (operation {I|tau}) gives
+    n'(G) = exp(-i (q+G).tau) n(G), hence chi0'_GG' = exp(-i (G-G').tau) chi0_GG'."""
+    p = syn.small_problem(config_tag=88, nproj=None)
+    tau = np.array([0.25, 0.1, -0.3])
+    I3 = np.eye(3, dtype=int)
+    moved = dataclasses.replace(p, sets=[o.rotate_set(s_, I3, tau=tau) for s_ in p.sets])
+    om, _ = o.frequency_grid(3)
+    iq = 1
+    gm = o.g_sphere(p.cell, p.qpoints[iq].q_red, p.ecut_chi)
+    a = o.chi0(p, iq, om)
+    b = o.chi0(moved, iq, om)
+    ph = np.exp(-2j * np.pi * (gm @ tau))
+    assert np.abs(b - a * ph[None, :, None] * np.conj(ph)[None, None, :]).max() <= 1e-13 * np.abs(a).max()
+    assert np.abs(b - a).max() > 1e-3 * np.abs(a).max()
