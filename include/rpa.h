@@ -174,6 +174,15 @@ rpa_status rpa_set_paw_Q(rpa_ctx* ctx, int32_t iq, int32_t natoms,
 rpa_status rpa_set_optical(rpa_ctx* ctx, int32_t iq, const double* qdir, int32_t natoms,
                            const int32_t* nproj, const double* Qgrad);
 
+/* Symmetrised inverse dielectric matrix of the RPA at q-point iq,
+ *   eps~^-1_GG'(q, i omega_j) = [(1 - v^1/2 chi0 v^1/2)^-1]_GG',
+ * for reuse of chi0 by other many-body kernels (e.g. the screened interaction
+ * W = v^1/2 eps~^-1 v^1/2 of GW): chi0 as in rpa_chi0 (with the optical
+ * limit if set), the Cholesky factor of the log-det, then L^-H L^-1 in FP64.
+ * out[nw][NG][NG] complex (full Hermitian matrix), host or device.
+ * RPA_ERR_NOT_HPD as for rpa_energy. */
+rpa_status rpa_epsilon_inv(rpa_ctx* ctx, int32_t iq, int32_t nw, const double* omega, double* out);
+
 /* chi0_GG'(q, i omega_j) of q-point iq (Eq. 3 summed as Eq. 17) for nw
  * frequencies omega[nw] (host).  Pairs (n at k, m at k+q) with f_n > f_m
  * enter with the real time-reversal-combined weight

@@ -373,6 +373,17 @@ def ec_terms(chi, v) -> np.ndarray:
     return out
 
 
+def epsilon_inv(chi, v) -> np.ndarray:
+    """Symmetrised inverse dielectric matrix of the RPA, (1 - v^1/2 chi0 v^1/2)^-1,
+    per frequency (the matrix whose log-determinant Eq. 1 integrates)."""
+    sv = np.sqrt(np.asarray(v, dtype=np.float64))
+    out = np.zeros_like(chi)
+    for j in range(chi.shape[0]):
+        M = sv[:, None] * chi[j] * sv[None, :]
+        out[j] = np.linalg.inv(np.eye(len(sv)) - M)
+    return out
+
+
 def energy(problem, omega, W, Qs=None, iqs=None, optical=None):
     """E_c = sum_q w_q sum_j W_j / (2 pi) e_q(w_j) (Eq. 2 with the IBZ weights of Sec. 2.1).
 

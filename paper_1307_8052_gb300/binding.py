@@ -40,6 +40,7 @@ SIGNATURES = {
     "rpa_set_optical": (_I, [_P, _I, _P, _I, _P, _P]),
     "rpa_set_orbitals_sym": (_I, [_P, _I, _I, _P, _P, _I, _I, _P, _P]),
     "rpa_chi0": (_I, [_P, _I, _I, _P, _P]),
+    "rpa_epsilon_inv": (_I, [_P, _I, _I, _P, _P]),
     "rpa_energy": (_I, [_P, _I, _P, _P, _I, _P, _P, _P, _P]),
     "rpa_set_profiling": (_I, [_P, _I]),
     "rpa_get_profile": (_I, [_P, _P, _P]),
@@ -232,6 +233,18 @@ def rpa_chi0(ctx, iq, omega, out=None):
         _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
         out = np.zeros((len(omega), ng.value, ng.value), dtype=np.complex128)
     _check(ctx, lib().rpa_chi0(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), _ptr(out, None, keep)))
+    return out
+
+
+def rpa_epsilon_inv(ctx, iq, omega, out=None):
+    """(1 - v^1/2 chi0 v^1/2)^-1 [nw][NG][NG] complex128; ``out`` may be a preallocated numpy array or CUDA tensor."""
+    keep = []
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    if out is None:
+        ng = ct.c_int32()
+        _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
+        out = np.zeros((len(omega), ng.value, ng.value), dtype=np.complex128)
+    _check(ctx, lib().rpa_epsilon_inv(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), _ptr(out, None, keep)))
     return out
 
 

@@ -1540,6 +1540,49 @@ rpa_status rpa_set_paw_Q(rpa_ctx* c, int32_t iq, int32_t natoms, const int32_t* 
   return RPA_OK;
 }
 
+rpa_status rpa_epsilon_inv(rpa_ctx* c, int32_t iq, int32_t nw, const double* omega, double* out) {
+  if (!c) return RPA_ERR_ARG;
+  if (nw < 1 || nw > 4096 || !omega || !out) return fail(c, RPA_ERR_ARG, "bad rpa_epsilon_inv arguments");
+  CUDA_OK(c, cudaSetDevice(c->prm.device));
+  prof_begin(c);
+  ++c->stamp;
+  rpa_status st = check_q_ready(c, iq);
+  if (st != RPA_OK) return st;
+  choose_transform_grid(c, &iq, 1);
+  double2* chi = nullptr;
+  if ((st = build_chi(c, iq, nw, omega, &chi)) != RPA_OK) return st;
+  QPt& Q = c->qpts[iq];
+  const int NG = Q.NG;
+  const size_t mat = sizeof(double2) * (size_t)nw * NG * NG;
+  void *p_work, *p_ld, *p_tr, *p_flag, *p_Y, *p_W, *p_cw;
+  if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw, NG), &p_work)) != RPA_OK) return st;
+  if ((st = workspace(c, "logdet", sizeof(double) * nw, &p_ld)) != RPA_OK) return st;
+  if ((st = workspace(c, "trace", sizeof(double) * nw, &p_tr)) != RPA_OK) return st;
+  if ((st = workspace(c, "flag", sizeof(int), &p_flag)) != RPA_OK) return st;
+  if ((st = workspace(c, "adj_Y", mat, &p_Y)) != RPA_OK) return st;
+  if ((st = workspace(c, "adj_W", mat, &p_W)) != RPA_OK) return st;
+  if ((st = workspace(c, "cw", sizeof(double) * nw, &p_cw)) != RPA_OK) return st;
+  CUDA_OK(c, cudaMemsetAsync(p_cw, 0, sizeof(double) * nw, c->stream));
+  {
+    int64_t nl = 0;
+    StageTimer tm(c, 3, 0);
+    CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
+                          ff_logdet(c), c->stream, &nl));
+    // (1 - M)^-1 = L^-H L^-1 from the factor (the Gamma output is not needed)
+    CUDA_OK(c, run_gamma((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y, (double2*)p_W,
+                         nullptr, nullptr, c->stream, &nl));
+    tm.add_launches(nl);
+  }
+  int flag = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&flag, p_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  const bool dev = is_device_ptr(out);
+  CUDA_OK(c, cudaMemcpyAsync(out, p_W, mat, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (flag) return fail(c, RPA_ERR_NOT_HPD, "1 - v^1/2 chi0 v^1/2 is not positive definite at q-point %d", iq);
+  prof_end(c);
+  return RPA_OK;
+}
+
 rpa_status rpa_chi0(rpa_ctx* c, int32_t iq, int32_t nw, const double* omega, double* chi_out) {
   if (!c) return RPA_ERR_ARG;
   if (nw < 1 || nw > 4096 || !omega || !chi_out) return fail(c, RPA_ERR_ARG, "bad rpa_chi0 arguments");

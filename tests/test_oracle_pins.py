@@ -372,3 +372,31 @@ def test_spin_channels_add_up():
     a = o.chi0(same, iq, om, Q)
     b = o.chi0(paired, iq, om, Q)
     assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+
+
+def test_epsilon_inverse_adiabatic_connection():
+    """The RPA correlation term from the coupling-constant integral
+    e = int_0^1 dlambda tr[((1 - lambda M)^-1 - 1) M] (adiabatic connection, exact
+    for the RPA) against the eigenvalue form ln det(1 - M) + tr M of the oracle."""
+    p = syn.small_problem(config_tag=89)
+    om, _ = o.frequency_grid(3)
+    iq = 1
+    qp = p.qpoints[iq]
+    gm = o.g_sphere(p.cell, qp.q_red, p.ecut_chi)
+    Q = syn.paw_Q(p.paw, p.cell, qp.q_red, gm)
+    chi = o.chi0(p, iq, om, Q)
+    v = o.coulomb(p.cell, qp.q_red, gm)
+    e_ref = o.ec_terms(chi, v)
+    x, wl = o.gauss_legendre(40)
+    lam, wl = 0.5 * (x + 1.0), 0.5 * wl
+    sv = np.sqrt(v)
+    e = np.zeros(len(om))
+    for lm, wgt in zip(lam, wl):
+        einv = o.epsilon_inv(lm * chi, v)
+        for j in range(len(om)):
+            M = sv[:, None] * chi[j] * sv[None, :]
+            e[j] -= wgt * np.trace((einv[j] - np.eye(len(v))) @ M).real
+    # d/dlambda [ln det(1 - lambda M) + lambda tr M] = -tr[(1-lambda M)^-1 M] + tr M
+    # so e = int_0^1 (tr M - tr[(1 - lambda M)^-1 M]) dlambda = -int tr[((1-lM)^-1 - 1) M]
+    assert np.allclose(e, e_ref, rtol=1e-9, atol=1e-12 * np.abs(e_ref).max())
+    assert np.abs(e_ref).max() > 1e-3
