@@ -260,11 +260,14 @@ rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
 rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
 
 /* Tuning knobs (no effect on results beyond rounding order):
- * RPA_TUNE_TC_FOLD     stages of 64 K-elements accumulated in FP32 tensor
- *                      memory before the partial sum is added to FP32
- *                      running sums in registers (split-bfloat16 modes), in
- *                      [1, 2^20]; default 1.  The tensor cores truncate while
- *                      accumulating, so longer folds bias |chi0| low.
+ * RPA_TUNE_TC_FOLD     units of K accumulated in FP32 tensor memory before
+ *                      the partial sum is added to FP32 running sums in
+ *                      registers (split-bfloat16 modes), in [1, 2^20];
+ *                      default 1.  A unit is 64 K-elements in BF16X2 and 32 in
+ *                      BF16X3 (twice the products per element), i.e. twelve
+ *                      tensor-core accumulation steps either way.  The tensor
+ *                      cores truncate while accumulating, so longer folds
+ *                      bias |chi0| low.
  * RPA_TUNE_PAIR_CHUNK  pairs per pair-density launch; 0 = sized automatically
  *                      so the transform intermediates stay in L2.
  * RPA_TUNE_TC_FLUSH    folds between additions of the register running sums

@@ -594,7 +594,10 @@ static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpa
   using C = Cfg<TERMS, BK, STAGES>;
   static_assert(C::SMEM_BYTES <= 227 * 1024, "shared-memory ring too large");
   const int nk = (int)(Kpad / BK);
-  const int fold = fold64 * (64 / BK);  // the fold length is counted in 64-element units
+  // the fold length counts 64-element units of three products (two terms);
+  // with three terms (six products per element) a unit is 32 elements, so a
+  // fold holds the same number of truncating tensor-core accumulations
+  const int fold = TERMS == 3 ? fold64 * (32 / BK) : fold64 * (64 / BK);
   cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<TERMS, BK, STAGES, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
   if (e != cudaSuccess) return e;
