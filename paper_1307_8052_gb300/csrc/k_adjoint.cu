@@ -112,6 +112,66 @@ cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2* A, i
   return cudaGetLastError();
 }
 
+// W = Y^H Y for lower-triangular Y (Y = L^-1): W[i][j] = sum_{k >= max(i,j)}
+// conj(Y[k][i]) Y[k][j].  Only lower-triangle 64 x 64 tiles of W are formed
+// (W is Hermitian), each summing k from its first row (Y[k][i] = 0 for k < i).
+__device__ __forceinline__ void lower_tile(int t, int& ti, int& tj) {
+  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
+
+__global__ void __launch_bounds__(256) yhy_lower_kernel(const double2* __restrict__ Y, int n, double2* __restrict__ W) {
+  __shared__ double2 As[ZK][ZT];
+  __shared__ double2 Bs[ZK][ZT];
+  const int z = blockIdx.y;
+  const double2* Yz = Y + (int64_t)z * n * n;
+  double2* Wz = W + (int64_t)z * n * n;
+  int ti, tj;
+  lower_tile(blockIdx.x, ti, tj);
+  const int m0 = ti * ZT, n0 = tj * ZT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
+  for (int k0 = m0; k0 < n; k0 += ZK) {
+#pragma unroll
+    for (int q = 0; q < (ZK * ZT) / 256; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int kk = e / ZT, c = e % ZT;
+      const bool kin = k0 + kk < n;
+      const double2 a = (kin && m0 + c < n) ? Yz[(int64_t)(k0 + kk) * n + m0 + c] : make_double2(0.0, 0.0);
+      As[kk][c] = make_double2(a.x, -a.y);
+      Bs[kk][c] = (kin && n0 + c < n) ? Yz[(int64_t)(k0 + kk) * n + n0 + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ZK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac<double>(acc[r][c], a[r], b[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = m0 + ty + 16 * r, j = n0 + tx + 16 * c;
+      if (i < n && j <= i) Wz[(int64_t)i * n + j] = acc[r][c];
+    }
+}
+
 // ---------------------------------------------------------------- (1 - M)^-1 from the Cholesky factor
 constexpr int FB = 32;
 
@@ -136,8 +196,9 @@ __global__ void __launch_bounds__(256) fwd_sub_diag_kernel(const double2* __rest
     Ld[r][l] = (l <= r) ? Lw[(int64_t)(i0 + r) * n + i0 + l] : make_double2(0.0, 0.0);
   }
   __syncthreads();
+  // columns beyond the block are zero in these rows (Y is lower triangular)
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+  if (c >= i0 + b) return;
   double2 y[FB];
 #pragma unroll
   for (int r = 0; r < FB; ++r) y[r] = (r < b) ? Yw[(int64_t)(i0 + r) * n + c] : make_double2(0.0, 0.0);
@@ -195,21 +256,25 @@ cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int n
   for (int i0 = 0; i0 < n; i0 += FB) {
     const int b = (n - i0) < FB ? (n - i0) : FB;
     if (i0 > 0) {
-      // Y[i0:i0+b, :] -= L[i0:i0+b, 0:i0] Y[0:i0, :]
-      if ((e = launch_zgemm(b, n, i0, make_double2(-1.0, 0.0), L + (int64_t)i0 * n, n, (int64_t)n * n, 0, Y, n,
+      // Y[i0:i0+b, 0:i0] -= L[i0:i0+b, 0:i0] Y[0:i0, 0:i0] (Y[0:i0, i0:] is zero)
+      if ((e = launch_zgemm(b, i0, i0, make_double2(-1.0, 0.0), L + (int64_t)i0 * n, n, (int64_t)n * n, 0, Y, n,
                             (int64_t)n * n, make_double2(1.0, 0.0), Y + (int64_t)i0 * n, n, (int64_t)n * n, nw, s)) !=
           cudaSuccess)
         return e;
       ++nl;
     }
-    fwd_sub_diag_kernel<<<dim3((n + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
+    fwd_sub_diag_kernel<<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
     ++nl;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // W = Y^H Y = L^-H L^-1 = (1 - M)^-1
-  if ((e = launch_zgemm(n, n, n, make_double2(1.0, 0.0), Y, n, (int64_t)n * n, 1, Y, n, (int64_t)n * n,
-                        make_double2(0.0, 0.0), Wm, n, (int64_t)n * n, nw, s)) != cudaSuccess)
-    return e;
+  // W = Y^H Y = L^-H L^-1 = (1 - M)^-1: lower tiles, then the upper triangle by symmetry
+  {
+    const int nt = (n + ZT - 1) / ZT;
+    yhy_lower_kernel<<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(Y, n, Wm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_hermitian_fill(Wm, nw, n, s)) != cudaSuccess) return e;
+    nl += 2;
+  }
   gamma_kernel<<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Wm, v, cw, n, nw, G64, G32);
   nl += 2;
   if (launches) *launches += nl;
