@@ -435,17 +435,13 @@ cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2,
   }
 }
 
-// ---------------------------------------------------------------- pair density stage C (+ PAW)
+// ---------------------------------------------------------------- pair density stage C
 template <typename T>
 __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict__ T2, int np, int n1, int n2, int N3,
                                                         const int* __restrict__ gfft, int NG, int g1lo, int g2lo,
-                                                        double inv_nr, const c2<T>* __restrict__ R,
-                                                        const c2<T>* __restrict__ Pm, int KP,
-                                                        const int* __restrict__ Ridx, int nR, int64_t p0,
-                                                        c2<T>* __restrict__ Nout) {
-  // Each thread handles one G and PG consecutive pairs: the fastest-axis DFT
-  // runs per pair, the PAW factor R_n(kp, G) is loaded once for the pairs that
-  // share the occupied band n.
+                                                        double inv_nr, int64_t p0, c2<T>* __restrict__ Nout) {
+  // Each thread handles one G and PG consecutive pairs (the fastest-axis DFT
+  // of each pair; PG independent loads per step).
   constexpr int PG = 4;
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
@@ -479,42 +475,90 @@ __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict_
       if (idx >= N3) idx -= N3;
     }
 #pragma unroll
-    for (int q = 0; q < PG; ++q) acc[q] = mk<T>(acc[q].x * scale, acc[q].y * scale);
-    if (KP > 0) {
-      const int64_t a0 = pidx[0] / nR;
-      bool same = true;
+    for (int q = 0; q < PG; ++q)
+      if (grp * PG + q < np) Nout[pidx[q] * NG + ig] = mk<T>(acc[q].x * scale, acc[q].y * scale);
+  }
+}
+
+// ---------------------------------------------------------------- PAW term (Eq. 6, steps 8-9)
+// N[(a nR + b) NG + g] += sum_kp Pm[b][kp] R[a][kp][g] for every occupied row a
+// of the block: one complex GEMM (nR x KP) x (KP x NG) per a, 64 x 64 tiles,
+// 4 x 4 outputs a thread.
+constexpr int PWT = 64, PWK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) paw_gemm_kernel(const c2<T>* __restrict__ R, const c2<T>* __restrict__ Pm,
+                                                       int KP, int nR, int NG, c2<T>* __restrict__ N) {
+  __shared__ c2<T> As[PWK][PWT];
+  __shared__ c2<T> Bs[PWK][PWT];
+  const int a = blockIdx.z;
+  const int b0 = blockIdx.y * PWT, g0 = blockIdx.x * PWT;
+  const c2<T>* Ra = R + (int64_t)a * KP * NG;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  c2<T> acc[4][4];
 #pragma unroll
-      for (int q = 1; q < PG; ++q) same = same && (pidx[q] / nR == a0);
-      if (same) {
-        const c2<T>* rr = R + a0 * (int64_t)KP * NG + ig;
-        for (int kp = 0; kp < KP; ++kp) {
-          const c2<T> r = rr[(int64_t)kp * NG];
+  for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int q = 0; q < PG; ++q) cmac<T>(acc[q], Pm[(pidx[q] % nR) * KP + kp], r);
-        }
-      } else {
+    for (int c = 0; c < 4; ++c) acc[r][c] = mk<T>(0, 0);
+  for (int k0 = 0; k0 < KP; k0 += PWK) {
 #pragma unroll
-        for (int q = 0; q < PG; ++q) {
-          const c2<T>* rr = R + (pidx[q] / nR) * (int64_t)KP * NG + ig;
-          const c2<T>* pm = Pm + (pidx[q] % nR) * KP;
-          for (int kp = 0; kp < KP; ++kp) cmac<T>(acc[q], pm[kp], rr[(int64_t)kp * NG]);
-        }
+    for (int q = 0; q < (PWK * PWT) / 256; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      {
+        const int r = e / PWK, kk = e % PWK;
+        As[kk][r] = (b0 + r < nR && k0 + kk < KP) ? Pm[(int64_t)(b0 + r) * KP + k0 + kk] : mk<T>(0, 0);
+      }
+      {
+        const int kk = e / PWT, c = e % PWT;
+        Bs[kk][c] = (k0 + kk < KP && g0 + c < NG) ? Ra[(int64_t)(k0 + kk) * NG + g0 + c] : mk<T>(0, 0);
       }
     }
+    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < PG; ++q)
-      if (grp * PG + q < np) Nout[pidx[q] * NG + ig] = acc[q];
+    for (int kk = 0; kk < PWK; ++kk) {
+      c2<T> x[4], y[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac<T>(acc[r][c], x[r], y[c]);
+    }
+    __syncthreads();
   }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int b = b0 + ty + 16 * r, g = g0 + tx + 16 * c;
+      if (b < nR && g < NG) {
+        c2<T>* p = N + ((int64_t)a * nR + b) * NG + g;
+        c2<T> v = *p;
+        v.x += acc[r][c].x;
+        v.y += acc[r][c].y;
+        *p = v;
+      }
+    }
+}
+
+template <typename T>
+cudaError_t launch_paw_gemm(const c2<T>* R, const c2<T>* Pm, int KP, int nL, int nR, int NG, c2<T>* N,
+                            cudaStream_t s) {
+  if (KP == 0 || nL == 0 || nR == 0 || NG == 0) return cudaSuccess;
+  dim3 grid((NG + PWT - 1) / PWT, (nR + PWT - 1) / PWT, nL);
+  paw_gemm_kernel<T><<<grid, 256, 0, s>>>(R, Pm, KP, nR, NG, N);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft, int NG, int g1lo,
-                             int g2lo, double inv_nr, const c2<T>* R, const c2<T>* Pm, int KP, const int* Ridx,
-                             int nR, int64_t p0, c2<T>* Nout, cudaStream_t s) {
+                             int g2lo, double inv_nr, int64_t p0, c2<T>* Nout, cudaStream_t s) {
   const int64_t total = (int64_t)((np + 3) / 4) * NG;
   if (total == 0) return cudaSuccess;
   pd_stageC_kernel<T><<<grid_for(total, 256), 256, N3 * sizeof(c2<T>), s>>>(T2, np, n1, n2, N3, gfft, NG, g1lo, g2lo,
-                                                                          inv_nr, R, Pm, KP, Ridx, nR, p0, Nout);
+                                                                          inv_nr, p0, Nout);
   return cudaGetLastError();
 }
 
@@ -617,8 +661,8 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
   template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
                                            int, int64_t, int, const c2<T>*, int, c2<T>*, cudaStream_t);          \
   template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \
-                                           const c2<T>*, const c2<T>*, int, const int*, int, int64_t, c2<T>*,      \
-                                           cudaStream_t);                                                        \
+                                           int64_t, c2<T>*, cudaStream_t);                                       \
+  template cudaError_t launch_paw_gemm<T>(const c2<T>*, const c2<T>*, int, int, int, int, c2<T>*, cudaStream_t); \
   template cudaError_t launch_paw_R<T>(const double2*, int, const int*, int, const double2*, const int*,          \
                                        const int*, const int*, const int64_t*, const int*, int, c2<T>*,          \
                                        cudaStream_t);                                                            \

@@ -521,8 +521,12 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
       CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                      c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
-                                     1.0 / (double)Nr, Rp, Pm, KP, skp.R_d, nR, p0, (c2<T>*)p_N, c->stream));
+                                     1.0 / (double)Nr, p0, (c2<T>*)p_N, c->stream));
       tm.add_launches(3);
+    }
+    if (paw) {
+      CUDA_OK(c, launch_paw_gemm<T>(Rp, Pm, KP, nL, nR, NG, (c2<T>*)p_N, c->stream));
+      tm.add_launches(1);
     }
   }
   if (Q.optical) {

@@ -61,12 +61,15 @@ cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2,
                              cudaStream_t s);
 
 // Pair densities, stage C: DFT along the fastest axis evaluated on the sphere
-// points g = G + G0, 1/Nr normalisation, PAW term, write N[p][NG].
+// points g = G + G0, 1/Nr normalisation, write N[p][NG].
 template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft,
-                             int NG, int g1lo, int g2lo, double inv_nr,
-                             const c2<T>* R, const c2<T>* Pm, int KP, const int* Ridx, int nR,
-                             int64_t p0, c2<T>* Nout, cudaStream_t s);
+                             int NG, int g1lo, int g2lo, double inv_nr, int64_t p0, c2<T>* Nout, cudaStream_t s);
+
+// PAW term of a block: N[(a nR + b)][g] += sum_kp Pm[b][kp] R[a][kp][g].
+template <typename T>
+cudaError_t launch_paw_gemm(const c2<T>* R, const c2<T>* Pm, int KP, int nL, int nR, int NG, c2<T>* N,
+                            cudaStream_t s);
 
 // PAW factor R_a[aL][kp][G] = sum_i conj(P_n,(a,i)) Q^a_ij(G), FP64 arithmetic.
 template <typename T>
