@@ -105,19 +105,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+HERK_DEVICE_END = "// ---------------------------------------------------------------- operand preparation"
+
+
 def herk_traffic():
     """DRAM bytes per launch of the rank-k kernel from the committed ncu summary,
-    or None when the kernel source has changed since the counters were taken."""
+    or None when the kernel's device code (the source up to its operand
+    preparation section) has changed since the counters were taken."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "herk_tc_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        with open(os.path.join(ROOT, d["source"]), "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(ROOT, d["source"])) as f:
+            src = f.read()
+        h = hashlib.sha256(src[:src.index(HERK_DEVICE_END)].encode()).hexdigest()
     except (OSError, KeyError, ValueError):
         return None
-    if h != d.get("source_sha256"):
+    if h != d.get("device_code_sha256"):
         return None
     return float(d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"])
 
@@ -390,7 +395,7 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": herk_traffic() if (bound == "tensor" and args.config == "bulk") else None,
                      "traffic_note": "ncu DRAM read+write bytes of one launch of the profiling case (one k-block, "
-                                     "NG 1180); null once the kernel source differs from the captured one",
+                                     "NG 1180); null once the kernel's device code differs from the captured one",
                      "peak_source": peak_kind if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x max clock"},
         "clocks": clk.summary(),
         "cpu_baseline": base,

@@ -32,16 +32,17 @@ __global__ void optical_paw_y_kernel(const double2* __restrict__ P, int KP, cons
   }
 }
 
-// D[a][b] = sum_k A_k(n_a) B_k(m_b) over K = npw (+ KP), 4 x 4 outputs a thread;
-// then N[(a nR + b) NG + ig0] = -i D / (e_m - e_n).
+// Partial D[a][b] = sum_k A_k(n_a) B_k(m_b) over this CTA's slice of K = npw
+// (+ KP), 4 x 4 outputs a thread, into Dp[split][nL][nR].  The K dimension is
+// split across CTAs because nL x nR is small (a few dozen tiles).
 template <typename T>
-__global__ void __launch_bounds__(256) optical_head_kernel(const double2* __restrict__ C, int npw,
-                                                           const double* __restrict__ s,
-                                                           const double2* __restrict__ P, int KP,
-                                                           const double2* __restrict__ Y, const int* __restrict__ L,
-                                                           int nL, const int* __restrict__ R, int nR,
-                                                           const double* __restrict__ eps, int NG, int ig0,
-                                                           c2<T>* __restrict__ N) {
+__global__ void __launch_bounds__(256) optical_dipole_kernel(const double2* __restrict__ C, int npw,
+                                                             const double* __restrict__ s,
+                                                             const double2* __restrict__ P, int KP,
+                                                             const double2* __restrict__ Y,
+                                                             const int* __restrict__ L, int nL,
+                                                             const int* __restrict__ R, int nR, int kslice,
+                                                             double2* __restrict__ Dp) {
   __shared__ double2 As[OK][OT];
   __shared__ double2 Bs[OK][OT];
   const int a0 = blockIdx.y * OT, b0 = blockIdx.x * OT;
@@ -52,14 +53,15 @@ __global__ void __launch_bounds__(256) optical_head_kernel(const double2* __rest
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
   const int K = npw + (P ? KP : 0);
-  for (int k0 = 0; k0 < K; k0 += OK) {
+  const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
+  for (int k0 = kbeg; k0 < kend; k0 += OK) {
 #pragma unroll
     for (int q = 0; q < (OK * OT) / 256; ++q) {
       const int e = threadIdx.x + 256 * q;
       const int kk = e / OT, r = e % OT;
       const int k = k0 + kk;
       double2 av = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
-      if (k < K) {
+      if (k < kend) {
         if (a0 + r < nL) {
           const int n = L[a0 + r];
           if (k < npw) {
@@ -94,32 +96,66 @@ __global__ void __launch_bounds__(256) optical_head_kernel(const double2* __rest
     }
     __syncthreads();
   }
+  double2* Dz = Dp + (int64_t)blockIdx.z * nL * nR;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int a = a0 + ty + 16 * r, b = b0 + tx + 16 * c;
-      if (a < nL && b < nR) {
-        const double de = eps[R[b]] - eps[L[a]];
-        // -i D / de
-        const double2 d = acc[r][c];
-        N[((int64_t)a * nR + b) * NG + ig0] = mk<T>((T)(d.y / de), (T)(-d.x / de));
-      }
+      if (a < nL && b < nR) Dz[(int64_t)a * nR + b] = acc[r][c];
     }
+}
+
+// N[(a nR + b) NG + ig0] = -i D / (e_m - e_n), D the sum of the nsplit partials
+template <typename T>
+__global__ void optical_head_kernel(const double2* __restrict__ Dp, int nsplit, const int* __restrict__ L, int nL,
+                                    const int* __restrict__ R, int nR, const double* __restrict__ eps, int NG,
+                                    int ig0, c2<T>* __restrict__ N) {
+  const int64_t total = (int64_t)nL * nR;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    double2 d = make_double2(0.0, 0.0);
+    for (int z = 0; z < nsplit; ++z) {
+      const double2 v = Dp[(int64_t)z * total + id];
+      d.x += v.x;
+      d.y += v.y;
+    }
+    const int a = (int)(id / nR), b = (int)(id % nR);
+    const double de = eps[R[b]] - eps[L[a]];
+    N[id * NG + ig0] = mk<T>((T)(d.y / de), (T)(-d.x / de));  // -i D / de
+  }
+}
+
+int64_t optical_scratch_elems(int nL, int nR, int npw, int KP) {
+  const int tiles = ((nR + OT - 1) / OT) * ((nL + OT - 1) / OT);
+  const int K = npw + KP;
+  const int nsplit = std::max(1, std::min((K + 255) / 256, (2 * 152 + tiles - 1) / tiles));
+  return (int64_t)nR * KP + (int64_t)nsplit * nL * nR;
 }
 
 template <typename T>
 cudaError_t launch_optical_head(const double2* C, int npw, const double* s, const double2* P, int KP,
-                                const double2* Qn, double2* Y, const int* L, int nL, const int* R, int nR,
+                                const double2* Qn, double2* scratch, const int* L, int nL, const int* R, int nR,
                                 const double* eps, int NG, int ig0, c2<T>* N, cudaStream_t st) {
   if (nL == 0 || nR == 0) return cudaSuccess;
+  // scratch: Y [nR][KP], then the K-split partials [nsplit][nL][nR]
+  const int kp = P ? KP : 0;
+  double2* Y = scratch;
+  double2* Dp = scratch + (int64_t)nR * kp;
   if (P) {
     const int64_t total = (int64_t)nR * KP;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     optical_paw_y_kernel<<<blocks, 256, 0, st>>>(P, KP, Qn, R, nR, Y);
   }
-  dim3 grid((nR + OT - 1) / OT, (nL + OT - 1) / OT);
-  optical_head_kernel<T><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, eps, NG, ig0, N);
+  const int tiles = ((nR + OT - 1) / OT) * ((nL + OT - 1) / OT);
+  const int K = npw + kp;
+  const int nsplit = std::max(1, std::min((K + 255) / 256, (2 * 152 + tiles - 1) / tiles));
+  const int kslice = ((K + nsplit - 1) / nsplit + OK - 1) / OK * OK;
+  dim3 grid((nR + OT - 1) / OT, (nL + OT - 1) / OT, nsplit);
+  optical_dipole_kernel<T><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, kslice, Dp);
+  const int64_t total = (int64_t)nL * nR;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  optical_head_kernel<T><<<blocks, 256, 0, st>>>(Dp, nsplit, L, nL, R, nR, eps, NG, ig0, N);
   return cudaGetLastError();
 }
 

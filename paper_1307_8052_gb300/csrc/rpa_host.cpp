@@ -535,8 +535,9 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
     if (pawo && sk.KP != Q.KPo)
       return fail(c, RPA_ERR_ARG, "projector count of set %d does not match the optical Qgrad", Q.k_of[t]);
     void* p_y = nullptr;
-    if (pawo && (st = workspace(c, "optical_y", sizeof(double2) * (size_t)nR * Q.KPo, &p_y)) != RPA_OK) return st;
-    StageTimer tm(c, 1, pawo ? 2 : 1);
+    const size_t ob = sizeof(double2) * (size_t)optical_scratch_elems(nL, nR, sk.npw, pawo ? Q.KPo : 0);
+    if ((st = workspace(c, "optical_scratch", ob, &p_y)) != RPA_OK) return st;
+    StageTimer tm(c, 1, pawo ? 3 : 2);
     CUDA_OK(c, launch_optical_head<T>(sk.C, sk.npw, Q.s_d[Q.k_of[t]], pawo ? sk.P : nullptr, Q.KPo, Q.Qn_d,
                                       (double2*)p_y, Lsub, nL, skp.R_d, nR, sk.eps_d, NG, Q.ig0, (c2<T>*)p_N,
                                       c->stream));

@@ -103,10 +103,12 @@ cudaError_t launch_hermitian_fill(double2* chi, int nw, int NG, cudaStream_t s);
 
 // Optical limit (k_optical.cu): G = 0 column of a block of pair densities at
 // q = 0 from q^.<psi_n|grad|psi_m> (plane-wave part with s[Q] = q^.(k+Q),
-// PAW part from the dense q^.Q_grad matrix Qn [KP][KP]; Y is scratch [nR][KP]).
+// PAW part from the dense q^.Q_grad matrix Qn [KP][KP]); scratch holds
+// optical_scratch_elems(nL, nR, npw, KP) complex FP64 elements.
+int64_t optical_scratch_elems(int nL, int nR, int npw, int KP);
 template <typename T>
 cudaError_t launch_optical_head(const double2* C, int npw, const double* s, const double2* P, int KP,
-                                const double2* Qn, double2* Y, const int* L, int nL, const int* R, int nR,
+                                const double2* Qn, double2* scratch, const int* L, int nL, const int* R, int nR,
                                 const double* eps, int NG, int ig0, c2<T>* N, cudaStream_t st);
 
 // IBZ -> BZ symmetry (k_optical.cu): conjugation of coefficients, and rotation
