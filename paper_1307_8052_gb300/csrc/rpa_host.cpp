@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -124,6 +125,11 @@ struct rpa_ctx {
   rpa_params prm{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // second stream of the tensor-core pipeline (operand preparation of the next
+  // block beside the rank-k kernel of the current one) and its events
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_pd[2] = {nullptr, nullptr}, ev_prep[2] = {nullptr, nullptr}, ev_herk[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double B[9] = {0};  // reciprocal rows
   double volume = 0.0;
   std::string err;
@@ -255,19 +261,21 @@ cudaEvent_t next_event(rpa_ctx* c) {
 struct StageTimer {
   rpa_ctx* c;
   int stage;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  StageTimer(rpa_ctx* cc, int s, int64_t launches) : c(cc), stage(s) {
+  StageTimer(rpa_ctx* cc, int s, int64_t launches, cudaStream_t stream = nullptr)
+      : c(cc), stage(s), st(stream ? stream : cc->stream) {
     c->prof_launch[s] += launches;
     if (c->profiling) {
       a = next_event(c);
-      cudaEventRecord(a, c->stream);
+      cudaEventRecord(a, st);
     }
   }
   void add_launches(int64_t n) { c->prof_launch[stage] += n; }
   ~StageTimer() {
     if (c->profiling) {
       cudaEvent_t b = next_event(c);
-      cudaEventRecord(b, c->stream);
+      cudaEventRecord(b, st);
       c->ev.push_back({stage, {a, b}});
     }
   }
@@ -413,7 +421,8 @@ int rows_per_block(const rpa_ctx* c, int nL, int nR, int NG, int nw) {
 
 // stages a2-a3 (pair densities + PAW) and the pair weights of rows [a0, a1) of one transition
 template <typename T>
-rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* omega_d, int nw, Block<T>& B) {
+rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* omega_d, int nw, Block<T>& B,
+                       int slot = 0) {
   OrbSet& sk = c->sets[Q.k_of[t]];
   OrbSet& skp = c->sets[Q.kq_of[t]];
   B.sk = &sk;
@@ -456,8 +465,9 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
   rpa_status st;
   if ((st = workspace(c, "pair_d", sizeof(double) * P, &p_d)) != RPA_OK) return st;
   if ((st = workspace(c, "pair_df", sizeof(double) * P, &p_df)) != RPA_OK) return st;
-  if ((st = workspace(c, "pair_w", sizeof(T) * P * nw, &p_w)) != RPA_OK) return st;
-  if ((st = workspace(c, "Nmat", sizeof(c2<T>) * (size_t)P * NG, &p_N)) != RPA_OK) return st;
+  // the weights and pair densities of two blocks may be alive at once (slots)
+  if ((st = workspace(c, slot ? "pair_w1" : "pair_w", sizeof(T) * P * nw, &p_w)) != RPA_OK) return st;
+  if ((st = workspace(c, slot ? "Nmat1" : "Nmat", sizeof(c2<T>) * (size_t)P * NG, &p_N)) != RPA_OK) return st;
   const double pref = c->prm.spin_factor / (c->volume * (double)c->prm.nk_bz);
   {
     StageTimer tm(c, 4, 2);
@@ -599,6 +609,91 @@ rpa_status check_q_ready(rpa_ctx* c, int iq) {
 
 // chi0 of one q-point, enqueued without any host synchronisation (frequencies
 // already on the device); bounded-wait failures land in c->dev_err.
+// Split-bfloat16 modes: every block of occupied rows of every transition,
+// pipelined over two streams.  On the context stream: pair densities of block
+// i, then the rank-k kernel of block i-1; on the second stream: the operand
+// preparation of block i, which runs beside that rank-k kernel (it needs few
+// registers and little shared memory, and is bound by HBM while the rank-k
+// kernel is bound by the tensor cores).  Pair densities, weights and operands
+// alternate between two slots; events order every reuse.  The second stream
+// is forked from and joined back to the context stream, so the sequence can
+// be captured in a CUDA graph.
+rpa_status chi_tc_pipeline(rpa_ctx* c, QPt& Q, const double* omega_d, int nw, double2* chi) {
+  rpa_status st;
+  if (!c->stream2) {
+    CUDA_OK(c, cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_pd[i], cudaEventDisableTiming));
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_prep[i], cudaEventDisableTiming));
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_herk[i], cudaEventDisableTiming));
+    }
+    CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
+  const int terms = c->prm.precision == RPA_BF16X3 ? 3 : 2;
+  struct Pending {
+    int64_t P = 0;
+    int NG = 0;
+    void* scr = nullptr;
+    size_t sb = 0;
+    int slot = 0;
+  };
+  std::vector<std::array<int, 3>> blocks;  // (transition, a0, a1)
+  for (size_t t = 0; t < Q.k_of.size(); ++t) {
+    const int nL = (int)c->sets[Q.k_of[t]].L.size(), nR = (int)c->sets[Q.kq_of[t]].R.size();
+    const int rows = rows_per_block(c, nL, nR, Q.NG, nw);
+    for (int a0 = 0; a0 < nL; a0 += rows) blocks.push_back({(int)t, a0, std::min(nL, a0 + rows)});
+  }
+  CUDA_OK(c, cudaEventRecord(c->ev_fork, c->stream));
+  CUDA_OK(c, cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+  bool herk_done[2] = {false, false};
+  Pending prev;
+  bool have_prev = false;
+  auto run_herk = [&](const Pending& b) -> rpa_status {
+    CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_prep[b.slot], 0));
+    {
+      StageTimer tm(c, 2, 1);
+      CUDA_OK(c, herk_tc_run(b.P, b.NG, nw, terms, (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH],
+                             (int)c->tune[RPA_TUNE_TC_PIPE], chi, b.scr, b.sb, c->dev_err, c->stream));
+    }
+    CUDA_OK(c, cudaEventRecord(c->ev_herk[b.slot], c->stream));
+    herk_done[b.slot] = true;
+    return RPA_OK;
+  };
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    const int slot = (int)(i & 1);
+    Block<float> B;
+    if ((st = pairs_block<float>(c, Q, blocks[i][0], blocks[i][1], blocks[i][2], omega_d, nw, B, slot)) != RPA_OK)
+      return st;
+    if (B.P > 0) {
+      Pending cur;
+      cur.P = B.P;
+      cur.NG = B.NG;
+      cur.slot = slot;
+      cur.sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
+      if (cur.sb && (st = workspace(c, slot ? "herk_tc1" : "herk_tc", cur.sb, &cur.scr)) != RPA_OK) return st;
+      CUDA_OK(c, cudaEventRecord(c->ev_pd[slot], c->stream));
+      CUDA_OK(c, cudaStreamWaitEvent(c->stream2, c->ev_pd[slot], 0));
+      // the slot's operands were last read by the rank-k kernel two blocks back
+      if (herk_done[slot]) CUDA_OK(c, cudaStreamWaitEvent(c->stream2, c->ev_herk[slot], 0));
+      {
+        StageTimer tm(c, 5, 2, c->stream2);
+        CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms, cur.scr, cur.sb,
+                                   c->stream2));
+      }
+      CUDA_OK(c, cudaEventRecord(c->ev_prep[slot], c->stream2));
+      if (have_prev && (st = run_herk(prev)) != RPA_OK) return st;
+      prev = cur;
+      have_prev = true;
+    }
+  }
+  if (have_prev && (st = run_herk(prev)) != RPA_OK) return st;
+  // join the second stream back into the context stream
+  CUDA_OK(c, cudaEventRecord(c->ev_join, c->stream2));
+  CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  return RPA_OK;
+}
+
 rpa_status build_chi_async(rpa_ctx* c, int iq, int nw, const double* p_om, double2** chi_out) {
   rpa_status st = check_q_ready(c, iq);
   if (st != RPA_OK) return st;
@@ -611,12 +706,16 @@ rpa_status build_chi_async(rpa_ctx* c, int iq, int nw, const double* p_om, doubl
     if ((st = build_grids(c, c->sets[Q.k_of[t]])) != RPA_OK) return st;
     if ((st = build_grids(c, c->sets[Q.kq_of[t]])) != RPA_OK) return st;
   }
-  for (size_t t = 0; t < Q.k_of.size(); ++t) {
-    if (c->prm.precision == RPA_FP64)
-      st = chi_block<double>(c, Q, (int)t, p_om, nw, (double2*)p_chi);
-    else
-      st = chi_block<float>(c, Q, (int)t, p_om, nw, (double2*)p_chi);
-    if (st != RPA_OK) return st;
+  if (c->prm.precision == RPA_BF16X2 || c->prm.precision == RPA_BF16X3) {
+    if ((st = chi_tc_pipeline(c, Q, p_om, nw, (double2*)p_chi)) != RPA_OK) return st;
+  } else {
+    for (size_t t = 0; t < Q.k_of.size(); ++t) {
+      if (c->prm.precision == RPA_FP64)
+        st = chi_block<double>(c, Q, (int)t, p_om, nw, (double2*)p_chi);
+      else
+        st = chi_block<float>(c, Q, (int)t, p_om, nw, (double2*)p_chi);
+      if (st != RPA_OK) return st;
+    }
   }
   *chi_out = (double2*)p_chi;
   return RPA_OK;
@@ -1032,6 +1131,17 @@ void rpa_destroy(rpa_ctx* c) {
   }
   for (auto& kv : c->ws) dev_free(kv.second.p);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->stream2) {
+    cudaStreamSynchronize(c->stream2);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(c->ev_pd[i]);
+      cudaEventDestroy(c->ev_prep[i]);
+      cudaEventDestroy(c->ev_herk[i]);
+    }
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
+    cudaStreamDestroy(c->stream2);
+  }
   dev_free(c->dev_err);
   dev_free(c->omega_d);
   if (c->own_stream) cudaStreamDestroy(c->stream);
