@@ -12,7 +12,12 @@
  *     (Table 1 steps 5-6), plus the PAW augmentation of Eq. 6 (steps 7-9);
  *   - E_c of Eqs. 1-2: sum over q of w_q, over Gauss-Legendre frequencies of
  *     W_j / (2 pi) [ln det(1 - v^1/2 chi0 v^1/2) + tr(v^1/2 chi0 v^1/2)]
- *     (Table 1 step 13).
+ *     (Table 1 step 13);
+ *   - the optical limit q -> 0 of Eqs. 12-14 (rpa_set_optical), the IBZ -> BZ
+ *     symmetry of Eq. 9 (rpa_set_orbitals_sym), the gradient of E_c
+ *     (rpa_energy_backward) and the inverse dielectric matrix
+ *     (rpa_epsilon_inv); many independent q-points or cells can be batched
+ *     into one CUDA graph (rpa_graph_*).
  *
  * Conventions (all functions):
  *   - Complex arrays are interleaved (re, im) doubles.
@@ -283,9 +288,11 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  * RPA_TUNE_TC_PIPE     tensor-core pipeline shape: 0 (default) 64-element K
  *                      stages x 2 in shared memory; 1: 32-element stages x 4.
  * RPA_TUNE_LOGDET      arithmetic of the Cholesky trailing updates in the
- *                      RPA_FP32 and RPA_BF16X2 modes: 1 (default) float-float
- *                      (pairs of FP32, about 44 significant bits; the matrix
- *                      stays FP64), 0: FP64.  RPA_FP64 always uses FP64.
+ *                      RPA_FP32, RPA_BF16X2 and RPA_BF16X3 modes: 1 (default)
+ *                      float-float (the part of the matrix still being
+ *                      updated held as pairs of FP32, about 44 significant
+ *                      bits; finished columns and pivots FP64), 0: FP64.
+ *                      RPA_FP64 always uses FP64.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
