@@ -14,7 +14,7 @@
 
 namespace rpa {
 
-constexpr int OT = 64;  // output tile edge (pairs)
+constexpr int OT = 64;  // output tile edge along the empty bands (pairs)
 constexpr int OK = 16;  // K chunk
 
 // Y[b][i] = sum_j Qn[i][j] P[R[b]][j]
@@ -33,9 +33,13 @@ __global__ void optical_paw_y_kernel(const double2* __restrict__ P, int KP, cons
 }
 
 // Partial D[a][b] = sum_k A_k(n_a) B_k(m_b) over this CTA's slice of K = npw
-// (+ KP), 4 x 4 outputs a thread, into Dp[split][nL][nR].  The K dimension is
-// split across CTAs because nL x nR is small (a few dozen tiles).
-template <typename T>
+// (+ KP), RT x 4 outputs a thread on a (16 RT) x 64 tile, into
+// Dp[split][nL][nR].  The row tile follows nL (the occupied bands of a block,
+// often 16 or fewer) so that no FP64 work goes to padding rows; the K
+// dimension is split across CTAs because the tile count is small.  Global
+// reads run along K (16 consecutive coefficients of one band per 16 threads);
+// the shared tiles are padded by one element against bank conflicts.
+template <typename T, int RT>
 __global__ void __launch_bounds__(256) optical_dipole_kernel(const double2* __restrict__ C, int npw,
                                                              const double* __restrict__ s,
                                                              const double2* __restrict__ P, int KP,
@@ -43,54 +47,58 @@ __global__ void __launch_bounds__(256) optical_dipole_kernel(const double2* __re
                                                              const int* __restrict__ L, int nL,
                                                              const int* __restrict__ R, int nR, int kslice,
                                                              double2* __restrict__ Dp) {
-  __shared__ double2 As[OK][OT];
-  __shared__ double2 Bs[OK][OT];
-  const int a0 = blockIdx.y * OT, b0 = blockIdx.x * OT;
+  constexpr int TL = 16 * RT;
+  __shared__ double2 As[OK][TL + 1];
+  __shared__ double2 Bs[OK][OT + 1];
+  const int a0 = blockIdx.y * TL, b0 = blockIdx.x * OT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double2 acc[4][4];
+  double2 acc[RT][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RT; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
   const int K = npw + (P ? KP : 0);
   const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
+  const int kk = threadIdx.x % OK, rr = threadIdx.x / OK;  // 16 rows x 16 k per pass
   for (int k0 = kbeg; k0 < kend; k0 += OK) {
+    const int k = k0 + kk;
 #pragma unroll
-    for (int q = 0; q < (OK * OT) / 256; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int kk = e / OT, r = e % OT;
-      const int k = k0 + kk;
-      double2 av = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
-      if (k < kend) {
-        if (a0 + r < nL) {
-          const int n = L[a0 + r];
-          if (k < npw) {
-            // i s(Q) conj(C_n(Q))
-            const double2 cn = C[(int64_t)n * npw + k];
-            av = make_double2(s[k] * cn.y, s[k] * cn.x);
-          } else {
-            const double2 pn = P[(int64_t)n * KP + (k - npw)];
-            av = make_double2(pn.x, -pn.y);
-          }
-        }
-        if (b0 + r < nR) {
-          const int m = R[b0 + r];
-          bv = k < npw ? C[(int64_t)m * npw + k] : Y[(int64_t)(b0 + r) * KP + (k - npw)];
+    for (int q = 0; q < RT; ++q) {
+      const int r = rr + 16 * q;
+      double2 av = make_double2(0.0, 0.0);
+      if (k < kend && a0 + r < nL) {
+        const int n = L[a0 + r];
+        if (k < npw) {
+          // i s(Q) conj(C_n(Q))
+          const double2 cn = C[(int64_t)n * npw + k];
+          av = make_double2(s[k] * cn.y, s[k] * cn.x);
+        } else {
+          const double2 pn = P[(int64_t)n * KP + (k - npw)];
+          av = make_double2(pn.x, -pn.y);
         }
       }
       As[kk][r] = av;
+    }
+#pragma unroll
+    for (int q = 0; q < OT / 16; ++q) {
+      const int r = rr + 16 * q;
+      double2 bv = make_double2(0.0, 0.0);
+      if (k < kend && b0 + r < nR) {
+        const int m = R[b0 + r];
+        bv = k < npw ? C[(int64_t)m * npw + k] : Y[(int64_t)(b0 + r) * KP + (k - npw)];
+      }
       Bs[kk][r] = bv;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < OK; ++kk) {
-      double2 av[4], bv[4];
+    for (int j = 0; j < OK; ++j) {
+      double2 av[RT], bv[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < RT; ++r) av[r] = As[j][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[j][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RT; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) cmac<double>(acc[r][c], av[r], bv[c]);
     }
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(256) optical_dipole_kernel(const double2* __re
   }
   double2* Dz = Dp + (int64_t)blockIdx.z * nL * nR;
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RT; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int a = a0 + ty + 16 * r, b = b0 + tx + 16 * c;
@@ -126,11 +134,16 @@ __global__ void optical_head_kernel(const double2* __restrict__ Dp, int nsplit, 
   }
 }
 
+static int dipole_rows(int nL) { return nL <= 16 ? 16 : nL <= 32 ? 32 : 64; }
+
+static int dipole_nsplit(int nL, int nR, int K) {
+  const int TL = dipole_rows(nL);
+  const int tiles = ((nR + OT - 1) / OT) * ((nL + TL - 1) / TL);
+  return std::max(1, std::min((K + 255) / 256, (2 * 152 + tiles - 1) / tiles));
+}
+
 int64_t optical_scratch_elems(int nL, int nR, int npw, int KP) {
-  const int tiles = ((nR + OT - 1) / OT) * ((nL + OT - 1) / OT);
-  const int K = npw + KP;
-  const int nsplit = std::max(1, std::min((K + 255) / 256, (2 * 152 + tiles - 1) / tiles));
-  return (int64_t)nR * KP + (int64_t)nsplit * nL * nR;
+  return (int64_t)nR * KP + (int64_t)dipole_nsplit(nL, nR, npw + KP) * nL * nR;
 }
 
 template <typename T>
@@ -147,12 +160,17 @@ cudaError_t launch_optical_head(const double2* C, int npw, const double* s, cons
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     optical_paw_y_kernel<<<blocks, 256, 0, st>>>(P, KP, Qn, R, nR, Y);
   }
-  const int tiles = ((nR + OT - 1) / OT) * ((nL + OT - 1) / OT);
   const int K = npw + kp;
-  const int nsplit = std::max(1, std::min((K + 255) / 256, (2 * 152 + tiles - 1) / tiles));
+  const int TL = dipole_rows(nL);
+  const int nsplit = dipole_nsplit(nL, nR, K);
   const int kslice = ((K + nsplit - 1) / nsplit + OK - 1) / OK * OK;
-  dim3 grid((nR + OT - 1) / OT, (nL + OT - 1) / OT, nsplit);
-  optical_dipole_kernel<T><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, kslice, Dp);
+  dim3 grid((nR + OT - 1) / OT, (nL + TL - 1) / TL, nsplit);
+  if (TL == 16)
+    optical_dipole_kernel<T, 1><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, kslice, Dp);
+  else if (TL == 32)
+    optical_dipole_kernel<T, 2><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, kslice, Dp);
+  else
+    optical_dipole_kernel<T, 4><<<grid, 256, 0, st>>>(C, npw, s, P, KP, Y, L, nL, R, nR, kslice, Dp);
   const int64_t total = (int64_t)nL * nR;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
   optical_head_kernel<T><<<blocks, 256, 0, st>>>(Dp, nsplit, L, nL, R, nR, eps, NG, ig0, N);
