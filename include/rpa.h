@@ -288,11 +288,15 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  * RPA_TUNE_TC_PIPE     tensor-core pipeline shape: 0 (default) 64-element K
  *                      stages x 2 in shared memory; 1: 32-element stages x 4.
  * RPA_TUNE_LOGDET      arithmetic of the Cholesky trailing updates in the
- *                      RPA_FP32, RPA_BF16X2 and RPA_BF16X3 modes: 1 (default)
+ *                      RPA_FP32, RPA_BF16X2 and RPA_BF16X3 modes: 2 (default)
  *                      float-float (the part of the matrix still being
  *                      updated held as pairs of FP32, about 44 significant
- *                      bits; finished columns and pivots FP64), 0: FP64.
- *                      RPA_FP64 always uses FP64.
+ *                      bits; finished columns and pivots FP64) with a
+ *                      look-ahead of one panel on a second stream (the next
+ *                      panel is factorised beside the rest of the current
+ *                      update); 1: the same arithmetic on one stream; 0: FP64.
+ *                      All three give the same result to rounding.
+ *                      RPA_FP64 always uses FP64 on one stream.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,

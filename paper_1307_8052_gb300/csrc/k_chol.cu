@@ -336,19 +336,21 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double2* __restrict__ 
 // each): the panel comes from Lp and the trailing matrix is float-float, so
 // the kernel issues no FP64 instruction.  The accumulators take 167 registers
 // a thread; small CTAs let six of them share an SM so that twelve warps hide
-// the latency of the dependent two-sum steps.
+// the latency of the dependent two-sum steps.  The tiles cover the lower
+// triangle of the square from row/column s0 to NG, or with strip set only its
+// first 32-column strip (which is the next panel, as UTF == CB).
 constexpr int UTF = 32;
+static_assert(UTF == CB, "the look-ahead strip of the trailing update is one panel wide");
 
-__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b,
-                                                               const float4* __restrict__ Lp) {
+__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b, int s0,
+                                                               int strip, const float4* __restrict__ Lp) {
   __shared__ float4 Li[CB][UTF];
   __shared__ float4 Lj[CB][UTF];
   const int w = blockIdx.y;
   float4* Aw = reinterpret_cast<float4*>(A) + (int64_t)w * NG * NG;
   const float4* Pw = Lp + (int64_t)w * NG * CB;
-  int ti, tj;
-  tri_tile(blockIdx.x, ti, tj);
-  const int s0 = k0 + b;
+  int ti = blockIdx.x, tj = 0;
+  if (!strip) tri_tile(blockIdx.x, ti, tj);
   const int r0 = s0 + ti * UTF, c0 = s0 + tj * UTF;
   for (int e = threadIdx.x; e < b * UTF; e += blockDim.x) {
     const int rr = e / b, l = e % b;
@@ -411,13 +413,94 @@ static inline int gridc(int64_t n) {
 
 // work layout (complex slots of 16 bytes): the matrix [nw][NG][NG], the
 // inverses of the diagonal blocks in FP64 and in float-float [nw][CB][CB]
-// each, and the float-float panel [nw][NG][CB]
+// each, and two float-float panels [nw][NG][CB] (alternate panels, so that the
+// look-ahead can solve panel k+1 while the update of panel k still reads its own)
 int64_t logdet_work_elems(int nw, int NG) {
-  return (int64_t)nw * NG * NG + 2 * (int64_t)nw * CB * CB + (int64_t)nw * NG * CB;
+  return (int64_t)nw * NG * NG + 2 * (int64_t)nw * CB * CB + 2 * (int64_t)nw * NG * CB;
+}
+
+// Launch on stream s with the given scheduling priority (lower is more urgent),
+// so that the short kernels of the look-ahead chain take SMs as soon as
+// trailing-update CTAs retire; the attribute also holds in a captured graph.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, int prio,
+                               Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = prio;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Float-float factorisation with a look-ahead of one panel.  The update of
+// panel k is split into its first column strip (panel k+1, on s, high
+// priority) and the rest (on the second stream).  Panel k+1 is factorised and
+// solved on s while the rest of the update of panel k runs beside it; the
+// strip update of panel k+1 waits for that rest, which also wrote the strip.
+// Events: ev_t (panel solved, s -> s2) and ev_u (rest updated, s2 -> s); s
+// waits for the last rest at the end, so the sequence can be captured.
+static cudaError_t run_logdet_ff_lookahead(int nw, int NG, double2* work, double* logdet, int* flag,
+                                           const LogdetStreams& la, cudaStream_t s, int64_t* nl) {
+  cudaError_t e;
+  int least = 0, greatest = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return e;
+  double2* Linv = work + (int64_t)nw * NG * NG;
+  float4* Linv_ff = reinterpret_cast<float4*>(Linv + (int64_t)nw * CB * CB);
+  float4* Lp0 = Linv_ff + (int64_t)nw * CB * CB;
+  bool rest_pending = false;  // a rest update has been issued on s2 and not yet waited for by s
+  for (int k0 = 0, k = 0; k0 < NG; k0 += CB, ++k) {
+    const int b = (NG - k0) < CB ? (NG - k0) : CB;
+    const int rest = NG - k0 - b;
+    float4* Lp = Lp0 + (int64_t)(k & 1) * nw * NG * CB;
+    if ((e = launch_prio(chol_diag_kernel<true>, dim3(nw), dim3(256), s, greatest, work, NG, k0, b, logdet, flag,
+                         Linv, Linv_ff)) != cudaSuccess)
+      return e;
+    ++*nl;
+    if (rest == 0) break;
+    const dim3 tg((rest + TROWS - 1) / TROWS, nw);
+    if ((e = launch_prio(chol_trsm_kernel<true>, tg, dim3(256), s, greatest, work, NG, k0, b,
+                         (const double2*)Linv, (const float4*)Linv_ff, Lp)) != cudaSuccess)
+      return e;
+    ++*nl;
+    const int nt = (rest + UTF - 1) / UTF;
+    const int s0 = k0 + b;
+    if (nt > 1) {
+      if ((e = cudaEventRecord(la.ev_t, s)) != cudaSuccess) return e;
+    }
+    // the strip (next panel) was last written by the rest update of panel k-1
+    if (rest_pending) {
+      if ((e = cudaStreamWaitEvent(s, la.ev_u, 0)) != cudaSuccess) return e;
+      rest_pending = false;
+    }
+    if ((e = launch_prio(chol_update_ff_kernel, dim3(nt, nw), dim3(64), s, greatest, work, NG, k0, b, s0, 1,
+                         (const float4*)Lp)) != cudaSuccess)
+      return e;
+    ++*nl;
+    if (nt > 1) {
+      const int nr = nt - 1;
+      if ((e = cudaStreamWaitEvent(la.s2, la.ev_t, 0)) != cudaSuccess) return e;
+      chol_update_ff_kernel<<<dim3(nr * (nr + 1) / 2, nw), 64, 0, la.s2>>>(work, NG, k0, b, s0 + UTF, 0, Lp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(la.ev_u, la.s2)) != cudaSuccess) return e;
+      rest_pending = true;
+      ++*nl;
+    }
+  }
+  if (rest_pending) {
+    if ((e = cudaStreamWaitEvent(s, la.ev_u, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work, double* logdet,
-                       double* trace, int* flag, bool ff_update, cudaStream_t s, int64_t* launches) {
+                       double* trace, int* flag, bool ff_update, cudaStream_t s, int64_t* launches,
+                       const LogdetStreams* la) {
   cudaError_t e;
   int64_t nl = 0;
   const int upd_smem = 2 * CB * UT * (int)sizeof(double2);
@@ -437,6 +520,11 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
   trace_kernel<<<nw, 256, 0, s>>>(chi, v, NG, trace);
   nl += 2;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ff_update && la) {
+    e = run_logdet_ff_lookahead(nw, NG, work, logdet, flag, *la, s, &nl);
+    if (launches) *launches += nl;
+    return e;
+  }
   for (int k0 = 0; k0 < NG; k0 += CB) {
     const int b = (NG - k0) < CB ? (NG - k0) : CB;
     const int rest = NG - k0 - b;
@@ -446,7 +534,7 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
       if (rest > 0) {
         chol_trsm_kernel<true><<<tg, 256, 0, s>>>(work, NG, k0, b, Linv, Linv_ff, Lp);
         const int nt = (rest + UTF - 1) / UTF;
-        chol_update_ff_kernel<<<dim3(nt * (nt + 1) / 2, nw), 64, 0, s>>>(work, NG, k0, b, Lp);
+        chol_update_ff_kernel<<<dim3(nt * (nt + 1) / 2, nw), 64, 0, s>>>(work, NG, k0, b, k0 + b, 0, Lp);
       }
     } else {
       chol_diag_kernel<false><<<nw, 256, 0, s>>>(work, NG, k0, b, logdet, flag, Linv, nullptr);

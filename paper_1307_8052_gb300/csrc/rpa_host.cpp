@@ -130,6 +130,8 @@ struct rpa_ctx {
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_pd[2] = {nullptr, nullptr}, ev_prep[2] = {nullptr, nullptr}, ev_herk[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // second stream and events of the look-ahead Cholesky (float-float log-det)
+  LogdetStreams ld{nullptr, nullptr, nullptr};
   double B[9] = {0};  // reciprocal rows
   double volume = 0.0;
   std::string err;
@@ -143,7 +145,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 1};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -291,7 +293,19 @@ void prof_end(rpa_ctx* c) {
 }
 
 // float-float trailing updates of the log-det in the mixed-precision modes
-bool ff_logdet(const rpa_ctx* c) { return c->prm.precision != RPA_FP64 && c->tune[RPA_TUNE_LOGDET] == 1; }
+bool ff_logdet(const rpa_ctx* c) { return c->prm.precision != RPA_FP64 && c->tune[RPA_TUNE_LOGDET] >= 1; }
+
+// The look-ahead streams of the float-float log-det (created on first use), or
+// nullptr in *la when the factorisation runs on one stream.
+rpa_status logdet_streams(rpa_ctx* c, const LogdetStreams** la) {
+  *la = nullptr;
+  if (!ff_logdet(c) || c->tune[RPA_TUNE_LOGDET] != 2) return RPA_OK;
+  if (!c->ld.ev_t) CUDA_OK(c, cudaEventCreateWithFlags(&c->ld.ev_t, cudaEventDisableTiming));
+  if (!c->ld.ev_u) CUDA_OK(c, cudaEventCreateWithFlags(&c->ld.ev_u, cudaEventDisableTiming));
+  if (!c->ld.s2) CUDA_OK(c, cudaStreamCreateWithFlags(&c->ld.s2, cudaStreamNonBlocking));
+  *la = &c->ld;
+  return RPA_OK;
+}
 
 // ---- stage a1: every band of a set onto the real-space grid (Eq. 8, Table 1 step 3)
 template <typename T>
@@ -737,9 +751,11 @@ rpa_status energy_enqueue(rpa_ctx* c, int nq, const int* iqs, int nw, const doub
     void* p_work;
     if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw, Q.NG), &p_work)) != RPA_OK) return st;
     int64_t nl = 0;
+    const LogdetStreams* la;
+    if ((st = logdet_streams(c, &la)) != RPA_OK) return st;
     StageTimer tm(c, 3, 0);
     CUDA_OK(c, run_logdet(chi, Q.v_d, nw, Q.NG, (double2*)p_work, (double*)p_ld + (size_t)i * nw,
-                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, ff_logdet(c), c->stream, &nl));
+                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, ff_logdet(c), c->stream, &nl, la));
     tm.add_launches(nl);
   }
   c->enq_iqs.assign(iqs, iqs + nq);
@@ -978,9 +994,11 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     if ((st = workspace(c, "cw", sizeof(double) * nw, &p_cw)) != RPA_OK) return st;
     int64_t nl = 0;
     {
+      const LogdetStreams* la;
+      if ((st = logdet_streams(c, &la)) != RPA_OK) return st;
       StageTimer tm(c, 3, 0);
       CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
-                            ff_logdet(c), c->stream, &nl));
+                            ff_logdet(c), c->stream, &nl, la));
       tm.add_launches(nl);
     }
     int flag = 0;
@@ -1142,6 +1160,12 @@ void rpa_destroy(rpa_ctx* c) {
     cudaEventDestroy(c->ev_join);
     cudaStreamDestroy(c->stream2);
   }
+  if (c->ld.s2) {
+    cudaStreamSynchronize(c->ld.s2);
+    cudaStreamDestroy(c->ld.s2);
+  }
+  if (c->ld.ev_t) cudaEventDestroy(c->ld.ev_t);
+  if (c->ld.ev_u) cudaEventDestroy(c->ld.ev_u);
   dev_free(c->dev_err);
   dev_free(c->omega_d);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1680,9 +1704,11 @@ rpa_status rpa_epsilon_inv(rpa_ctx* c, int32_t iq, int32_t nw, const double* ome
   CUDA_OK(c, cudaMemsetAsync(p_cw, 0, sizeof(double) * nw, c->stream));
   {
     int64_t nl = 0;
+    const LogdetStreams* la;
+    if ((st = logdet_streams(c, &la)) != RPA_OK) return st;
     StageTimer tm(c, 3, 0);
     CUDA_OK(c, run_logdet(chi, Q.v_d, nw, NG, (double2*)p_work, (double*)p_ld, (double*)p_tr, (int*)p_flag,
-                          ff_logdet(c), c->stream, &nl));
+                          ff_logdet(c), c->stream, &nl, la));
     // (1 - M)^-1 = L^-H L^-1 from the factor (the Gamma output is not needed)
     CUDA_OK(c, run_gamma((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y, (double2*)p_W,
                          nullptr, nullptr, c->stream, &nl));
@@ -1908,7 +1934,7 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "tensor-core pipeline shape must be 0 or 1");
       break;
     case RPA_TUNE_LOGDET:
-      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "log-det update arithmetic must be 0 or 1");
+      if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "log-det update choice must be 0, 1 or 2");
       break;
     case RPA_TUNE_OPERAND_MB:
       if (value < 16 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "operand budget %lld MB out of range", (long long)value);

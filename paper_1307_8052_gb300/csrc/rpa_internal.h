@@ -123,11 +123,18 @@ cudaError_t launch_rotate_P(const double2* P, int nb, int KP, int natoms, const 
 // inverses of its diagonal blocks.
 int64_t logdet_work_elems(int nw, int NG);
 
+// Second stream and events of the look-ahead factorisation (float-float mode).
+struct LogdetStreams {
+  cudaStream_t s2;
+  cudaEvent_t ev_t, ev_u;
+};
+
 // Log-det of 1 - v^1/2 chi v^1/2 by blocked Cholesky in FP64, batched over w:
 // per-w ln det in logdet, tr(v^1/2 chi v^1/2) in trace, pivot failure in flag.
-// ff_update evaluates the trailing updates in float-float arithmetic.
+// ff_update evaluates the trailing updates in float-float arithmetic; with la
+// it also factorises the next panel beside the rest of the current update.
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work,
                        double* logdet, double* trace, int* flag, bool ff_update, cudaStream_t s,
-                       int64_t* launches);
+                       int64_t* launches, const LogdetStreams* la = nullptr);
 
 }  // namespace rpa

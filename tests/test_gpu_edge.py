@@ -1,7 +1,7 @@
 """Edge cases through the C ABI against the oracle, in every mode: a
 transition without pairs, degenerate band energies across the Fermi level,
-a one-vector response sphere (far below one tensor-core tile), and a single
-frequency."""
+a one-vector response sphere (far below one tensor-core tile), a single
+frequency, and response spheres around the Cholesky panel width."""
 import dataclasses
 
 import numpy as np
@@ -92,3 +92,29 @@ def test_tiny_sphere_and_one_frequency(precision):
     assert chi.shape == (1, 2, 2)
     assert np.abs(chi - ref).max() <= TOL[precision] * np.abs(ref).max()
     assert np.abs(t[0] - tr).max() <= max(TOL[precision], 1e-10) * np.abs(tr).max()
+
+
+@pytest.mark.parametrize("ecut_chi", [2.0, 2.4, 3.3, 5.5])
+def test_logdet_lookahead_at_panel_boundaries(ecut_chi):
+    """Response spheres around the 32-wide Cholesky panels (NG 29/32: one
+    panel; 35/40: a panel and a ragged strip; 65/64: a strip with and without
+    a rest update; 141/130: several rest updates, ragged last tile): the
+    float-float factorisation with the look-ahead equals the one-stream
+    factorisation bit for bit, and both match FP64 eigenvalues of the GPU's own
+    chi0."""
+    p = syn.small_problem(config_tag=84, ecut_chi=ecut_chi)
+    om, W = o.frequency_grid(p.nw)
+    ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, "bf16x2")
+    try:
+        b.load_problem(ctx, p, paw_Q=lambda i, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[i].q_red, gm))
+        for iq, qp in enumerate(p.qpoints):
+            chi = b.rpa_chi0(ctx, iq, om)
+            want = o.ec_terms(chi, o.coulomb(p.cell, qp.q_red, b.rpa_gvectors(ctx, iq)))
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_LOGDET, 2)
+            _, t2 = b.rpa_energy(ctx, [iq], [1.0], om, W)
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_LOGDET, 1)
+            _, t1 = b.rpa_energy(ctx, [iq], [1.0], om, W)
+            assert np.array_equal(t1, t2)
+            assert np.abs(t2[0] - want).max() <= 1e-10 * np.abs(want).max()
+    finally:
+        b.rpa_destroy(ctx)

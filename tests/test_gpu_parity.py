@@ -157,17 +157,22 @@ def test_config1_geometry_two_transitions(precision):
         assert _rel(chi, ref) < TOL[precision]["chi"]
         # the log-det of the GPU's own chi0 (NG ~ 1200: 38 panels, ragged last
         # tile) against FP64 eigenvalues of the same matrix; in the FP32 and
-        # BF16X2 modes with both trailing-update arithmetics
+        # BF16X2 modes with every trailing-update choice: float-float with the
+        # look-ahead (default), float-float on one stream (the same tiles in
+        # the same order, so bit-identical), FP64
         v = o.coulomb(p.cell, qp.q_red, b.rpa_gvectors(ctx, 0))
         want = o.ec_terms(chi, v)
         _, t = b.rpa_energy(ctx, [0], [1.0], om, W)
         assert np.abs(t[0] - want).max() / np.abs(want).max() < (1e-11 if precision == "fp64" else 1e-10)
         if precision != "fp64":
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_LOGDET, 1)
+            _, t1 = b.rpa_energy(ctx, [0], [1.0], om, W)
+            assert np.array_equal(t1, t)
             b.rpa_set_tuning(ctx, b.RPA_TUNE_LOGDET, 0)
             _, t64 = b.rpa_energy(ctx, [0], [1.0], om, W)
             assert np.abs(t64[0] - want).max() / np.abs(want).max() < 1e-11
             with pytest.raises(b.RpaError):
-                b.rpa_set_tuning(ctx, b.RPA_TUNE_LOGDET, 2)
+                b.rpa_set_tuning(ctx, b.RPA_TUNE_LOGDET, 3)
     finally:
         b.rpa_destroy(ctx)
 
