@@ -257,6 +257,8 @@ def run_ours(args):
                              paw_Q=lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))
         for iq in optical_q:
             b.rpa_set_optical(ctx, iq, OPTICAL_QDIR, p.paw.nproj, syn.paw_Qnabla(p.paw, p.config))
+        if args.paw_tc:
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_PAW_TC, 1)
         return ctx, ngs
 
     ctx, ngs = make_ctx(args.precision)
@@ -375,6 +377,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_SLAB if args.config == "slab" else WORKLOAD, "precision": args.precision,
                    "q_points": nq, "NG": ngs,
                    "optical_limit": (f"q=0 head and wings along {OPTICAL_QDIR}" if optical_q else None),
+                   "paw_product": "tensor cores" if args.paw_tc else "CUDA cores (FP32)",
                    "pairs_per_q": Kq, "nw": p.nw, "l2": "inputs larger than L2 (grids >= 1.4 GB, rank-k operands >= 3 GB per block)",
                    "parallelism": f"replicas x{world}"},
         "s_per_q": t_step / nq,
@@ -558,6 +561,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--config", choices=["bulk", "slab", "batched", "backward"], default="bulk")
     ap.add_argument("--slab-q", type=int, default=1, help="q-points per step of the slab workload")
+    ap.add_argument("--paw-tc", action="store_true",
+                    help="PAW product on the tensor cores (split modes; faster for many projectors, larger E_c error)")
     ap.add_argument("--instances", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":

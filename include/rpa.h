@@ -297,6 +297,16 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      update); 1: the same arithmetic on one stream; 0: FP64.
  *                      All three give the same result to rounding.
  *                      RPA_FP64 always uses FP64 on one stream.
+ * RPA_TUNE_PAW_TC      the PAW product of Eq. 6 (sum_kp P_m,kp R_n(kp, G), R
+ *                      the factor of each occupied band) in the RPA_BF16X2
+ *                      and RPA_BF16X3 modes: 0 (default) on the CUDA cores in
+ *                      FP32, 1 on the tensor cores with the mode's bfloat16
+ *                      split.  1 is faster for many projectors (slab
+ *                      workload, 304 projectors: 6.43 -> 6.08 s per q) but
+ *                      adds the truncation bias of the tensor cores'
+ *                      accumulation to the PAW part of every pair density
+ *                      (bulk workload, 39 projectors: E_c within 6.7e-7 of
+ *                      FP64 instead of 2.6e-7).  Other modes ignore it.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -306,7 +316,8 @@ typedef enum {
   RPA_TUNE_OPERAND_MB = 4,
   RPA_TUNE_TC_PIPE = 5,
   RPA_TUNE_LOGDET = 6,
-  RPA_TUNE_COUNT = 7
+  RPA_TUNE_PAW_TC = 7,
+  RPA_TUNE_COUNT = 8
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

@@ -172,12 +172,18 @@ struct Maps {
 // (Eq. 17 transposed).  A holds the pair densities (rows p, shared by all w),
 // X / Z the per-frequency Gam (rows w * NGpad + g); K runs over w and k, and
 // the weight of row p is applied to every fold as it leaves tensor memory.
+// Without weights the variant is a plain batched product
+// out_y[p][g] (+)= sum_k A[p][k] conj(B_y[g][k]) over blockIdx.y = y (the PAW
+// term of Eq. 6: one batch per occupied band, B_y = conj R_y).
 struct GemmArgs {
   int64_t P;          // rows (pairs)
   int nkw;            // K stages per frequency
   int ngt;            // column tiles (NGpad / BN)
-  const float* wgt;   // [nw][P]
-  float2* out;        // [P][NG]
+  const float* wgt;   // [nw][P], or null: weight 1
+  float2* out;        // [P][NG] per batch
+  int nwb;            // frequencies per batch: B rows (y * nwb + w) * NGpad + g
+  int accumulate;     // add to out instead of writing it
+  int64_t out_batch;  // elements between the outputs of consecutive batches
 };
 
 template <int TERMS, int BK, int STAGES, bool GEMM>
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.y;
+  const int w = blockIdx.y;  // HERK: frequency; GEMM: batch
   int ti, tj;
   if constexpr (GEMM) {
     ti = blockIdx.x / ga.ngt;  // row tile of pairs
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int wk = GEMM ? kb / ga.nkw : 0;
         const int k = GEMM ? (kb - wk * ga.nkw) * BK : kb * BK;
         const int arow = GEMM ? i0 : w * NGpad + i0;
-        const int brow = GEMM ? wk * NGpad + j0 : j0;
+        const int brow = GEMM ? (w * ga.nwb + wk) * NGpad + j0 : j0;
 #pragma unroll
         for (int t = 0; t < TERMS; ++t) tma_load_2d(st + t * TILE_BYTES, &maps.a[t], &full[s], k, arow);
 #pragma unroll
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int wf = (f * fold) / ga.nkw;  // folds never straddle frequencies (fold divides nkw)
         if (wf != wcur) {
           wcur = wf;
-          wrow = gi < ga.P ? 2.f * ga.wgt[(int64_t)wf * ga.P + gi] : 0.f;
+          wrow = gi >= ga.P ? 0.f : ga.wgt ? 2.f * ga.wgt[(int64_t)wf * ga.P + gi] : 1.f;
         }
         sc = wrow;
       }
@@ -398,10 +404,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if ((f + 1) % flush == 0) RPA_TC_FLUSH();
     }
     if constexpr (GEMM) {
-      float2* orow = ga.out + (int64_t)gi * NG + j0 + cbase;
+      float2* orow = ga.out + (int64_t)w * ga.out_batch + (int64_t)gi * NG + j0 + cbase;
 #pragma unroll
       for (int c = 0; c < 32; ++c)
-        if (c < ncol) orow[c] = make_float2(sre[c], sim[c]);
+        if (c < ncol) {
+          float2 o = make_float2(sre[c], sim[c]);
+          if (ga.accumulate) {
+            const float2 v = orow[c];
+            o.x += v.x;
+            o.y += v.y;
+          }
+          orow[c] = o;
+        }
     } else {
       RPA_TC_FLUSH();
     }
@@ -508,6 +522,50 @@ __global__ void __launch_bounds__(256) prep_a_kernel(const float2* __restrict__ 
         A[o + term_stride] = __halves2bfloat162(rm, im);
         A[o + 2 * term_stride] = __halves2bfloat162(rl, il);
       }
+    }
+  }
+}
+
+// B operand of the PAW product from R[y][kp][g] (one batch y per occupied
+// band): with b = conj R, X[t][y NGpad + g][2 kp + c] = split(Re b, Im b) and
+// Z = split(-Im b, Re b); rows to NGpad and K to KN = 2 * round32(KP), zero
+// padding (transpose through shared memory).
+template <int TERMS>
+__global__ void __launch_bounds__(256) prep_r_kernel(const float2* __restrict__ R, int KP, int NG, int NGpad,
+                                                     int64_t KN, __nv_bfloat162* __restrict__ X,
+                                                     __nv_bfloat162* __restrict__ Z, int64_t term_stride) {
+  __shared__ float2 t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int y = blockIdx.z;
+  const float2* Ry = R + (int64_t)y * KP * NG;
+  const int k0 = blockIdx.y * 32, g0 = blockIdx.x * 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, g = g0 + tx;
+    t[r][tx] = (k < KP && g < NG) ? Ry[(int64_t)k * NG + g] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int g = g0 + r;
+    const float2 v = t[tx][r];
+    const int64_t o = ((int64_t)y * NGpad + g) * (KN / 2) + k0 + tx;
+    // b = (v.x, -v.y): X = (v.x, -v.y), Z = (v.y, v.x); the split is odd in its argument
+    __nv_bfloat16 rh, rm, rl, ih, im, il;
+    if (TERMS == 2) {
+      split2(v.x, rh, rl);
+      split2(v.y, ih, il);
+      X[o] = __halves2bfloat162(rh, __hneg(ih));
+      X[o + term_stride] = __halves2bfloat162(rl, __hneg(il));
+      Z[o] = __halves2bfloat162(ih, rh);
+      Z[o + term_stride] = __halves2bfloat162(il, rl);
+    } else {
+      split3(v.x, rh, rm, rl);
+      split3(v.y, ih, im, il);
+      X[o] = __halves2bfloat162(rh, __hneg(ih));
+      X[o + term_stride] = __halves2bfloat162(rm, __hneg(im));
+      X[o + 2 * term_stride] = __halves2bfloat162(rl, __hneg(il));
+      Z[o] = __halves2bfloat162(ih, rh);
+      Z[o + term_stride] = __halves2bfloat162(im, rm);
+      Z[o + 2 * term_stride] = __halves2bfloat162(il, rl);
     }
   }
 }
@@ -753,8 +811,86 @@ cudaError_t nbar_tc_run(const float2* N, const float* wgt, int64_t P, int NG, in
   ga.ngt = NGpad / BN;
   ga.wgt = wgt;
   ga.out = out;
+  ga.nwb = nw;
+  ga.accumulate = 0;
+  ga.out_batch = 0;
   const int nk = ga.nkw * nw;
   const dim3 grid((unsigned)((Prows / BM) * ga.ngt), 1);
+  cudaError_t e;
+  if (terms == 3) {
+    using C = Cfg<3, 32, 3>;
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<3, 32, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  C::SMEM_BYTES)) != cudaSuccess)
+      return e;
+    herk_tc_kernel<3, 32, 3, true><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+                                                                           ga);
+  } else {
+    using C = Cfg<2, 64, 2>;
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<2, 64, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  C::SMEM_BYTES)) != cudaSuccess)
+      return e;
+    herk_tc_kernel<2, 64, 2, true><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+                                                                           ga);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- PAW term on the tensor cores
+// N[(y nR + b)][g] += sum_kp Pm[b][kp] R[y][kp][g] (Eq. 6 with the factor R of
+// each occupied band y) as the unweighted batched variant of the kernel: A =
+// split Pm [terms][Prows][KN], B = split conj R [terms][nL NGpad][KN] as X / Z.
+size_t paw_tc_bytes(int nL, int nR, int KP, int NG, int terms) {
+  const int64_t NGpad = (NG + tc::BM - 1) / tc::BM * tc::BM;
+  const int64_t KN = nbar_kn(KP);
+  return (size_t)terms * ((size_t)nbar_prows(nR) * KN + (size_t)2 * nL * NGpad * KN) * 2;
+}
+
+cudaError_t paw_tc_run(const float2* Pm, const float2* R, int KP, int nL, int nR, int NG, int terms, void* scratch,
+                       size_t bytes, float2* N, int* err, cudaStream_t s) {
+  using namespace tc;
+  if (nL == 0 || nR == 0 || NG == 0 || KP == 0) return cudaSuccess;
+  if ((terms != 2 && terms != 3) || bytes < paw_tc_bytes(nL, nR, KP, NG, terms)) return cudaErrorInvalidValue;
+  const int NGpad = (NG + BM - 1) / BM * BM;
+  const int64_t KN = nbar_kn(KP), Prows = nbar_prows(nR);
+  if ((int64_t)nL * NGpad > (1 << 30) || nL > 65535) return cudaErrorInvalidValue;
+  const int64_t aop = Prows * KN, bop = (int64_t)nL * NGpad * KN;  // bf16 elements per term
+  __nv_bfloat16* A = (__nv_bfloat16*)scratch;
+  __nv_bfloat16* X = A + aop * terms;
+  __nv_bfloat16* Z = X + bop * terms;
+  {
+    const int64_t total = Prows * KN / 2;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    const dim3 pg(NGpad / 32, (unsigned)(KN / 2 / 32), nL);
+    if (terms == 3) {
+      prep_n_kernel<3><<<blocks, 256, 0, s>>>(Pm, nR, KP, Prows, (int)KN, (__nv_bfloat162*)A, aop / 2);
+      prep_r_kernel<3><<<pg, 256, 0, s>>>(R, KP, NG, NGpad, KN, (__nv_bfloat162*)X, (__nv_bfloat162*)Z, bop / 2);
+    } else {
+      prep_n_kernel<2><<<blocks, 256, 0, s>>>(Pm, nR, KP, Prows, (int)KN, (__nv_bfloat162*)A, aop / 2);
+      prep_r_kernel<2><<<pg, 256, 0, s>>>(R, KP, NG, NGpad, KN, (__nv_bfloat162*)X, (__nv_bfloat162*)Z, bop / 2);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int bk = terms == 3 ? 32 : 64;
+  Maps maps;
+  memset(&maps, 0, sizeof(maps));
+  for (int t = 0; t < terms; ++t) {
+    if (!make_map(&maps.a[t], A + aop * t, KN, Prows, bk) ||
+        !make_map(&maps.x[t], X + bop * t, KN, (int64_t)nL * NGpad, bk) ||
+        !make_map(&maps.z[t], Z + bop * t, KN, (int64_t)nL * NGpad, bk))
+      return cudaErrorInvalidValue;
+  }
+  GemmArgs ga;
+  ga.P = nR;
+  ga.nkw = (int)(KN / bk);
+  ga.ngt = NGpad / BN;
+  ga.wgt = nullptr;
+  ga.out = N;
+  ga.nwb = 1;
+  ga.accumulate = 1;
+  ga.out_batch = (int64_t)nR * NG;
+  const int nk = ga.nkw;
+  const dim3 grid((unsigned)((Prows / BM) * ga.ngt), (unsigned)nL);
   cudaError_t e;
   if (terms == 3) {
     using C = Cfg<3, 32, 3>;

@@ -31,6 +31,10 @@ size_t nbar_tc_a_bytes(int64_t P, int NG, int terms);
 cudaError_t nbar_tc_prepare_gam(const float2* Gam, int NG, int nw, int terms, void* gbuf, cudaStream_t s);
 cudaError_t nbar_tc_run(const float2* N, const float* wgt, int64_t P, int NG, int nw, int terms, const void* gbuf,
                         void* abuf, size_t abytes, float2* out, int* err, cudaStream_t s);
+// PAW term N[(y nR + b)][g] += sum_kp Pm[b][kp] R[y][kp][g] on the tensor cores (k_herk_tc.cu)
+size_t paw_tc_bytes(int nL, int nR, int KP, int NG, int terms);
+cudaError_t paw_tc_run(const float2* Pm, const float2* R, int KP, int nL, int nR, int NG, int terms, void* scratch,
+                       size_t bytes, float2* N, int* err, cudaStream_t s);
 // adjoint kernels (k_adjoint.cu)
 cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
                       double2* G64, float2* G32, cudaStream_t s, int64_t* launches);
@@ -145,7 +149,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -549,8 +553,25 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
       tm.add_launches(3);
     }
     if (paw) {
-      CUDA_OK(c, launch_paw_gemm<T>(Rp, Pm, KP, nL, nR, NG, (c2<T>*)p_N, c->stream));
-      tm.add_launches(1);
+      const int prec = c->prm.precision;
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if ((prec == RPA_BF16X2 || prec == RPA_BF16X3) && c->tune[RPA_TUNE_PAW_TC] == 1) {
+          // split-bfloat16 modes: the PAW product on the tensor cores with the
+          // same split as the rank-k update
+          const int terms = prec == RPA_BF16X3 ? 3 : 2;
+          const size_t pb = paw_tc_bytes(nL, nR, KP, NG, terms);
+          void* p_pt;
+          if ((st = workspace(c, "paw_tc", pb, &p_pt)) != RPA_OK) return st;
+          CUDA_OK(c, paw_tc_run(Pm, Rp, KP, nL, nR, NG, terms, p_pt, pb, (float2*)p_N, c->dev_err, c->stream));
+          tm.add_launches(3);
+          done = true;
+        }
+      }
+      if (!done) {
+        CUDA_OK(c, launch_paw_gemm<T>(Rp, Pm, KP, nL, nR, NG, (c2<T>*)p_N, c->stream));
+        tm.add_launches(1);
+      }
     }
   }
   if (Q.optical) {
@@ -1935,6 +1956,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_LOGDET:
       if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "log-det update choice must be 0, 1 or 2");
+      break;
+    case RPA_TUNE_PAW_TC:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "PAW product choice must be 0 or 1");
       break;
     case RPA_TUNE_OPERAND_MB:
       if (value < 16 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "operand budget %lld MB out of range", (long long)value);

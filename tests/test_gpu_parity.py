@@ -246,6 +246,35 @@ def test_tuning_knobs_change_rounding_only():
         b.rpa_destroy(ctx)
 
 
+@pytest.mark.parametrize("precision", ["bf16x2", "bf16x3"])
+def test_paw_product_on_tensor_cores(precision):
+    """The opt-in tensor-core PAW product (Eq. 6 with the per-band factor R)
+    against the oracle: chi0 and the energy terms within the mode's bounds, and
+    the projector count (9) far from a K tile so the zero padding of K is
+    exercised; out-of-range choices are rejected."""
+    p = syn.small_problem(config_tag=95)
+    iq = 1
+    om, W = o.frequency_grid(6)
+    ref = o.chi0(p, iq, om, _oracle_Q(p, iq))
+    v = o.coulomb(p.cell, p.qpoints[iq].q_red, o.g_sphere(p.cell, p.qpoints[iq].q_red, p.ecut_chi))
+    want = o.ec_terms(ref, v)
+    ctx = _ctx(p, precision)
+    try:
+        plain = b.rpa_chi0(ctx, iq, om)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_PAW_TC, 1)
+        chi = b.rpa_chi0(ctx, iq, om)
+        _, t = b.rpa_energy(ctx, [iq], [1.0], om, W)
+        assert _rel(chi, ref) < TOL[precision]["chi"]
+        assert np.abs(t[0] - want).max() <= TOL[precision]["term"] * np.abs(want).max()
+        assert abs(np.dot(W, t[0]) - np.dot(W, want)) <= TOL[precision]["ec"] * abs(np.dot(W, want))
+        assert 0 < _rel(chi, plain) < TOL[precision]["chi"]
+        with pytest.raises(b.RpaError) as e:
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_PAW_TC, 2)
+        assert e.value.status == b.RPA_ERR_ARG
+    finally:
+        b.rpa_destroy(ctx)
+
+
 def test_minimal_transform_grid_equals_caller_grid():
     """The alias-free minimal transform grid and the caller's full grid give the
     same chi0 (both equal the plane-wave sums of Eq. 4)."""
