@@ -465,9 +465,28 @@ __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict_
       src[q] = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
       acc[q] = mk<T>(0, 0);
     }
-    // the PG pairs advance together: four independent loads per step
+    // the PG pairs advance together, UJ steps at a time: PG x UJ independent
+    // loads are in flight before their multiply-adds (the reads of the
+    // stage-B output are strided, so their latency, not issue, is the limit)
+    constexpr int UJ = 4;
     int idx = 0;
-    for (int j3 = 0; j3 < N3; ++j3) {
+    int j3 = 0;
+    for (; j3 + UJ <= N3; j3 += UJ) {
+      c2<T> x[UJ][PG], f[UJ];
+#pragma unroll
+      for (int u = 0; u < UJ; ++u) {
+#pragma unroll
+        for (int q = 0; q < PG; ++q) x[u][q] = src[q][j3 + u];
+        f[u] = tw[idx];
+        idx += step;
+        if (idx >= N3) idx -= N3;
+      }
+#pragma unroll
+      for (int u = 0; u < UJ; ++u)
+#pragma unroll
+        for (int q = 0; q < PG; ++q) cmac<T>(acc[q], x[u][q], f[u]);
+    }
+    for (; j3 < N3; ++j3) {
       const c2<T> f = tw[idx];
 #pragma unroll
       for (int q = 0; q < PG; ++q) cmac<T>(acc[q], src[q][j3], f);
