@@ -34,6 +34,18 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(b.SIGNATURES), "binding signatures out of step with the header"
 
 
+def test_header_constants_match_the_binding():
+    """Every enumerator and numeric macro of include/rpa.h (status codes,
+    precision modes, tuning parameters, profile stage count) has the same value
+    in the Python binding, so a knob added on one side cannot drift."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "rpa.h")).read(), flags=re.S)
+    consts = re.findall(r"\b(RPA_[A-Z0-9_]+)\s*=\s*(\d+)", txt)
+    consts += re.findall(r"#define\s+(RPA_[A-Z0-9_]+)\s+(\d+)", txt)
+    assert len(consts) >= 20
+    for name, value in consts:
+        assert getattr(b, name, None) == int(value), name
+
+
 def test_gauss_legendre_matches_oracle(lib):
     for n in (1, 2, 8, 16, 33):
         om, W = b.rpa_gauss_legendre(n, 1.0)
