@@ -16,12 +16,15 @@
 //
 // Data path: one prep kernel per k-block writes the unweighted X, Z operand
 // splits (K-major, bfloat16), one prep kernel writes the weighted A splits for
-// all frequencies; the GEMM kernel streams 128x64 tiles with TMA
-// (cp.async.bulk.tensor, 128-byte swizzle) into a 2-stage shared-memory ring,
-// one thread issues tcgen05.mma (M = N = 128, K = 16) into two TMEM
-// accumulator buffers (Re 128 + Im 128 columns each), and eight epilogue
-// warps drain one buffer with tcgen05.ld while the MMAs fill the other.
-// Only lower-triangle tiles are launched.  Every wait is bounded by the GPU
+// all frequencies; the kernel streams 128-row tiles with TMA
+// (cp.async.bulk.tensor; 64-element stages with the 128-byte swizzle in a
+// 2-stage ring, or 32-element stages with the 64-byte swizzle for three
+// terms), one thread issues one tcgen05.mma (M = 128, N = 256, K = 16) per
+// product with the X tile stacked on the Z tile, so Re and Im land in one
+// 256-column TMEM buffer; two such buffers alternate, and sixteen epilogue
+// warps drain one with tcgen05.ld while the MMAs fill the other.  Only
+// lower-triangle tiles are launched.  A batched product variant (GEMM = true)
+// serves the adjoint and the PAW term.  Every wait is bounded by the GPU
 // global timer; on timeout the CTA raises a flag, drains, frees TMEM and exits.
 #include "rpa_internal.h"
 

@@ -7,10 +7,11 @@
 //    conj(u_nk(r)) u_m,k+q(r) is fused into the first (slowest-axis) DFT, the
 //    middle axis follows, and the fastest axis is evaluated only on the
 //    response sphere g = G + G0 (the "mapG" gather of step 6 fused into the
-//    transform).  The PAW term of Eq. 6 (steps 8-9) is added in the same
-//    epilogue from the factorised form sum_(a,j) P_mj R^a_n(j,G) with
-//    R^a_n(j,G) = sum_i conj(P_ni) Q^a_ij(G), which equals the paper's
-//    outer-product-then-contract order exactly in exact arithmetic.
+//    transform).  The PAW term of Eq. 6 (steps 8-9) is then added by one
+//    complex GEMM per occupied band (paw_gemm_kernel) from the factorised form
+//    sum_(a,j) P_mj R^a_n(j,G) with R^a_n(j,G) = sum_i conj(P_ni) Q^a_ij(G)
+//    (paw_R_kernel), which equals the paper's outer-product-then-contract
+//    order in exact arithmetic.
 //
 // Twiddles come from a table tw[t] = exp(2 pi i t / N), t in [0, N), filled
 // with sincospi in double precision; every phase index is reduced exactly in
