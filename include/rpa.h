@@ -67,8 +67,12 @@ typedef enum {
  *              products), FP32 accumulation in tensor memory, FP64 chi0.
  * RPA_BF16X3 : as BF16X2 with three bfloat16 terms (hi + mid + lo, about
  *              24 bits per operand) and six products (hh, hm, mh, mm, hl, lh).
- * In every mode the PAW projection products, the log-det and the frequency
- * quadrature run in FP64. */
+ * In every mode the PAW factor R_n(j, G) = sum_i conj(P_ni) Q_ij(G) is formed
+ * in FP64 and stored in the mode's working precision; the PAW product
+ * sum_j P_mj R_n(j, G) runs in FP32 on the CUDA cores in the mixed modes (or
+ * on the tensor cores, RPA_TUNE_PAW_TC).  The log-det is FP64 in RPA_FP64 and
+ * float-float (about 44 bits, FP64 pivots) in the other modes
+ * (RPA_TUNE_LOGDET); the frequency quadrature is FP64. */
 typedef enum {
   RPA_FP64 = 0,
   RPA_FP32 = 1,
@@ -197,8 +201,10 @@ rpa_status rpa_chi0(rpa_ctx* ctx, int32_t iq, int32_t nw, const double* omega,
                     double* chi_out);
 
 /* E_c = sum_i wq[i] sum_j W[j] / (2 pi) e_{iqs[i]}(omega_j) (Eqs. 1-2) over
- * nq q-points; e_q(w) = ln det(1 - M) + tr M, M = v^1/2 chi0 v^1/2, by FP64
- * Cholesky on the device.  *Ec host; terms (nullable, host) receives
+ * nq q-points; e_q(w) = ln det(1 - M) + tr M, M = v^1/2 chi0 v^1/2, by a
+ * blocked Cholesky on the device (FP64; float-float trailing updates with FP64
+ * pivots in the mixed modes, RPA_TUNE_LOGDET).  *Ec host; terms (nullable,
+ * host) receives
  * e_q(omega_j) as terms[nq][nw].  RPA_ERR_NOT_HPD if a Cholesky pivot is not
  * positive. */
 rpa_status rpa_energy(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
@@ -264,7 +270,8 @@ rpa_status rpa_energy_backward(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
 rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
 rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
 
-/* Tuning knobs (no effect on results beyond rounding order):
+/* Tuning knobs (they change launch shapes and rounding, never the quantity
+ * computed):
  * RPA_TUNE_TC_FOLD     units of K accumulated in FP32 tensor memory before
  *                      the partial sum is added to FP32 running sums in
  *                      registers (split-bfloat16 modes), in [1, 2^20];
