@@ -204,9 +204,8 @@ rpa_status rpa_chi0(rpa_ctx* ctx, int32_t iq, int32_t nw, const double* omega,
  * nq q-points; e_q(w) = ln det(1 - M) + tr M, M = v^1/2 chi0 v^1/2, by a
  * blocked Cholesky on the device (FP64; float-float trailing updates with FP64
  * pivots in the mixed modes, RPA_TUNE_LOGDET).  *Ec host; terms (nullable,
- * host) receives
- * e_q(omega_j) as terms[nq][nw].  RPA_ERR_NOT_HPD if a Cholesky pivot is not
- * positive. */
+ * host) receives e_q(omega_j) as terms[nq][nw].  RPA_ERR_NOT_HPD if a
+ * Cholesky pivot is not positive. */
 rpa_status rpa_energy(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
                       const double* wq, int32_t nw, const double* omega,
                       const double* W, double* Ec, double* terms);
