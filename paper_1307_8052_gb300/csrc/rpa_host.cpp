@@ -1283,27 +1283,63 @@ rpa_status rpa_set_orbitals(rpa_ctx* c, int32_t kidx, const double k_red[3], int
     pos[q] = (int)flat;
   }
   rpa_status st;
-  if ((st = dev_alloc(c, (void**)&s.C, sizeof(double2) * (size_t)nbands * npw)) != RPA_OK) return st;
+  // A set that replaces one of the same shape (the usual case when the
+  // orbitals are updated every step) takes over its device buffers instead of
+  // freeing and allocating them again; its grids are marked stale (stamp 0,
+  // below every call's stamp) and rebuilt in place by the next call.  The
+  // previous work that read them is complete: every call ends synchronised
+  // with the context stream, which the other streams join.  If the upload
+  // then fails (a CUDA error), the set kidx is dropped rather than kept.
+  auto old_it = c->sets.find(kidx);
+  if (old_it != c->sets.end()) {
+    OrbSet& o = old_it->second;
+    if (o.nb == nbands && o.npw == npw) {
+      std::swap(s.C, o.C);
+      std::swap(s.eps_d, o.eps_d);
+      std::swap(s.f_d, o.f_d);
+      std::swap(s.pos_d, o.pos_d);
+      std::swap(s.U, o.U);
+      std::swap(s.Ubytes, o.Ubytes);
+      if (o.L.size() == s.L.size()) std::swap(s.L_d, o.L_d);
+      if (o.R.size() == s.R.size()) std::swap(s.R_d, o.R_d);
+      o.valid = false;  // its buffers now belong to s; dropped below or on failure
+    }
+  }
   auto cleanup = [&]() {
     dev_free(s.C); dev_free(s.eps_d); dev_free(s.f_d); dev_free(s.pos_d); dev_free(s.L_d); dev_free(s.R_d);
+    dev_free(s.U);
+    if (old_it != c->sets.end() && !old_it->second.valid) {
+      OrbSet& o = old_it->second;
+      dev_free(o.C); dev_free(o.eps_d); dev_free(o.f_d); dev_free(o.pos_d);
+      dev_free(o.L_d); dev_free(o.R_d); dev_free(o.P); dev_free(o.U);
+      c->sets.erase(old_it);
+    }
   };
-  if ((st = dev_alloc(c, (void**)&s.eps_d, sizeof(double) * nbands)) != RPA_OK) { cleanup(); return st; }
-  if ((st = dev_alloc(c, (void**)&s.f_d, sizeof(double) * nbands)) != RPA_OK) { cleanup(); return st; }
-  if ((st = dev_alloc(c, (void**)&s.pos_d, sizeof(int) * npw)) != RPA_OK) { cleanup(); return st; }
-  if ((st = dev_alloc(c, (void**)&s.L_d, sizeof(int) * std::max<size_t>(1, s.L.size()))) != RPA_OK) { cleanup(); return st; }
-  if ((st = dev_alloc(c, (void**)&s.R_d, sizeof(int) * std::max<size_t>(1, s.R.size()))) != RPA_OK) { cleanup(); return st; }
+  if (!s.C && (st = dev_alloc(c, (void**)&s.C, sizeof(double2) * (size_t)nbands * npw)) != RPA_OK) { cleanup(); return st; }
+  if (!s.eps_d && (st = dev_alloc(c, (void**)&s.eps_d, sizeof(double) * nbands)) != RPA_OK) { cleanup(); return st; }
+  if (!s.f_d && (st = dev_alloc(c, (void**)&s.f_d, sizeof(double) * nbands)) != RPA_OK) { cleanup(); return st; }
+  if (!s.pos_d && (st = dev_alloc(c, (void**)&s.pos_d, sizeof(int) * npw)) != RPA_OK) { cleanup(); return st; }
+  if (!s.L_d && (st = dev_alloc(c, (void**)&s.L_d, sizeof(int) * std::max<size_t>(1, s.L.size()))) != RPA_OK) { cleanup(); return st; }
+  if (!s.R_d && (st = dev_alloc(c, (void**)&s.R_d, sizeof(int) * std::max<size_t>(1, s.R.size()))) != RPA_OK) { cleanup(); return st; }
   if ((st = copy_in(c, s.C, C, sizeof(double2) * (size_t)nbands * npw)) != RPA_OK) { cleanup(); return st; }
-  CUDA_OK(c, cudaMemcpyAsync(s.eps_d, s.eps.data(), sizeof(double) * nbands, cudaMemcpyHostToDevice, c->stream));
-  CUDA_OK(c, cudaMemcpyAsync(s.f_d, s.f.data(), sizeof(double) * nbands, cudaMemcpyHostToDevice, c->stream));
-  CUDA_OK(c, cudaMemcpyAsync(s.pos_d, pos.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, c->stream));
-  if (!s.L.empty())
-    CUDA_OK(c, cudaMemcpyAsync(s.L_d, s.L.data(), sizeof(int) * s.L.size(), cudaMemcpyHostToDevice, c->stream));
-  if (!s.R.empty())
-    CUDA_OK(c, cudaMemcpyAsync(s.R_d, s.R.data(), sizeof(int) * s.R.size(), cudaMemcpyHostToDevice, c->stream));
-  CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  auto it = c->sets.find(kidx);
-  if (it != c->sets.end()) {
-    OrbSet& o = it->second;
+  cudaError_t ue = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (ue == cudaSuccess && bytes) ue = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+  };
+  up(s.eps_d, s.eps.data(), sizeof(double) * nbands);
+  up(s.f_d, s.f.data(), sizeof(double) * nbands);
+  up(s.pos_d, pos.data(), sizeof(int) * npw);
+  up(s.L_d, s.L.data(), sizeof(int) * s.L.size());
+  up(s.R_d, s.R.data(), sizeof(int) * s.R.size());
+  if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
+  if (ue != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    return fail(c, RPA_ERR_CUDA, "orbital upload: %s", cudaGetErrorString(ue));
+  }
+  s.grid_stamp = 0;
+  if (old_it != c->sets.end()) {
+    OrbSet& o = old_it->second;
     dev_free(o.C); dev_free(o.eps_d); dev_free(o.f_d); dev_free(o.pos_d);
     dev_free(o.L_d); dev_free(o.R_d); dev_free(o.P); dev_free(o.U);
   }
