@@ -1287,9 +1287,10 @@ rpa_status rpa_set_orbitals(rpa_ctx* c, int32_t kidx, const double k_red[3], int
   // orbitals are updated every step) takes over its device buffers instead of
   // freeing and allocating them again; its grids are marked stale (stamp 0,
   // below every call's stamp) and rebuilt in place by the next call.  The
-  // previous work that read them is complete: every call ends synchronised
-  // with the context stream, which the other streams join.  If the upload
-  // then fails (a CUDA error), the set kidx is dropped rather than kept.
+  // new contents are written on the context stream, after all earlier work
+  // that read the buffers (the other streams join the context stream before
+  // a call returns), and the upload is complete when this call returns.  If
+  // it fails (a CUDA error), the set kidx is dropped rather than kept.
   auto old_it = c->sets.find(kidx);
   if (old_it != c->sets.end()) {
     OrbSet& o = old_it->second;
