@@ -177,25 +177,47 @@ def test_config1_geometry_two_transitions(precision):
         b.rpa_destroy(ctx)
 
 
-def test_config1_full_size_sampled_bf16x2():
-    """The bench's workload at full size (all 8 k, 16 occupied x 1200 empty bands,
-    PAW) in the bench's mode and launch configuration: chi0 elements on sampled
-    G rows/columns against the oracle evaluated at those G only, plus properties
-    that hold at any size (Hermitian, non-positive diagonal)."""
+@pytest.fixture(scope="module")
+def full_size_case():
+    """The bench's bulk workload at full size (all 8 k, 16 occupied x 1200 empty
+    bands, 3 x 13 PAW projectors, 16 frequencies) at q = (0, 1/2, 1/2), and the
+    oracle at 23 sampled G indices: both ragged edges (0, 1, NG-2, NG-1), the last
+    row of every 128-row tile of the rank-k kernel and one random row inside each
+    tile, in shuffled order, so every row and column tile of the lower-triangle
+    grid and both of its ragged edges are checked."""
     p = syn.config1()
     iq = 3
     om, _ = o.frequency_grid(16)
-    ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, "bf16x2")
+    ng = len(o.g_sphere(p.cell, p.qpoints[iq].q_red, p.ecut_chi))
+    rng = np.random.default_rng(11)
+    g = {0, 1, ng - 2, ng - 1}
+    for t in range((ng + 127) // 128):
+        lo, hi = 128 * t, min(ng, 128 * t + 128)
+        g.add(int(rng.integers(lo, hi)))
+        g.add(hi - 1)
+    gidx = np.array(sorted(g))
+    rng.shuffle(gidx)
+    ref = o.chi0_sampled(p, iq, om, gidx, _oracle_Q(p, iq))
+    return p, iq, om, gidx, ref
+
+
+@pytest.mark.parametrize("precision", ["bf16x2", "fp64"])
+def test_config1_full_size_sampled(full_size_case, precision):
+    """Full-size chi0 in the bench's launch configuration (bf16x2) and in the plain
+    FP64 mode: elements on the sampled G rows/columns against the oracle
+    evaluated at those G only, plus properties that hold at any size (Hermitian,
+    non-positive diagonal)."""
+    p, iq, om, gidx, ref = full_size_case
+    ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, precision)
     try:
         b.load_problem(ctx, p, qs=[iq], paw_Q=lambda i, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[i].q_red, gm))
         chi = b.rpa_chi0(ctx, iq, om)
     finally:
         b.rpa_destroy(ctx)
     ng = chi.shape[1]
-    gidx = [0, 1, 17, ng // 2, ng - 2, ng - 1]
-    ref = o.chi0_sampled(p, iq, om, gidx, _oracle_Q(p, iq))
+    assert ng > 1100 and ng % 128 != 0 and max(gidx) == ng - 1
     got = chi[:, gidx][:, :, gidx]
-    assert np.abs(got - ref).max() / np.abs(ref).max() < TOL["bf16x2"]["chi"]
+    assert np.abs(got - ref).max() / np.abs(ref).max() < TOL[precision]["chi"]
     assert np.array_equal(chi[3], chi[3].conj().T)
     assert np.all(np.einsum("wii->wi", chi).real <= 0)
 
