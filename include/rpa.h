@@ -344,7 +344,8 @@ rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
  * Scratch: one process-wide static device array per device (17 MiB + 2 KiB,
  * held until the process exits).  Limits: 1 <= nw <= 64 and
  * nw * ng * ng <= 1048576 (e.g. ng <= 256 at nw = 16); larger sizes, null or
- * host pointers return RPA_ERR_ARG without touching the GPU.  The first call on
+ * host pointers, and device memory of a GPU other than the current device
+ * return RPA_ERR_ARG without touching the GPU.  The first call on
  * a device looks up the scratch address on that device (cudaGetSymbolAddress);
  * make that first call before any stream capture.  It calls no cudaMalloc,
  * cudaFree or other allocating routine.  Every call reuses the same array and

@@ -590,6 +590,8 @@ extern "C" rpa_status rpa_logdet_noalloc(const double* chi, const double* v, int
       return RPA_ERR_ARG;
     }
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return RPA_ERR_ARG;
+    // device memory of another GPU is not readable by this device's kernels
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) return RPA_ERR_ARG;
   }
   // one-time set-up per device: the device address of the static scratch
   void* base = nullptr;

@@ -65,3 +65,18 @@ def test_logdet_noalloc_rejects_oversize_and_host_pointers():
     with pytest.raises(b.RpaError) as e:
         b.rpa_logdet_noalloc(big[:1].cpu(), v.cpu(), out[:1].cpu())
     assert e.value.status == b.RPA_ERR_ARG
+
+
+def test_logdet_noalloc_rejects_memory_of_another_device():
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second visible GPU")
+    build()
+    b.load()
+    torch.cuda.set_device(0)
+    chi = torch.zeros((1, 8, 8), dtype=torch.complex128, device="cuda:1")
+    v = torch.ones(8, dtype=torch.float64, device="cuda:1")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda:1")
+    with pytest.raises(b.RpaError) as e:
+        b.rpa_logdet_noalloc(chi, v, out)
+    assert e.value.status == b.RPA_ERR_ARG
