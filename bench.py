@@ -13,9 +13,13 @@ is one E_c evaluation over all 8 q-points: wavefunctions to the grid, pair
 densities + PAW, rank-k update, FP64 log-det and quadrature.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-With --gpus N > 1 it expects torchrun: every rank runs its own replica of the
-step (independent problems, no data-path collective) and rank 0 prints one
-JSON line with the whole-job throughput.
+With --gpus N > 1 it expects torchrun.  By default the 8 q-points of one step
+are split over the ranks (shard.shard_qpoints, balanced by NG^2 x pairs); each
+rank evaluates its share with its own context, E_c is the sum of one scalar per
+rank (shard.sharded_energy) and no collective touches the data path: total
+work is fixed, so the line says "scaling": "strong".  With --replicas every
+rank runs the whole step on its own copy of the workload instead (weak
+scaling).  Rank 0 prints one JSON line with the whole-job throughput.
 """
 from __future__ import annotations
 
@@ -240,28 +244,39 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     p = make_workload(args.config)
-    iqs = workload_qpoints(args, p)
-    nq = len(iqs)
+    iqs_all = workload_qpoints(args, p)
     om, W = b.rpa_gauss_legendre(p.nw, 1.0)
-    wq = [p.qpoints[i].weight for i in iqs]
     Kall = pairs_per_q(p)
-    Kq = [Kall[i] for i in iqs]
 
     # q = 0 of the bulk mesh carries the optical-limit head and wings (Eqs. 12-14)
-    optical_q = [i for i in iqs if np.all(p.qpoints[i].q_red == 0)] if args.config == "bulk" else []
+    optical_all = [i for i in iqs_all if np.all(p.qpoints[i].q_red == 0)] if args.config == "bulk" else []
 
-    def make_ctx(precision):
+    def make_ctx(precision, qs):
         ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, precision, device=local,
                            stream=stream.cuda_stream)
-        ngs = b.load_problem(ctx, p, qs=iqs,
+        ngs = b.load_problem(ctx, p, qs=qs,
                              paw_Q=lambda iq, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, gm))
-        for iq in optical_q:
-            b.rpa_set_optical(ctx, iq, OPTICAL_QDIR, p.paw.nproj, syn.paw_Qnabla(p.paw, p.config))
+        for iq in optical_all:
+            if iq in qs:
+                b.rpa_set_optical(ctx, iq, OPTICAL_QDIR, p.paw.nproj, syn.paw_Qnabla(p.paw, p.config))
         if args.paw_tc:
             b.rpa_set_tuning(ctx, b.RPA_TUNE_PAW_TC, 1)
         return ctx, ngs
 
-    ctx, ngs = make_ctx(args.precision)
+    # every rank loads every q-point of the step (the response spheres give the
+    # cost of each), then evaluates the share shard.shard_qpoints assigns it,
+    # or the whole step with --replicas
+    ctx, ngs_all = make_ctx(args.precision, iqs_all)
+    costs = [float(ng) ** 2 * Kall[iq] for ng, iq in zip(ngs_all, iqs_all)]
+    shards = shard.partition(iqs_all, costs, world, args.replicas)
+    iqs = shards[rank]
+    nq = len(iqs)
+    wq = [p.qpoints[i].weight for i in iqs]
+    Kq = [Kall[i] for i in iqs]
+    ngs = [ngs_all[iqs_all.index(i)] for i in iqs]
+    # whole-job work: every rank's share (replicas: world copies of the step)
+    job_flops = float(sum(rankk_flops([ngs_all[iqs_all.index(i)] for i in part], [Kall[i] for i in part], p.nw)
+                          for part in shards))
     flops = rankk_flops(ngs, Kq, p.nw)
     b.rpa_set_profiling(ctx, True)
 
@@ -274,8 +289,18 @@ def run_ours(args):
     def max_over_ranks(x):
         return shard.max_over_ranks(x, device="cuda")
 
+    wq_all = [p.qpoints[i].weight for i in iqs_all]
+
+    def evaluate(qs, wqs):
+        return b.rpa_energy(ctx, qs, wqs, om, W)[0]
+
+    def step():
+        # this rank's share (or the whole step with --replicas); E_c summed over the ranks
+        return shard.sharded_step(evaluate, iqs_all, costs, wq_all, rank, world, device="cuda",
+                                  replicas=args.replicas)
+
     for _ in range(args.warmup):
-        b.rpa_energy(ctx, iqs, wq, om, W)
+        step()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -284,7 +309,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            E, terms = b.rpa_energy(ctx, iqs, wq, om, W)
+            E = step()
             ms, nl = b.rpa_get_profile(ctx)
             stage_ms += ms
             launches += nl
@@ -292,7 +317,7 @@ def run_ours(args):
         barrier()
     t_step = e0.elapsed_time(e1) / args.steps / 1e3
     t_step = max_over_ranks(t_step)
-    value = world * flops / t_step / 1e12
+    value = job_flops / t_step / 1e12
 
     # end to end through the public API from pinned host buffers
     pinned = []
@@ -312,7 +337,7 @@ def run_ours(args):
             b.rpa_set_paw(ctx, i, p.paw.nproj, pinned[i][1])
         for iq in iqs:
             b.rpa_set_paw_Q(ctx, iq, p.paw.nproj, Qpin[iq])
-        return b.rpa_energy(ctx, iqs, wq, om, W)
+        return step()
 
     t_e2e = float("nan")
     if not args.no_e2e:
@@ -326,39 +351,57 @@ def run_ours(args):
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3)
     b.rpa_set_profiling(ctx, False)
 
-    # plain FP64 form on one q-point for the mixed-vs-FP64 statement
-    fp64 = None
-    if args.fp64_q >= 0 and args.config == "bulk":
+    # plain FP64 form, and the FP32 mode, on one q-point (rank 0) for the
+    # mixed-vs-FP64 statement: time per q, TFLOP/s, E_c error against FP64
+    modes = {}
+    if rank == 0 and args.fp64_q >= 0 and args.config == "bulk":
         iq = args.fp64_q
-        pos = iqs.index(iq)
-        ctx64, ngs64 = make_ctx("fp64")
-        b.rpa_set_profiling(ctx64, True)
-        barrier()
-        e0.record(stream)
-        E64, t64 = b.rpa_energy(ctx64, [iq], [1.0], om, W)
-        e1.record(stream)
-        barrier()
-        s64 = e0.elapsed_time(e1) / 1e3
-        ms64, _ = b.rpa_get_profile(ctx64)
-        b.rpa_destroy(ctx64)
+        pos = iqs_all.index(iq)
+        fq = rankk_flops([ngs_all[pos]], [Kall[iq]], p.nw)
         Emix, tmix = b.rpa_energy(ctx, [iq], [1.0], om, W)
-        f64 = rankk_flops([ngs64[pos]], [Kq[pos]], p.nw)
-        fp64 = {"q": iq, "s_per_q": s64, "chi0_tflops": f64 / s64 / 1e12,
-                "rankk_ms": ms64[2], "logdet_ms": ms64[3],
-                "speedup_mixed_vs_fp64": s64 / (t_step / nq),
-                "ec_q_fp64": E64, "ec_q_mixed": Emix, "ec_rel_error": abs(Emix - E64) / abs(E64),
-                "terms_max_rel_error": float(np.max(np.abs(tmix - t64)) / np.max(np.abs(t64)))}
+        for mode in ("fp64", "fp32"):
+            if mode == "fp32" and args.no_fp32:
+                continue
+            cm, _ = make_ctx(mode, [iq])
+            if mode == "fp32":
+                b.rpa_energy(cm, [iq], [1.0], om, W)  # one untimed warm-up (the FP64 run is long enough without)
+            b.rpa_set_profiling(cm, True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            Em, tm = b.rpa_energy(cm, [iq], [1.0], om, W)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sm_ = e0.elapsed_time(e1) / 1e3
+            msm, _ = b.rpa_get_profile(cm)
+            b.rpa_destroy(cm)
+            modes[mode] = {"q": iq, "s_per_q": sm_, "chi0_tflops": fq / sm_ / 1e12, "rankk_ms": msm[2],
+                           "logdet_ms": msm[3], "E_c_q": Em, "terms": tm}
+        if "fp64" in modes:
+            E64, t64 = modes["fp64"]["E_c_q"], modes["fp64"].pop("terms")
+            modes["fp64"].update({"speedup_mixed_vs_fp64": modes["fp64"]["s_per_q"] / (t_step / max(nq, 1)),
+                                  "ec_q_fp64": E64, "ec_q_mixed": Emix,
+                                  "ec_rel_error": abs(Emix - E64) / abs(E64),
+                                  "terms_max_rel_error": float(np.max(np.abs(tmix - t64)) / np.max(np.abs(t64)))})
+            if "fp32" in modes:
+                t32 = modes["fp32"].pop("terms")
+                E32 = modes["fp32"]["E_c_q"]
+                modes["fp32"].update({"ec_rel_error_vs_fp64": abs(E32 - E64) / abs(E64),
+                                      "terms_max_rel_error_vs_fp64":
+                                          float(np.max(np.abs(t32 - t64)) / np.max(np.abs(t64))),
+                                      "speedup_vs_fp64": modes["fp64"]["s_per_q"] / modes["fp32"]["s_per_q"]})
 
     peaks, peak_kind = load_peaks()
     herk_ms = stage_ms[2] / args.steps
+    peak_sus = None
     if args.precision in ("bf16x2", "bf16x3"):
         peak = peaks.get("bf16_tflops_sustained" if args.sustained else "bf16_tflops")
+        peak_sus = peaks.get("bf16_tflops_sustained")
         bound = "tensor"
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = (152 * 128 * 2 * sm_mhz * 1e6 / 1e12) if args.precision == "fp32" else 1.05
         bound = "alu"
-    achieved = flops / (herk_ms / 1e3) / 1e12
+    achieved = flops / (herk_ms / 1e3) / 1e12 if herk_ms > 0 else None
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     pd_fl = pd_flops([int(np.prod(p.grid))] * len(Kq), Kq)
     base = None
@@ -368,23 +411,38 @@ def run_ours(args):
     if rank != 0:
         return
     stage_names = ["wf_to_grid", "pair_density_paw", "rankk_kernel", "logdet", "other", "rankk_operand_prep"]
+    mixed = args.precision in ("fp32", "bf16x2", "bf16x3")
+    terms = {"bf16x2": 2, "bf16x3": 3}.get(args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak" if (args.replicas or world == 1) else "strong",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x2": "bf16x2->f32",
                                        "bf16x3": "bf16x3->f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD_SLAB if args.config == "slab" else WORKLOAD, "precision": args.precision,
-                   "q_points": nq, "NG": ngs,
-                   "optical_limit": (f"q=0 head and wings along {OPTICAL_QDIR}" if optical_q else None),
+                   "q_points": len(iqs_all), "NG": ngs_all,
+                   "optical_limit": (f"q=0 head and wings along {OPTICAL_QDIR}" if optical_all else None),
                    "paw_product": "tensor cores" if args.paw_tc else "CUDA cores (FP32)",
-                   "pairs_per_q": Kq, "nw": p.nw, "l2": "inputs larger than L2 (grids >= 1.4 GB, rank-k operands >= 3 GB per block)",
-                   "parallelism": f"replicas x{world}"},
-        "s_per_q": t_step / nq,
+                   "rankk": (f"tcgen05 split bfloat16 ({terms} terms per operand, FP32 accumulation in TMEM, "
+                             "FP32 register folds, FP64 chi0)" if terms else
+                             "CUDA cores, FP32 with compensated folds into FP64 chi0" if args.precision == "fp32"
+                             else "CUDA cores, FP64"),
+                   "logdet": ("blocked Cholesky, float-float trailing update (~44 bits) with FP64 pivots, "
+                              "FP64 diagonal blocks and inverses, one-panel look-ahead" if mixed else
+                              "blocked Cholesky, FP64 throughout"),
+                   "quadrature": "FP64 Gauss-Legendre, 16 nodes mapped to [0, inf)",
+                   "pairs_per_q": [Kall[i] for i in iqs_all], "nw": p.nw,
+                   "l2": "inputs larger than L2 (grids >= 1.4 GB, pair densities + rank-k operands >= 0.5 GB per block)",
+                   "parallelism": (f"replicas x{world}" if args.replicas or world == 1 else
+                                   f"q-points sharded over {world} ranks (no data-path collective): "
+                                   + "; ".join(f"rank {r}: q {part}" for r, part in enumerate(shards)))},
+        "s_per_q": t_step / max(nq, 1),
         "E_c": E,
         "stage_ms_per_step": {n: float(m / args.steps) for n, m in zip(stage_names, stage_ms)},
-        "fp64": fp64,
-        "e2e": {"value": world * flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+        "fp64": modes.get("fp64"),
+        "fp32": modes.get("fp32"),
+        "e2e": {"value": job_flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3},
         "gpu_launches": int(launches.sum()),
         "roofline_pair_density": {
@@ -395,11 +453,16 @@ def run_ours(args):
             "flops_convention": "6 N_r + 5 N_r log2 N_r per pair on the caller's grid (FFT count)",
             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"},
         "roofline": {"bound": bound, "kernel": "rank-k update (Eq. 17)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                     "peak_sustained": peak_sus,
+                     "frac_sustained": (achieved / peak_sus) if (achieved and peak_sus) else None,
+                     "issued_frac": ((achieved * {2: 3, 3: 6}[terms] / peak) if (achieved and terms) else None),
+                     "issued_note": "hardware bf16 products per algorithmic product: 3 (two terms) or 6 (three)",
                      "traffic": herk_traffic() if (bound == "tensor" and args.config == "bulk") else None,
                      "traffic_note": "ncu DRAM read+write bytes of one launch of the profiling case (one k-block, "
                                      "NG 1180); null once the kernel's device code differs from the captured one",
-                     "peak_source": peak_kind if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x max clock"},
+                     "peak_source": (f"{peak_kind} (bf16 burst; frac_sustained uses the sustained figure)"
+                                     if bound == "tensor" else "derived: 152 SM x 128 FP32 lanes x 2 x max clock")},
         "clocks": clk.summary(),
         "cpu_baseline": base,
     }
@@ -557,6 +620,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16x2", "bf16x3"], default="bf16x2")
     ap.add_argument("--fp64-q", type=int, default=3, help="q-point timed in plain FP64 (-1: skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-mode q-point")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: every rank runs the whole step (weak scaling) instead of a share of its q-points")
     ap.add_argument("--sustained", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--config", choices=["bulk", "slab", "batched", "backward"], default="bulk")

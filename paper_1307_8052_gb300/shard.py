@@ -64,3 +64,29 @@ def sharded_energy(evaluate, costs: Sequence[float], wq: Sequence[float], rank: 
     mine = shard_qpoints(costs, world)[rank]
     part = evaluate(mine, [wq[i] for i in mine]) if mine else 0.0
     return sum_over_ranks(part, device)
+
+
+def partition(iqs: Sequence[int], costs: Sequence[float], world: int, replicas: bool = False) -> list[list[int]]:
+    """q-point indices of every rank: a balanced share of ``iqs`` (``costs[i]``
+    belongs to ``iqs[i]``), or all of them on every rank with ``replicas``."""
+    if replicas:
+        return [list(iqs) for _ in range(world)]
+    return [[iqs[i] for i in part] for part in shard_qpoints(costs, world)]
+
+
+def sharded_step(evaluate_q, iqs: Sequence[int], costs: Sequence[float], wq: Sequence[float], rank: int,
+                 world: int, device=None, replicas: bool = False) -> float:
+    """One E_c step over the q-points ``iqs`` (weights ``wq``, costs ``costs``,
+    aligned with ``iqs``) on ``world`` ranks.
+
+    ``evaluate_q(q_indices, weights)`` returns the weighted energy of the given
+    q-points on this rank (a wrapper of ``rpa_energy``).  Sharded: this rank's
+    balanced share is evaluated and the scalar partial energies are summed over
+    the ranks, so every rank returns the E_c of all of ``iqs``.  Replicas:
+    every rank evaluates all of ``iqs`` on its own and returns that E_c."""
+    if replicas:
+        return float(evaluate_q(list(iqs), list(wq)))
+
+    def by_position(pos, wqs):
+        return evaluate_q([iqs[i] for i in pos], wqs)
+    return sharded_energy(by_position, costs, wq, rank, world, device)

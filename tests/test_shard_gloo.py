@@ -45,12 +45,22 @@ def _rank_main(rank, world, port, out):
         wq = [qp.weight for qp in p.qpoints]
 
         def evaluate(iqs, wqs):
+            # the oracle's energy with the weights the step hands over
+            sub = [p.qpoints[i].weight for i in iqs]
+            assert np.allclose(sub, wqs)
             E, _ = o.energy(p, om, W, Qs=Qs, iqs=iqs)
             return E
 
         E = shard.sharded_energy(evaluate, costs, wq, rank, world)
+        # the step function the bench runs, over the q-points in a permuted
+        # order (costs and weights aligned with that order)
+        order = list(range(len(p.qpoints)))[::-1]
+        E_step = shard.sharded_step(evaluate, order, [costs[i] for i in order], [wq[i] for i in order], rank, world)
+        mine = shard.partition(order, [costs[i] for i in order], world)[rank]
+        E_rep = shard.sharded_step(evaluate, order, [costs[i] for i in order], [wq[i] for i in order], rank, world,
+                                   replicas=True)
         t = shard.max_over_ranks(1.0 + rank)
-        out[rank] = (E, t)
+        out[rank] = (E, t, E_step, mine, E_rep)
     finally:
         dist.destroy_process_group()
 
@@ -79,7 +89,14 @@ def test_two_gloo_ranks_sum_sharded_energy():
     Qs = {iq: syn.paw_Q(p.paw, p.cell, qp.q_red, o.g_sphere(p.cell, qp.q_red, p.ecut_chi))
           for iq, qp in enumerate(p.qpoints)}
     E_ref, _ = o.energy(p, om, W, Qs=Qs)
+    shares = []
     for r in range(2):
-        E, t = res[r]
+        E, t, E_step, mine, E_rep = res[r]
         assert abs(E - E_ref) <= 1e-12 * abs(E_ref)
+        assert abs(E_step - E_ref) <= 1e-12 * abs(E_ref)
+        assert abs(E_rep - E_ref) <= 1e-12 * abs(E_ref)
         assert t == 2.0
+        shares.append(mine)
+    # the two ranks' shares cover every q-point once
+    assert sorted(shares[0] + shares[1]) == list(range(len(p.qpoints)))
+    assert shares[0] and shares[1]
