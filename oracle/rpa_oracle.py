@@ -425,11 +425,15 @@ def dE_dchi(chi, v, omega_weights, wq) -> np.ndarray:
     return out
 
 
-def energy_grad(problem, omega, W, Qs=None, iqs=None):
+def energy_grad(problem, omega, W, Qs=None, iqs=None, optical=None):
     """E_c and its gradient with respect to every orbital set's C and P.
 
-    Returns (E, gC, gP, gchi) with gC[s] shaped like sets[s].C, gP[s] like
-    sets[s].P (or None) and gchi[iq] the dE/dchi0 array of each q."""
+    ``optical[iq] = (qdir, Qnabla)`` switches on the optical limit of a q = 0
+    point as in ``energy``: the G = 0 pair densities are the head of Eq. 12,
+    so their adjoint runs through Eq. 13 (the dipole matrix) instead of the
+    plane-wave sum and the PAW term.  Returns (E, gC, gP, gchi) with gC[s]
+    shaped like sets[s].C, gP[s] like sets[s].P (or None) and gchi[iq] the
+    dE/dchi0 array of each q."""
     iqs = list(range(len(problem.qpoints))) if iqs is None else list(iqs)
     sets = problem.sets
     gC = [np.zeros_like(s.C) for s in sets]
@@ -442,8 +446,12 @@ def energy_grad(problem, omega, W, Qs=None, iqs=None):
         Qflat = None if Qs is None else Qs[iq]
         gm = g_sphere(problem.cell, qp.q_red, problem.ecut_chi)
         ng = len(gm)
-        v = coulomb(problem.cell, qp.q_red, gm)
-        chi = chi0(problem, iq, omega, Qflat)
+        opt = None if optical is None else optical.get(iq)
+        v = coulomb(problem.cell, qp.q_red, gm, optical=opt is not None)
+        chi = chi0(problem, iq, omega, Qflat, optical=opt)
+        ig0 = -1
+        if opt is not None:
+            ig0 = int(np.flatnonzero(np.all(np.asarray(gm) == 0, axis=1))[0])
         e = ec_terms(chi, v)
         E += qp.weight * float(np.sum(np.asarray(W) * e)) / TWO_PI
         Gam = dE_dchi(chi, v, np.asarray(W), qp.weight)
@@ -452,12 +460,44 @@ def energy_grad(problem, omega, W, Qs=None, iqs=None):
             ik, ikp, G0 = int(qp.k_of[t]), int(qp.kq_of[t]), qp.G0[t]
             sk, skp = sets[ik], sets[ikp]
             n, nsel, msel = pair_block(sets, nproj, Qflat, gm, ik, ikp, G0)
+            if ig0 >= 0:
+                D = nabla_matrix(sk, problem.cell, opt[0], nsel, msel, nproj, opt[1])
+                n[ig0] = optical_head(D, sk.eps[nsel], sk.eps[msel])
             w = pair_weights(sk.eps[nsel], sk.f[nsel], skp.eps[msel], skp.f[msel], omega,
                              problem.spin_factor, problem.volume, problem.nk_bz)
             # dE/dn_p = 2 sum_j w_p(w_j) Gamma_j n_p
             nbar = np.zeros_like(n)
             for j in range(len(omega)):
                 nbar += 2.0 * np.einsum("gh,hab->gab", Gam[j], n) * w[None, :, :, j]
+            if ig0 >= 0:
+                # the head replaced the G = 0 pair densities: their adjoint runs
+                # through Eq. 12-13 only.  n0 = -i D / (e_m - e_n), so with
+                # b = i nbar(0) / (e_m - e_n), dE = Re sum conj(b) dD and
+                # D = i sum_Q conj(C_n) s C_m + sum_ij conj(P_ni) Qd_ij P_mj
+                dlt = sk.eps[msel][None, :] - sk.eps[nsel][:, None]
+                bmat = 1j * nbar[ig0] / dlt
+                nbar[ig0] = 0.0
+                qhat = np.asarray(opt[0], dtype=np.float64)
+                qhat = qhat / np.linalg.norm(qhat)
+                kQ = (np.asarray(sk.k_red, dtype=np.float64)[None, :] +
+                      np.asarray(sk.miller, dtype=np.float64)) @ reciprocal(problem.cell)
+                sv = kQ @ qhat
+                # g_{C_m}(Q) += sum_n -i b_nm s(Q) C_n(Q);  g_{C_n}(Q) += sum_m i conj(b_nm) s(Q) C_m(Q)
+                gC[ik][msel] += (-1j * bmat.T @ sk.C[nsel]) * sv[None, :]
+                gC[ik][nsel] += (1j * np.conj(bmat) @ sk.C[msel]) * sv[None, :]
+                if nproj is not None and opt[1] is not None and len(nproj):
+                    off = 0
+                    for a, ni in enumerate(np.asarray(nproj, dtype=np.int64)):
+                        ni = int(ni)
+                        Qd = np.einsum("d,dij->ij", qhat, np.asarray(opt[1][a]))
+                        cols = np.arange(off, off + ni)
+                        Pn = sk.P[nsel][:, off:off + ni]
+                        Pm = sk.P[msel][:, off:off + ni]
+                        # g_{P_mj} += sum_n b_nm sum_i P_ni conj(Qd_ij)
+                        gP[ik][np.ix_(msel, cols)] += bmat.T @ Pn @ np.conj(Qd)
+                        # g_{P_ni} += sum_m conj(b_nm) sum_j Qd_ij P_mj
+                        gP[ik][np.ix_(nsel, cols)] += np.conj(bmat) @ Pm @ Qd.T
+                        off += ni
             # through the pseudo pair density (Eq. 4): explicit adjoint of the plane-wave sum
             box, lo, hi = _index_box(np.asarray(skp.miller, dtype=np.int64))
             millk = np.asarray(sk.miller, dtype=np.int64)

@@ -97,3 +97,39 @@ def test_optical_coulomb_head():
     i0 = int(np.flatnonzero(np.all(gm == 0, axis=1))[0])
     assert v0[i0] == 0.0 and v1[i0] == 4 * np.pi
     assert np.array_equal(np.delete(v0, i0), np.delete(v1, i0))
+
+
+def test_optical_gradient_matches_central_differences():
+    """The gradient through the optical head (adjoint of Eqs. 12-13, plane-wave
+    and PAW parts) against central differences of the optical-limit energy,
+    in random C and P directions of both orbital sets of a q = 0 point."""
+    p = syn.small_problem(config_tag=98, a=5.0, grid=(10, 10, 10), ecut_wf=2.0, ecut_chi=1.2,
+                          nocc=2, nunocc=6, mesh=(2, 1, 1), nproj=(2, 3), nw=4)
+    iq = 0
+    assert np.all(p.qpoints[iq].q_red == 0)
+    Qs = {i: syn.paw_Q(p.paw, p.cell, qp.q_red, o.g_sphere(p.cell, qp.q_red, p.ecut_chi))
+          for i, qp in enumerate(p.qpoints)}
+    opt = {iq: ([0.3, 1.0, -0.4], syn.paw_Qnabla(p.paw, p.config))}
+    om, W = o.frequency_grid(4)
+    E0, gC, gP, _ = o.energy_grad(p, om, W, Qs, iqs=[iq], optical=opt)
+    Eref, _ = o.energy(p, om, W, Qs, iqs=[iq], optical=opt)
+    assert abs(E0 - Eref) <= 1e-14 * abs(Eref)
+    # the head matters: without the optical limit the energy and gradient differ
+    _, gC_plain, _, _ = o.energy_grad(p, om, W, Qs, iqs=[iq])
+    assert np.abs(gC[0] - gC_plain[0]).max() > 1e-3 * np.abs(gC[0]).max()
+    rng = np.random.default_rng(29)
+    h = 1e-6
+    for trial in range(8):
+        s = trial % len(p.sets)
+        which = "C" if trial < 4 else "P"
+        base = getattr(p.sets[s], which)
+        d = rng.standard_normal(base.shape) + 1j * rng.standard_normal(base.shape)
+        setattr(p.sets[s], which, base + h * d)
+        Ep, _ = o.energy(p, om, W, Qs, iqs=[iq], optical=opt)
+        setattr(p.sets[s], which, base - h * d)
+        Em, _ = o.energy(p, om, W, Qs, iqs=[iq], optical=opt)
+        setattr(p.sets[s], which, base)
+        fd = (Ep - Em) / (2 * h)
+        g = gC[s] if which == "C" else gP[s]
+        an = float(np.sum(np.conj(g) * d).real)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (which, s, fd, an)
