@@ -179,7 +179,8 @@ rpa_status rpa_set_paw_Q(rpa_ctx* ctx, int32_t iq, int32_t natoms,
  * and of |n_0|^2 cancel), so chi0 and E_c of iq include the head and wings.
  * qdir = NULL switches the limit off again (n(0) and v_0 = 0 of q = 0).  The
  * setting lasts until rpa_set_qpoint replaces iq.  rpa_energy_backward
- * returns RPA_ERR_STATE for a q-point with the optical limit. */
+ * differentiates through the head: the G = 0 part of dE/dn flows back through
+ * the dipole matrix of Eq. 13 into dE/dC and dE/dP (FP64). */
 rpa_status rpa_set_optical(rpa_ctx* ctx, int32_t iq, const double* qdir, int32_t natoms,
                            const int32_t* nproj, const double* Qgrad);
 
@@ -232,7 +233,18 @@ rpa_status rpa_energy_collect(rpa_ctx* ctx, const double* wq, const double* W,
  * buffers, then captures them into a graph.  rpa_graph_launch replays it on
  * that stream; afterwards call rpa_energy_collect on each context.  The
  * graph is bound to the contexts' buffers: do not change orbitals, q-points,
- * tuning or frequencies of those contexts while the graph is alive. */
+ * tuning or frequencies of those contexts while the graph is alive.
+ * When every context uses RPA_BF16X2 (RPA_TUNE_BATCH_PERSIST of ctxs[0] = 1,
+ * the default), the graph is built around persistent launches: the k-blocks
+ * of all contexts and q-points are packed, in order, into groups (at most
+ * RPA_TUNE_BATCH_MB, 16 GiB by default, of rank-k operands and 32 blocks
+ * each; a larger block alone); per group the pair densities and operand
+ * preparation of its blocks run into a graph-owned buffer, one persistent
+ * tensor-core launch (one CTA per SM)
+ * pulls every (block, tile, frequency) item of the group from a device queue,
+ * and the log-dets of the q-points completed by the group follow.  Results
+ * are bit-identical to the per-context form.  That buffer and the queue are
+ * allocated here and freed by rpa_graph_destroy. */
 typedef struct rpa_graph rpa_graph;
 rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq,
                             const int32_t* iqs, rpa_graph** out);
@@ -313,6 +325,52 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      accumulation to the PAW part of every pair density
  *                      (bulk workload, 39 projectors: E_c within 6.7e-7 of
  *                      FP64 instead of 2.6e-7).  Other modes ignore it.
+ * RPA_TUNE_TC_FUSE     RPA_BF16X2 with RPA_TUNE_TC_PIPE = 0: 0 (default)
+ *                      stores weighted bfloat16 operands for every frequency
+ *                      before the tensor-core kernel; 1 applies the frequency
+ *                      weights w_p(w) of Eq. 16 inside the kernel (one
+ *                      frequency-independent FP32 copy of the pair densities
+ *                      is staged, converter warps scale and split it in
+ *                      shared memory): 6x less operand memory and DRAM
+ *                      traffic, but the kernel is ~27% slower on GB300 (the
+ *                      conversion's shared-memory traffic competes with the
+ *                      tensor cores' operand reads).  Both give bit-identical
+ *                      chi0.
+ * RPA_TUNE_TC_WAIT_US  limit, in microseconds, of every wait of the
+ *                      tensor-core kernel on another role's progress, in
+ *                      [1000, 60000000]; default 4000000 (4 s).  A wait that
+ *                      runs out makes the call return RPA_ERR_TIMEOUT; the
+ *                      kernel first lets every load and product it issued
+ *                      finish, so the context stays usable.
+ * RPA_TUNE_TC_STALL    test of that path: 0 (default) off; k >= 1 makes the
+ *                      load role of every tensor-core CTA withhold its K
+ *                      stage k-1 and all later ones, so the waits run out.
+ * RPA_TUNE_PD_FUSE     0 (default): the middle- and fastest-axis transforms
+ *                      of the pair densities run as two kernels through
+ *                      global memory; 1: as one kernel per (pair, slab of
+ *                      first-axis outputs) through shared memory when a slab
+ *                      fits (48 KB), measured 8% slower on the bulk
+ *                      workload.  Bit-identical results.
+ * RPA_TUNE_BATCH_PERSIST  read from the first context of rpa_graph_create:
+ *                      1 (default) builds the graph of a batch whose
+ *                      contexts all use RPA_BF16X2 (same RPA_TUNE_TC_FUSE,
+ *                      RPA_TUNE_TC_PIPE = 0) around one persistent rank-k
+ *                      launch per group of k-blocks (one CTA per SM pulling
+ *                      (block, tile, frequency) items of every instance from
+ *                      a device queue); 0 captures each context's own
+ *                      sequence of launches.  Bit-identical results.
+ * RPA_TUNE_BATCH_MB    read from the first context of rpa_graph_create: the
+ *                      rank-k operand memory (MiB) of one group of that
+ *                      persistent form; default 16384.
+ * RPA_TUNE_GAMMA      dE/dchi0 = c_w v^1/2 [1 - (1 - M)^-1] v^1/2 of
+ *                      rpa_energy_backward in RPA_FP32, RPA_BF16X2 and
+ *                      RPA_BF16X3 (RPA_FP64 always uses FP64): 0 (default)
+ *                      from the Cholesky factor in FP64; 2 the same products
+ *                      in float-float on the FP32 pipe (about 44 bits); 1 the
+ *                      FP32 form -c_w v^1/2 M (1 - M)^-1 v^1/2, fastest but
+ *                      with ~1e-5 relative error in dE/dchi0 and ~3e-4 in
+ *                      dE/dC and dE/dP on the bulk gradient workload (FP64:
+ *                      <= 3e-6).
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -323,7 +381,14 @@ typedef enum {
   RPA_TUNE_TC_PIPE = 5,
   RPA_TUNE_LOGDET = 6,
   RPA_TUNE_PAW_TC = 7,
-  RPA_TUNE_COUNT = 8
+  RPA_TUNE_TC_FUSE = 8,
+  RPA_TUNE_TC_WAIT_US = 9,
+  RPA_TUNE_TC_STALL = 10,
+  RPA_TUNE_PD_FUSE = 11,
+  RPA_TUNE_BATCH_PERSIST = 12,
+  RPA_TUNE_BATCH_MB = 13,
+  RPA_TUNE_GAMMA = 14,
+  RPA_TUNE_COUNT = 15
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

@@ -12,6 +12,7 @@
 //  * Pair densities (Eq. 10): xbar(r) = (1/N_r) sum_G nbar(G) exp(+i (G+G0).r)
 //    by the transposed pruned transforms, ubar_m += xbar u_n,
 //    ubar_n += conj(xbar) u_m, and gC(Q) = sum_r exp(-i Q.r) ubar(r).
+#include "ff_math.cuh"
 #include "rpa_internal.h"
 
 namespace rpa {
@@ -26,28 +27,29 @@ __host__ __device__ inline int pmod_a(int64_t a, int n) {
   return (int)(r < 0 ? r + n : r);
 }
 
-// ---------------------------------------------------------------- complex FP64 GEMM
+// ---------------------------------------------------------------- complex GEMM (FP64 or FP32)
 // C[z] = beta C[z] + alpha opA(A[z]) B[z]; opA = 0: A is M x K (row-major, lda),
 // opA = 1: A is stored K x M and used conjugate-transposed.
 constexpr int ZT = 64, ZK = 16;
 
-__global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2 alpha, const double2* __restrict__ A,
-                                                    int64_t lda, int64_t sA, int opA, const double2* __restrict__ B,
-                                                    int64_t ldb, int64_t sB, double2 beta, double2* __restrict__ C,
+template <typename T>
+__global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, c2<T> alpha, const c2<T>* __restrict__ A,
+                                                    int64_t lda, int64_t sA, int opA, const c2<T>* __restrict__ B,
+                                                    int64_t ldb, int64_t sB, c2<T> beta, c2<T>* __restrict__ C,
                                                     int64_t ldc, int64_t sC) {
-  __shared__ double2 As[ZK][ZT];
-  __shared__ double2 Bs[ZK][ZT];
+  __shared__ c2<T> As[ZK][ZT];
+  __shared__ c2<T> Bs[ZK][ZT];
   const int z = blockIdx.z;
   A += z * sA;
   B += z * sB;
   C += z * sC;
   const int m0 = blockIdx.y * ZT, n0 = blockIdx.x * ZT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double2 acc[4][4];
+  c2<T> acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < 4; ++c) acc[r][c] = mk<T>(0, 0);
   for (int k0 = 0; k0 < K; k0 += ZK) {
 #pragma unroll
     for (int q = 0; q < (ZK * ZT) / 256; ++q) {
@@ -55,26 +57,26 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2
       // A tile: element (row m0+r, k k0+kk)
       {
         const int r = e / ZK, kk = e % ZK;
-        double2 v = make_double2(0.0, 0.0);
+        c2<T> v = mk<T>(0, 0);
         if (m0 + r < M && k0 + kk < K) {
           if (opA == 0) {
             v = A[(int64_t)(m0 + r) * lda + k0 + kk];
           } else {
-            const double2 t = A[(int64_t)(k0 + kk) * lda + m0 + r];
-            v = make_double2(t.x, -t.y);
+            const c2<T> t = A[(int64_t)(k0 + kk) * lda + m0 + r];
+            v = mk<T>(t.x, -t.y);
           }
         }
         As[kk][r] = v;
       }
       {
         const int kk = e / ZT, c = e % ZT;
-        Bs[kk][c] = (k0 + kk < K && n0 + c < N) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : make_double2(0.0, 0.0);
+        Bs[kk][c] = (k0 + kk < K && n0 + c < N) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : mk<T>(0, 0);
       }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < ZK; ++kk) {
-      double2 a[4], b[4];
+      c2<T> a[4], b[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
 #pragma unroll
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) cmac<double>(acc[r][c], a[r], b[c]);
+        for (int c = 0; c < 4; ++c) cmac<T>(acc[r][c], a[r], b[c]);
     }
     __syncthreads();
   }
@@ -92,10 +94,10 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2
     for (int c = 0; c < 4; ++c) {
       const int m = m0 + ty + 16 * r, n = n0 + tx + 16 * c;
       if (m < M && n < N) {
-        double2* p = C + (int64_t)m * ldc + n;
-        const double2 old = (beta.x == 0.0 && beta.y == 0.0) ? make_double2(0.0, 0.0) : *p;
-        const double2 a = acc[r][c];
-        double2 v;
+        c2<T>* p = C + (int64_t)m * ldc + n;
+        const c2<T> old = (beta.x == 0 && beta.y == 0) ? mk<T>(0, 0) : *p;
+        const c2<T> a = acc[r][c];
+        c2<T> v;
         v.x = beta.x * old.x - beta.y * old.y + alpha.x * a.x - alpha.y * a.y;
         v.y = beta.x * old.y + beta.y * old.x + alpha.x * a.y + alpha.y * a.x;
         *p = v;
@@ -103,13 +105,20 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2
     }
 }
 
+template <typename T>
+static cudaError_t launch_gemm_t(int M, int N, int K, c2<T> alpha, const c2<T>* A, int64_t lda, int64_t sA, int opA,
+                                 const c2<T>* B, int64_t ldb, int64_t sB, c2<T> beta, c2<T>* C, int64_t ldc, int64_t sC,
+                                 int batch, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT, batch);
+  zgemm_kernel<T><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, opA, B, ldb, sB, beta, C, ldc, sC);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2* A, int64_t lda, int64_t sA, int opA,
                          const double2* B, int64_t ldb, int64_t sB, double2 beta, double2* C, int64_t ldc,
                          int64_t sC, int batch, cudaStream_t s) {
-  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT, batch);
-  zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, opA, B, ldb, sB, beta, C, ldc, sC);
-  return cudaGetLastError();
+  return launch_gemm_t<double>(M, N, K, alpha, A, lda, sA, opA, B, ldb, sB, beta, C, ldc, sC, batch, s);
 }
 
 // W = Y^H Y for lower-triangular Y (Y = L^-1): W[i][j] = sum_{k >= max(i,j)}
@@ -123,35 +132,36 @@ __device__ __forceinline__ void lower_tile(int t, int& ti, int& tj) {
   tj = t - i * (i + 1) / 2;
 }
 
-__global__ void __launch_bounds__(256) yhy_lower_kernel(const double2* __restrict__ Y, int n, double2* __restrict__ W) {
-  __shared__ double2 As[ZK][ZT];
-  __shared__ double2 Bs[ZK][ZT];
+template <typename T>
+__global__ void __launch_bounds__(256) yhy_lower_kernel(const c2<T>* __restrict__ Y, int n, c2<T>* __restrict__ W) {
+  __shared__ c2<T> As[ZK][ZT];
+  __shared__ c2<T> Bs[ZK][ZT];
   const int z = blockIdx.y;
-  const double2* Yz = Y + (int64_t)z * n * n;
-  double2* Wz = W + (int64_t)z * n * n;
+  const c2<T>* Yz = Y + (int64_t)z * n * n;
+  c2<T>* Wz = W + (int64_t)z * n * n;
   int ti, tj;
   lower_tile(blockIdx.x, ti, tj);
   const int m0 = ti * ZT, n0 = tj * ZT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double2 acc[4][4];
+  c2<T> acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < 4; ++c) acc[r][c] = mk<T>(0, 0);
   for (int k0 = m0; k0 < n; k0 += ZK) {
 #pragma unroll
     for (int q = 0; q < (ZK * ZT) / 256; ++q) {
       const int e = threadIdx.x + 256 * q;
       const int kk = e / ZT, c = e % ZT;
       const bool kin = k0 + kk < n;
-      const double2 a = (kin && m0 + c < n) ? Yz[(int64_t)(k0 + kk) * n + m0 + c] : make_double2(0.0, 0.0);
-      As[kk][c] = make_double2(a.x, -a.y);
-      Bs[kk][c] = (kin && n0 + c < n) ? Yz[(int64_t)(k0 + kk) * n + n0 + c] : make_double2(0.0, 0.0);
+      const c2<T> a = (kin && m0 + c < n) ? Yz[(int64_t)(k0 + kk) * n + m0 + c] : mk<T>(0, 0);
+      As[kk][c] = mk<T>(a.x, -a.y);
+      Bs[kk][c] = (kin && n0 + c < n) ? Yz[(int64_t)(k0 + kk) * n + n0 + c] : mk<T>(0, 0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < ZK; ++kk) {
-      double2 a[4], b[4];
+      c2<T> a[4], b[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
 #pragma unroll
@@ -159,7 +169,7 @@ __global__ void __launch_bounds__(256) yhy_lower_kernel(const double2* __restric
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) cmac<double>(acc[r][c], a[r], b[c]);
+        for (int c = 0; c < 4; ++c) cmac<T>(acc[r][c], a[r], b[c]);
     }
     __syncthreads();
   }
@@ -175,47 +185,49 @@ __global__ void __launch_bounds__(256) yhy_lower_kernel(const double2* __restric
 // ---------------------------------------------------------------- (1 - M)^-1 from the Cholesky factor
 constexpr int FB = 32;
 
-__global__ void set_identity_kernel(double2* __restrict__ Y, int n, int nw) {
+template <typename T>
+__global__ void set_identity_kernel(c2<T>* __restrict__ Y, int n, int nw) {
   const int64_t total = (int64_t)nw * n * n;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(id % n);
     const int i = (int)((id / n) % n);
-    Y[id] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    Y[id] = mk<T>(i == j ? 1 : 0, 0);
   }
 }
 
 // Y[i0 .. i0+b) <- L_ii^-1 Y[i0 .. i0+b), one column of Y per thread.
-__global__ void __launch_bounds__(256) fwd_sub_diag_kernel(const double2* __restrict__ L, double2* __restrict__ Y,
+template <typename T>
+__global__ void __launch_bounds__(256) fwd_sub_diag_kernel(const c2<T>* __restrict__ L, c2<T>* __restrict__ Y,
                                                            int n, int i0, int b) {
-  __shared__ double2 Ld[FB][FB + 1];
+  __shared__ c2<T> Ld[FB][FB + 1];
   const int w = blockIdx.y;
-  const double2* Lw = L + (int64_t)w * n * n;
-  double2* Yw = Y + (int64_t)w * n * n;
+  const c2<T>* Lw = L + (int64_t)w * n * n;
+  c2<T>* Yw = Y + (int64_t)w * n * n;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int r = e / b, l = e % b;
-    Ld[r][l] = (l <= r) ? Lw[(int64_t)(i0 + r) * n + i0 + l] : make_double2(0.0, 0.0);
+    Ld[r][l] = (l <= r) ? Lw[(int64_t)(i0 + r) * n + i0 + l] : mk<T>(0, 0);
   }
   __syncthreads();
   // columns beyond the block are zero in these rows (Y is lower triangular)
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= i0 + b) return;
-  double2 y[FB];
+  c2<T> y[FB];
 #pragma unroll
-  for (int r = 0; r < FB; ++r) y[r] = (r < b) ? Yw[(int64_t)(i0 + r) * n + c] : make_double2(0.0, 0.0);
+  for (int r = 0; r < FB; ++r) y[r] = (r < b) ? Yw[(int64_t)(i0 + r) * n + c] : mk<T>(0, 0);
 #pragma unroll
   for (int r = 0; r < FB; ++r) {
     if (r < b) {
-      double2 s = y[r];
+      c2<T> s = y[r];
 #pragma unroll
       for (int l = 0; l < FB; ++l) {
         if (l < r) {
-          const double2 a = Ld[r][l], x = y[l];
+          const c2<T> a = Ld[r][l], x = y[l];
           s.x -= a.x * x.x - a.y * x.y;
           s.y -= a.x * x.y + a.y * x.x;
         }
       }
-      const double d = 1.0 / Ld[r][r].x;
-      y[r] = make_double2(s.x * d, s.y * d);
+      const T d = (T)1 / Ld[r][r].x;
+      y[r] = mk<T>(s.x * d, s.y * d);
     }
   }
 #pragma unroll
@@ -247,11 +259,255 @@ __global__ void gamma_kernel(const double2* __restrict__ Wm, const double* __res
   }
 }
 
+// ---------------------------------------------------------------- float-float products of Gamma
+// The two O(n^3) products of (1 - M)^-1 = L^-H L^-1 in float-float: inputs and
+// outputs FP64, each FP64 element split into hi + lo FP32 on load, every
+// complex multiply-add an exact FMA two-product with two-sum accumulation
+// (about 44 significant bits; the FP32 pipe instead of the FP64 one).
+// GRAM = false: C[z] = beta C[z] + alpha A[z] B[z] (A M x K, B K x N, row-major).
+// GRAM = true:  W[z] = Y^H Y on lower-triangle tiles, k from the tile's first
+// row (Y lower triangular).
+__device__ __forceinline__ void ffc_mac(float4& acc, float4 a, float4 b) {
+  // re += a.re b.re - a.im b.im, im += a.re b.im + a.im b.re
+  ff_mac(acc.x, acc.y, a.x, a.y, b.x, b.y);
+  ff_mac(acc.x, acc.y, -a.z, -a.w, b.z, b.w);
+  ff_mac(acc.z, acc.w, a.x, a.y, b.z, b.w);
+  ff_mac(acc.z, acc.w, a.z, a.w, b.x, b.y);
+}
+
+template <bool GRAM>
+__global__ void __launch_bounds__(256) gemm_ff_kernel(int M, int N, int K, double2 alpha, const double2* __restrict__ A,
+                                                      int64_t lda, int64_t sA, const double2* __restrict__ B,
+                                                      int64_t ldb, int64_t sB, double2 beta, double2* __restrict__ C,
+                                                      int64_t ldc, int64_t sC) {
+  __shared__ float4 As[ZK][ZT];
+  __shared__ float4 Bs[ZK][ZT];
+  const int z = GRAM ? blockIdx.y : blockIdx.z;
+  A += z * sA;
+  B += z * sB;
+  C += z * sC;
+  int m0, n0, kbeg = 0;
+  if constexpr (GRAM) {
+    int ti, tj;
+    lower_tile(blockIdx.x, ti, tj);
+    m0 = ti * ZT;
+    n0 = tj * ZT;
+    kbeg = m0;  // Y[k][i] = 0 for k < i
+  } else {
+    m0 = blockIdx.y * ZT;
+    n0 = blockIdx.x * ZT;
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float4 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k0 = kbeg; k0 < K; k0 += ZK) {
+#pragma unroll
+    for (int q = 0; q < (ZK * ZT) / 256; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int kk = e / ZT, c = e % ZT;
+      const bool kin = k0 + kk < K;
+      double2 a = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      if constexpr (GRAM) {
+        // A = Y^H: element (i = m0 + c, k) = conj(Y[k][i]); B = Y: (k, j = n0 + c)
+        if (kin && m0 + c < M) {
+          a = A[(int64_t)(k0 + kk) * lda + m0 + c];
+          a.y = -a.y;
+        }
+        if (kin && n0 + c < N) bv = B[(int64_t)(k0 + kk) * ldb + n0 + c];
+      } else {
+        if (kin && m0 + c < M) a = A[(int64_t)(m0 + c) * lda + k0 + kk];
+        if (kin && n0 + c < N) bv = B[(int64_t)(k0 + kk) * ldb + n0 + c];
+      }
+      As[kk][c] = ff_split(a);
+      Bs[kk][c] = ff_split(bv);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < ZK; ++kk) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ffc_mac(acc[r][c], a[r], b[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int m = m0 + ty + 16 * r, n = n0 + tx + 16 * c;
+      if (m >= M || n >= N || (GRAM && n > m)) continue;
+      double2* p = C + (int64_t)m * ldc + n;
+      const double2 a = ff_to_double(acc[r][c]);
+      const double2 old = (beta.x == 0.0 && beta.y == 0.0) ? make_double2(0.0, 0.0) : *p;
+      double2 v;
+      v.x = beta.x * old.x - beta.y * old.y + alpha.x * a.x - alpha.y * a.y;
+      v.y = beta.x * old.y + beta.y * old.x + alpha.x * a.y + alpha.y * a.x;
+      *p = v;
+    }
+}
+
+// Gamma as run_gamma with its two products in float-float.
+cudaError_t run_gamma_ff(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
+                         double2* G64, float2* G32, cudaStream_t s, int64_t* launches) {
+  cudaError_t e;
+  int64_t nl = 0;
+  set_identity_kernel<double><<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Y, n, nw);
+  ++nl;
+  for (int i0 = 0; i0 < n; i0 += FB) {
+    const int b = (n - i0) < FB ? (n - i0) : FB;
+    if (i0 > 0) {
+      // Y[i0:i0+b, 0:i0] -= L[i0:i0+b, 0:i0] Y[0:i0, 0:i0]
+      dim3 grid((i0 + ZT - 1) / ZT, (b + ZT - 1) / ZT, nw);
+      gemm_ff_kernel<false><<<grid, 256, 0, s>>>(b, i0, i0, make_double2(-1.0, 0.0), L + (int64_t)i0 * n, n,
+                                                 (int64_t)n * n, Y, n, (int64_t)n * n, make_double2(1.0, 0.0),
+                                                 Y + (int64_t)i0 * n, n, (int64_t)n * n);
+      ++nl;
+    }
+    fwd_sub_diag_kernel<double><<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
+    ++nl;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int nt = (n + ZT - 1) / ZT;
+  gemm_ff_kernel<true><<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(n, n, n, make_double2(1.0, 0.0), Y, n,
+                                                                    (int64_t)n * n, Y, n, (int64_t)n * n,
+                                                                    make_double2(0.0, 0.0), Wm, n, (int64_t)n * n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_hermitian_fill(Wm, nw, n, s)) != cudaSuccess) return e;
+  gamma_kernel<<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Wm, v, cw, n, nw, G64, G32);
+  nl += 4;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+// Mixed modes: L (FP64 lower factor) -> FP32 with a zero upper triangle.
+__global__ void lower_to32_kernel(const double2* __restrict__ L, int n, int nw, float2* __restrict__ L32) {
+  const int64_t total = (int64_t)nw * n * n;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % n);
+    const int i = (int)((id / n) % n);
+    const double2 v = L[id];
+    L32[id] = j <= i ? make_float2((float)v.x, (float)v.y) : make_float2(0.f, 0.f);
+  }
+}
+
+// M = v^1/2 chi v^1/2 in FP32 as a full Hermitian matrix from the lower triangle of chi.
+__global__ void m_from_chi_kernel(const double2* __restrict__ chi, const double* __restrict__ v, int n, int nw,
+                                  float2* __restrict__ M) {
+  const int64_t total = (int64_t)nw * n * n;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % n);
+    const int64_t r = id / n;
+    const int i = (int)(r % n);
+    const int w = (int)(r / n);
+    const double sc = sqrt(v[i]) * sqrt(v[j]);
+    double2 x;
+    if (j <= i) {
+      x = chi[id];
+    } else {
+      const double2 t = chi[((int64_t)w * n + j) * n + i];
+      x = make_double2(t.x, -t.y);
+    }
+    M[id] = make_float2((float)(sc * x.x), (float)(sc * x.y));
+  }
+}
+
+// W[i][j] = conj(W[j][i]) for j > i (FP32)
+__global__ void hermitian_fill32_kernel(float2* __restrict__ W, int n, int nw) {
+  const int64_t total = (int64_t)nw * n * n;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % n);
+    const int64_t r = id / n;
+    const int i = (int)(r % n);
+    const int w = (int)(r / n);
+    if (j > i) {
+      const float2 t = W[((int64_t)w * n + j) * n + i];
+      W[id] = make_float2(t.x, -t.y);
+    }
+  }
+}
+
+// Gamma = c_w v^1/2 [I - (1 - M)^-1] v^1/2 = -c_w v^1/2 M (1 - M)^-1 v^1/2: from
+// X = M W (W = (1 - M)^-1; X Hermitian in exact arithmetic), without the
+// cancellation of I - W when M is small (high frequencies).
+__global__ void gamma_mx_kernel(const float2* __restrict__ X, const double* __restrict__ v,
+                                const double* __restrict__ cw, int n, int nw, double2* __restrict__ G64,
+                                float2* __restrict__ G32) {
+  const int64_t total = (int64_t)nw * n * n;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % n);
+    const int64_t r = id / n;
+    const int i = (int)(r % n);
+    const int w = (int)(r / n);
+    const double s = -cw[w] * sqrt(v[i]) * sqrt(v[j]);
+    const float2 x = X[id];
+    const float2 xt = X[((int64_t)w * n + j) * n + i];
+    double re = 0.5 * ((double)x.x + (double)xt.x), im = 0.5 * ((double)x.y - (double)xt.y);
+    if (i == j) im = 0.0;
+    const double2 g = make_double2(s * re, s * im);
+    if (G64) G64[id] = g;
+    if (G32) G32[id] = make_float2((float)g.x, (float)g.y);
+  }
+}
+
+// The mixed-mode Gamma on the FP32 pipe: Y = L^-1 by the same blocked forward
+// substitution, W = Y^H Y, X = M W, Gamma from X.  (1 - M) >= 1 (chi0 <= 0), so
+// L has a unit-bounded inverse and FP32 keeps about 1e-6 relative accuracy.
+// Scratch: Yb and Wb of nw n^2 complex FP64 each, used as two FP32 matrices
+// apiece; G32 holds the FP32 factor until Gamma overwrites it.
+cudaError_t run_gamma_mixed(const double2* L, const double2* chi, const double* v, const double* cw, int nw, int n,
+                            double2* Yb, double2* Wb, double2* G64, float2* G32, cudaStream_t s, int64_t* launches) {
+  cudaError_t e;
+  int64_t nl = 0;
+  const int64_t mat = (int64_t)nw * n * n;
+  float2* Y = (float2*)Yb;
+  float2* Mm = Y + mat;
+  float2* W = (float2*)Wb;
+  float2* X = W + mat;
+  float2* L32 = G32;
+  lower_to32_kernel<<<gridx(mat), 256, 0, s>>>(L, n, nw, L32);
+  m_from_chi_kernel<<<gridx(mat), 256, 0, s>>>(chi, v, n, nw, Mm);
+  set_identity_kernel<float><<<gridx(mat), 256, 0, s>>>(Y, n, nw);
+  nl += 3;
+  for (int i0 = 0; i0 < n; i0 += FB) {
+    const int b = (n - i0) < FB ? (n - i0) : FB;
+    if (i0 > 0) {
+      if ((e = launch_gemm_t<float>(b, i0, i0, make_float2(-1.f, 0.f), L32 + (int64_t)i0 * n, n, (int64_t)n * n, 0,
+                                    Y, n, (int64_t)n * n, make_float2(1.f, 0.f), Y + (int64_t)i0 * n, n,
+                                    (int64_t)n * n, nw, s)) != cudaSuccess)
+        return e;
+      ++nl;
+    }
+    fwd_sub_diag_kernel<float><<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L32, Y, n, i0, b);
+    ++nl;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int nt = (n + ZT - 1) / ZT;
+  yhy_lower_kernel<float><<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(Y, n, W);
+  hermitian_fill32_kernel<<<gridx(mat), 256, 0, s>>>(W, n, nw);
+  nl += 2;
+  if ((e = launch_gemm_t<float>(n, n, n, make_float2(1.f, 0.f), Mm, n, (int64_t)n * n, 0, W, n, (int64_t)n * n,
+                                make_float2(0.f, 0.f), X, n, (int64_t)n * n, nw, s)) != cudaSuccess)
+    return e;
+  gamma_mx_kernel<<<gridx(mat), 256, 0, s>>>(X, v, cw, n, nw, G64, G32);
+  nl += 2;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
 cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
                       double2* G64, float2* G32, cudaStream_t s, int64_t* launches) {
   cudaError_t e;
   int64_t nl = 0;
-  set_identity_kernel<<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Y, n, nw);
+  set_identity_kernel<double><<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Y, n, nw);
   ++nl;
   for (int i0 = 0; i0 < n; i0 += FB) {
     const int b = (n - i0) < FB ? (n - i0) : FB;
@@ -263,14 +519,14 @@ cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int n
         return e;
       ++nl;
     }
-    fwd_sub_diag_kernel<<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
+    fwd_sub_diag_kernel<double><<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
     ++nl;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // W = Y^H Y = L^-H L^-1 = (1 - M)^-1: lower tiles, then the upper triangle by symmetry
   {
     const int nt = (n + ZT - 1) / ZT;
-    yhy_lower_kernel<<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(Y, n, Wm);
+    yhy_lower_kernel<double><<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(Y, n, Wm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_hermitian_fill(Wm, nw, n, s)) != cudaSuccess) return e;
     nl += 2;

@@ -177,6 +177,173 @@ cudaError_t launch_optical_head(const double2* C, int npw, const double* s, cons
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- adjoint of the head
+// The head n0_nm = -i D_nm / (e_m - e_n) replaced the G = 0 pair densities, so
+// dE/dn0 (the G = 0 column of Nbar) flows back through the dipole matrix D of
+// Eq. 13 instead of the transforms and the PAW term.  With
+//   b_nm = i Nbar_nm(0) / (e_m - e_n),   dE = Re sum conj(b) dD,
+// the PyTorch-convention gradients (g = 2 dE/dconj(z)) are
+//   g_C_m(Q) += sum_n -i b_nm s(Q) C_n(Q),    g_C_n(Q) += sum_m i conj(b_nm) s(Q) C_m(Q),
+//   g_P_mj += sum_n b_nm sum_i P_ni conj(Qn_ij),  g_P_ni += sum_m conj(b_nm) sum_j Qn_ij P_mj,
+// all FP64.
+
+// b[a][r] = i Nbar[(a nR + r) NG + ig0] / (e_R[r] - e_L[a]); that Nbar column is cleared
+template <typename T>
+__global__ void optical_adj_b_kernel(c2<T>* __restrict__ Nbar, int NG, int ig0, const int* __restrict__ L, int nL,
+                                     const int* __restrict__ R, int nR, const double* __restrict__ eps,
+                                     double2* __restrict__ bm) {
+  const int64_t total = (int64_t)nL * nR;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(id / nR), r = (int)(id % nR);
+    const c2<T> nb = Nbar[id * NG + ig0];
+    const double de = eps[R[r]] - eps[L[a]];
+    bm[id] = make_double2(-(double)nb.y / de, (double)nb.x / de);  // i nb / de
+    Nbar[id * NG + ig0] = mk<T>(0, 0);
+  }
+}
+
+// out[ro(i) ldo + j] += sum_k coef(i, k) op_x(X[rx(k) sxk + j sxj]) sc(j), i < M, j < N, k < K,
+// coef(i, k) = mult op_a(A[ra(i) sai + k sak]); ro, ra, rx are optional row
+// lists, op_* an optional conjugation, sc an optional real column scale.
+struct AdjGemm {
+  double2* out;
+  const int* ro;
+  int64_t ldo;
+  const double2* A;
+  const int* ra;
+  int64_t sai, sak;
+  double2 mult;
+  int conj_a;
+  const double2* X;
+  const int* rx;
+  int64_t sxk, sxj;
+  int conj_x;
+  const double* sc;
+  int M, N, K;
+};
+
+__global__ void __launch_bounds__(256) optical_adj_gemm_kernel(const AdjGemm g) {
+  __shared__ double2 As[16][17];
+  __shared__ double2 Xs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    {
+      // coefficient tile: row i0 + ty, column k0 + tx
+      const int k = k0 + tx;
+      double2 v = make_double2(0.0, 0.0);
+      if (i < g.M && k < g.K) {
+        const int64_t r = g.ra ? g.ra[i] : i;
+        v = g.A[r * g.sai + (int64_t)k * g.sak];
+        if (g.conj_a) v.y = -v.y;
+        v = make_double2(g.mult.x * v.x - g.mult.y * v.y, g.mult.x * v.y + g.mult.y * v.x);
+      }
+      As[ty][tx] = v;
+    }
+    {
+      // X tile: row k0 + ty, column j0 + tx
+      const int k = k0 + ty;
+      double2 v = make_double2(0.0, 0.0);
+      if (k < g.K && j < g.N) {
+        const int64_t r = g.rx ? g.rx[k] : k;
+        v = g.X[r * g.sxk + (int64_t)j * g.sxj];
+        if (g.conj_x) v.y = -v.y;
+      }
+      Xs[ty][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) cmac<double>(acc, As[ty][kk], Xs[kk][tx]);
+    __syncthreads();
+  }
+  if (i < g.M && j < g.N) {
+    const double f = g.sc ? g.sc[j] : 1.0;
+    double2* o = g.out + (g.ro ? (int64_t)g.ro[i] : (int64_t)i) * g.ldo + j;
+    double2 v = *o;
+    v.x += f * acc.x;
+    v.y += f * acc.y;
+    *o = v;
+  }
+}
+
+static cudaError_t adj_gemm(const AdjGemm& g, cudaStream_t st) {
+  if (g.M == 0 || g.N == 0 || g.K == 0) return cudaSuccess;
+  dim3 grid((g.N + 15) / 16, (g.M + 15) / 16);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  optical_adj_gemm_kernel<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+int64_t optical_adj_scratch_elems(int nL, int nR, int KP) { return (int64_t)nL * nR + (int64_t)(nL + nR) * KP; }
+
+template <typename T>
+cudaError_t launch_optical_adjoint(c2<T>* Nbar, int NG, int ig0, const int* L, int nL, const int* R, int nR,
+                                   const double* eps, const double2* C, int npw, const double* s, const double2* P,
+                                   int KP, const double2* Qn, double2* scratch, double2* gC, double2* gP,
+                                   cudaStream_t st) {
+  if (nL == 0 || nR == 0) return cudaSuccess;
+  double2* bm = scratch;                       // [nL][nR]
+  double2* Y = bm + (int64_t)nL * nR;          // [nL][KP]
+  double2* Z = Y + (int64_t)nL * KP;           // [nR][KP]
+  {
+    const int64_t total = (int64_t)nL * nR;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    optical_adj_b_kernel<T><<<blocks, 256, 0, st>>>(Nbar, NG, ig0, L, nL, R, nR, eps, bm);
+  }
+  const double2 one = make_double2(1.0, 0.0), mi = make_double2(0.0, -1.0), pi = make_double2(0.0, 1.0);
+  cudaError_t e;
+  // g_C_m(Q) += sum_n -i b_nm s(Q) C_n(Q): rows R, coef(r, a) = -i b[a][r]
+  if ((e = adj_gemm({gC, R, npw, bm, nullptr, 1, nR, mi, 0, C, L, npw, 1, 0, s, nR, npw, nL}, st)) != cudaSuccess)
+    return e;
+  // g_C_n(Q) += sum_m i conj(b_nm) s(Q) C_m(Q): rows L, coef(a, r) = i conj(b[a][r])
+  if ((e = adj_gemm({gC, L, npw, bm, nullptr, nR, 1, pi, 1, C, R, npw, 1, 0, s, nL, npw, nR}, st)) != cudaSuccess)
+    return e;
+  if (P && Qn && gP && KP > 0) {
+    if ((e = cudaMemsetAsync(Y, 0, sizeof(double2) * (size_t)(nL + nR) * KP, st)) != cudaSuccess) return e;
+    // Y[a][j] = sum_i P[L[a]][i] conj(Qn[i][j])
+    if ((e = adj_gemm({Y, nullptr, KP, P, L, KP, 1, one, 0, Qn, nullptr, KP, 1, 1, nullptr, nL, KP, KP}, st)) !=
+        cudaSuccess)
+      return e;
+    // g_P[R[r]][j] += sum_a b[a][r] Y[a][j]
+    if ((e = adj_gemm({gP, R, KP, bm, nullptr, 1, nR, one, 0, Y, nullptr, KP, 1, 0, nullptr, nR, KP, nL}, st)) !=
+        cudaSuccess)
+      return e;
+    // Z[r][i] = sum_j P[R[r]][j] Qn[i][j]
+    if ((e = adj_gemm({Z, nullptr, KP, P, R, KP, 1, one, 0, Qn, nullptr, 1, KP, 0, nullptr, nR, KP, KP}, st)) !=
+        cudaSuccess)
+      return e;
+    // g_P[L[a]][i] += sum_r conj(b[a][r]) Z[r][i]
+    if ((e = adj_gemm({gP, L, KP, bm, nullptr, nR, 1, one, 1, Z, nullptr, KP, 1, 0, nullptr, nL, KP, nR}, st)) !=
+        cudaSuccess)
+      return e;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_optical_adjoint<float>(float2*, int, int, const int*, int, const int*, int, const double*,
+                                                   const double2*, int, const double*, const double2*, int,
+                                                   const double2*, double2*, double2*, double2*, cudaStream_t);
+template cudaError_t launch_optical_adjoint<double>(double2*, int, int, const int*, int, const int*, int,
+                                                    const double*, const double2*, int, const double*, const double2*,
+                                                    int, const double2*, double2*, double2*, double2*, cudaStream_t);
+
+// dst[i] += src[i]
+__global__ void add_c128_kernel(double2* __restrict__ dst, const double2* __restrict__ src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    dst[i].x += src[i].x;
+    dst[i].y += src[i].y;
+  }
+}
+
+cudaError_t launch_add_c128(double2* dst, const double2* src, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  add_c128_kernel<<<blocks, 256, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_optical_head<float>(const double2*, int, const double*, const double2*, int,
                                                 const double2*, double2*, const int*, int, const int*, int,
                                                 const double*, int, int, float2*, cudaStream_t);

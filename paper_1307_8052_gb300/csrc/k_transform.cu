@@ -18,6 +18,8 @@
 // integer arithmetic, so no angle is ever rounded before the table lookup.
 #include "rpa_internal.h"
 
+#include <algorithm>
+
 namespace rpa {
 
 static inline int grid_for(int64_t n, int threads) {
@@ -500,6 +502,140 @@ __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict_
   }
 }
 
+// ---------------------------------------------------------------- pair density stages B + C fused
+// One block per (pair, slab of OB first-axis outputs o1): the middle-axis DFT
+// of the slab goes to shared memory,
+//   T2[o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i g2 j2 / N2),
+// and the fastest axis is then evaluated on the sphere points whose g1 lies in
+// the slab (a contiguous range of the Miller-ordered sphere, g1start),
+//   N[p][G] = (1/N_r) sum_j3 T2[o1(G)][o2(G)][j3] exp(-2 pi i g3 j3 / N3),
+// written along G.  Same products in the same order as stage B followed by
+// stage C (bit-identical), without the global round trip of T2 and with the
+// fastest-axis lines read from shared memory.
+template <typename T, int NO>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) pd_stageBC_kernel(const c2<T>* __restrict__ T1, int np, int n1, int N2, int N3,
+                                                         const c2<T>* __restrict__ twg, int n2,
+                                                         const int* __restrict__ gfft,
+                                                         const int* __restrict__ g1start, int OB, int NG, int g1lo,
+                                                         int g2lo, double inv_nr, int64_t p0,
+                                                         c2<T>* __restrict__ Nout) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw2 = reinterpret_cast<c2<T>*>(smem_raw);  // [N2][TS], outputs o2 < n2 <= NO
+  c2<T>* tw3 = tw2 + N2 * TS;                         // exp(2 pi i t / N3)
+  c2<T>* T2s = tw3 + N3;                              // [OB][n2][N3]
+  for (int e = threadIdx.x; e < N2 * TS; e += blockDim.x) tw2[e] = twg[e];
+  fill_twiddles<T>(tw3, N3);  // ends with a block barrier
+  const int nslab = (n1 + OB - 1) / OB;
+  const T scale = (T)inv_nr;
+  for (int64_t item = blockIdx.x; item < (int64_t)np * nslab; item += gridDim.x) {
+    const int pl = (int)(item / nslab);
+    const int o1a = (int)(item % nslab) * OB;
+    const int ob = min(OB, n1 - o1a);
+    for (int cidx = threadIdx.x; cidx < ob * N3; cidx += blockDim.x) {
+      const int r = cidx / N3, j3 = cidx % N3;
+      const c2<T>* src = T1 + ((int64_t)pl * n1 + o1a + r) * N2 * N3 + j3;
+      c2<T> acc[NO];
+#pragma unroll
+      for (int t = 0; t < NO; ++t) acc[t] = mk<T>(0, 0);
+      // the middle-axis line in slices of 4: four independent loads in
+      // flight before their multiply-adds (the line is strided by N3); in
+      // FP32 at most 64 registers, so two 512-thread blocks fit on an SM
+      for (int jb = 0; jb < N2; jb += 4) {
+        c2<T> x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = jb + u < N2 ? src[(int64_t)(jb + u) * N3] : mk<T>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (jb + u < N2) {
+            const c2<T>* twj = tw2 + (jb + u) * TS;
+#pragma unroll
+            for (int t = 0; t < NO; ++t) cmac<T>(acc[t], x[u], twj[t]);
+          }
+        }
+      }
+      c2<T>* dst = T2s + (int64_t)r * n2 * N3 + j3;
+#pragma unroll
+      for (int t = 0; t < NO; ++t)
+        if (t < n2) dst[(int64_t)t * N3] = acc[t];
+    }
+    __syncthreads();
+    const int gs = g1start[o1a], ge = g1start[o1a + ob];
+    for (int ig = gs + threadIdx.x; ig < ge; ig += blockDim.x) {
+      const int g1 = gfft[3 * ig], g2 = gfft[3 * ig + 1], g3 = gfft[3 * ig + 2];
+      const c2<T>* line = T2s + ((int64_t)(g1 - g1lo - o1a) * n2 + (g2 - g2lo)) * N3;
+      const int step = pmod(-(int64_t)g3, N3);
+      c2<T> acc = mk<T>(0, 0);
+      int idx = 0;
+      for (int j3 = 0; j3 < N3; ++j3) {
+        cmac<T>(acc, line[j3], tw3[idx]);
+        idx += step;
+        if (idx >= N3) idx -= N3;
+      }
+      Nout[(p0 + pl) * NG + ig] = mk<T>(acc.x * scale, acc.y * scale);
+    }
+    __syncthreads();
+  }
+}
+
+// g1start[o] = the first sphere point with g1 - g1lo >= o, o in [0, n1]
+// (the sphere is sorted by g1; binary search per o).
+__global__ void g1start_kernel(const int* __restrict__ gfft, int NG, int g1lo, int n1, int* __restrict__ out) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o <= n1; o += gridDim.x * blockDim.x) {
+    int lo = 0, hi = NG;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (gfft[3 * mid] - g1lo < o) lo = mid + 1;
+      else hi = mid;
+    }
+    out[o] = lo;
+  }
+}
+
+cudaError_t launch_g1start(const int* gfft, int NG, int g1lo, int n1, int* out, cudaStream_t s) {
+  g1start_kernel<<<(n1 + 1 + 127) / 128, 128, 0, s>>>(gfft, NG, g1lo, n1, out);
+  return cudaGetLastError();
+}
+
+// Slab height OB of the fused kernel: the largest that keeps its shared
+// memory within 48 KB (0 if even one first-axis output does not fit, or the
+// middle axis has more than 16 outputs).
+template <typename T>
+int pd_stageBC_slab(int n1, int n2, int N2, int N3) {
+  if (n2 > TS) return 0;
+  const int64_t fixed = ((int64_t)N2 * TS + N3) * (int64_t)sizeof(c2<T>);
+  const int64_t per = (int64_t)n2 * N3 * (int64_t)sizeof(c2<T>);
+  const int64_t room = 48 * 1024 - fixed;
+  if (room < per) return 0;
+  return (int)std::min<int64_t>(n1, room / per);
+}
+
+template <typename T, int NO>
+static cudaError_t launch_stageBC_no(const c2<T>* T1, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
+                                     const int* gfft, const int* g1start, int OB, int NG, int g1lo, int g2lo,
+                                     double inv_nr, int64_t p0, c2<T>* Nout, cudaStream_t s) {
+  const int nslab = (n1 + OB - 1) / OB;
+  const int64_t items = (int64_t)np * nslab;
+  const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, ((int64_t)OB * N3 + 31) / 32 * 32));
+  const size_t smem = ((size_t)N2 * TS + N3 + (size_t)OB * n2 * N3) * sizeof(c2<T>);
+  const int blocks = (int)std::min<int64_t>(items, 152 * 16);
+  pd_stageBC_kernel<T, NO><<<blocks, threads, smem, s>>>(T1, np, n1, N2, N3, tw, n2, gfft, g1start, OB, NG, g1lo, g2lo,
+                                                         inv_nr, p0, Nout);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pd_stageBC(const c2<T>* T1, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
+                              const int* gfft, const int* g1start, int OB, int NG, int g1lo, int g2lo, double inv_nr,
+                              int64_t p0, c2<T>* Nout, cudaStream_t s) {
+  if (np == 0 || OB < 1) return cudaSuccess;
+  switch (width_for(n2)) {
+    case 8: return launch_stageBC_no<T, 8>(T1, np, n1, N2, N3, tw, n2, gfft, g1start, OB, NG, g1lo, g2lo, inv_nr, p0, Nout, s);
+    case 12: return launch_stageBC_no<T, 12>(T1, np, n1, N2, N3, tw, n2, gfft, g1start, OB, NG, g1lo, g2lo, inv_nr, p0, Nout, s);
+    case 14: return launch_stageBC_no<T, 14>(T1, np, n1, N2, N3, tw, n2, gfft, g1start, OB, NG, g1lo, g2lo, inv_nr, p0, Nout, s);
+    default: return launch_stageBC_no<T, 16>(T1, np, n1, N2, N3, tw, n2, gfft, g1start, OB, NG, g1lo, g2lo, inv_nr, p0, Nout, s);
+  }
+}
+
 // ---------------------------------------------------------------- PAW term (Eq. 6, steps 8-9)
 // N[(a nR + b) NG + g] += sum_kp Pm[b][kp] R[a][kp][g] for every occupied row a
 // of the block: one complex GEMM (nR x KP) x (KP x NG) per a, 64 x 64 tiles,
@@ -680,6 +816,9 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
   template cudaError_t launch_twiddle_matrix<T>(c2<T>*, int, int, int, cudaStream_t);                             \
   template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
                                            int, int64_t, int, const c2<T>*, int, c2<T>*, cudaStream_t);          \
+  template cudaError_t launch_pd_stageBC<T>(const c2<T>*, int, int, int, int, const c2<T>*, int, const int*,     \
+                                             const int*, int, int, int, int, double, int64_t, c2<T>*, cudaStream_t); \
+  template int pd_stageBC_slab<T>(int, int, int, int);                                                            \
   template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \
                                            int64_t, c2<T>*, cudaStream_t);                                       \
   template cudaError_t launch_paw_gemm<T>(const c2<T>*, const c2<T>*, int, int, int, int, c2<T>*, cudaStream_t); \

@@ -20,11 +20,19 @@
 namespace rpa {
 // tensor-core rank-k update (k_herk_tc.cu): operand preparation (bf16 split of
 // the weighted and plain pair densities into scratch), then the tcgen05 kernel
-cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms,
+cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms, int fused,
                             void* scratch, size_t scratch_bytes, cudaStream_t s);
-cudaError_t herk_tc_run(int64_t P, int NG, int nw, int split_terms, int fold_stages, int flush_folds, int pipe,
-                        double2* chi, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
-size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms);
+cudaError_t herk_tc_run(int64_t P, int NG, int nw, int split_terms, int fused, int fold_stages, int flush_folds, int pipe,
+                        int64_t wait_us, int stall_stage, double2* chi, void* scratch, size_t scratch_bytes, int* err,
+                        cudaStream_t s);
+size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms, int fused);
+// persistent launch of many two-term k-blocks (k_herk_tc.cu)
+int herk_tc_batch_max_jobs();
+cudaError_t herk_tc_batch_run(int njobs, const int64_t* P, const int* NG, const int* nw, void* const* scratch,
+                              const size_t* scratch_bytes, const int* unit_of, double2* const* chi, int fused,
+                              int fold_stages, int flush_folds, int64_t wait_us, int* queue, int* err,
+                              cudaStream_t s);
+cudaError_t launch_or_flags(const int* src, int* const* dst, int n, cudaStream_t s);
 // adjoint product 2 sum_w w N conj(Gam_w) on the tensor cores (k_herk_tc.cu)
 size_t nbar_tc_gam_bytes(int NG, int nw, int terms);
 size_t nbar_tc_a_bytes(int64_t P, int NG, int terms);
@@ -38,6 +46,10 @@ cudaError_t paw_tc_run(const float2* Pm, const float2* R, int KP, int nL, int nR
 // adjoint kernels (k_adjoint.cu)
 cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
                       double2* G64, float2* G32, cudaStream_t s, int64_t* launches);
+cudaError_t run_gamma_mixed(const double2* L, const double2* chi, const double* v, const double* cw, int nw, int n,
+                            double2* Yb, double2* Wb, double2* G64, float2* G32, cudaStream_t s, int64_t* launches);
+cudaError_t run_gamma_ff(const double2* L, const double* v, const double* cw, int nw, int n, double2* Y, double2* Wm,
+                         double2* G64, float2* G32, cudaStream_t s, int64_t* launches);
 template <typename T>
 cudaError_t launch_nbar(const c2<T>* N, int64_t P, int NG, const T* wgt, const c2<T>* Gam, int nw, c2<T>* Nbar,
                         cudaStream_t s);
@@ -119,7 +131,8 @@ struct QPt {
   int ig0 = -1;                 // index of G = 0 in the sphere
   double2* Qn_d = nullptr;      // q^.Qgrad as a dense block-diagonal [KPo][KPo], or null
   int KPo = 0;
-  std::map<int, double*> s_d;   // per orbital set: q^.(k+Q) of its plane waves
+  std::map<int, double*> s_d;   // per orbital set: q^.(k+Q) of its plane waves (made on first use)
+  double qhat[3] = {0, 0, 0};   // the normalised direction q^
 };
 
 
@@ -149,7 +162,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 0};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -199,6 +212,33 @@ void free_optical(QPt& Q) {
   Q.s_d.clear();
   Q.optical = false;
   Q.KPo = 0;
+}
+
+// q^.(k+Q) of every plane wave of orbital set id (Cartesian, B rows) for the
+// optical limit of Q, uploaded on first use; rpa_set_orbitals drops it when
+// the set's plane waves change.
+rpa_status optical_s(rpa_ctx* c, QPt& Q, int id, const double** out) {
+  auto it = Q.s_d.find(id);
+  if (it != Q.s_d.end()) {
+    *out = it->second;
+    return RPA_OK;
+  }
+  const OrbSet& os = c->sets[id];
+  const double* B = c->B;
+  std::vector<double> sv(os.npw);
+  for (int g = 0; g < os.npw; ++g) {
+    const double r[3] = {os.k[0] + os.miller[3 * g], os.k[1] + os.miller[3 * g + 1], os.k[2] + os.miller[3 * g + 2]};
+    double acc = 0.0;
+    for (int d = 0; d < 3; ++d) acc += Q.qhat[d] * (r[0] * B[d] + r[1] * B[3 + d] + r[2] * B[6 + d]);
+    sv[g] = acc;
+  }
+  double* sd = nullptr;
+  rpa_status st = dev_alloc(c, (void**)&sd, sizeof(double) * os.npw);
+  if (st != RPA_OK) return st;
+  Q.s_d[id] = sd;
+  CUDA_OK(c, cudaMemcpy(sd, sv.data(), sizeof(double) * os.npw, cudaMemcpyHostToDevice));
+  *out = sd;
+  return RPA_OK;
 }
 
 rpa_status workspace(rpa_ctx* c, const char* name, size_t bytes, void** out) {
@@ -426,12 +466,26 @@ struct Block {
 // Occupied-band rows [a0, a1) of a transition form one block: the pair
 // rectangle is always whole rows x all empty bands, so every kernel sees a
 // plain (nL x nR) rectangle.  Rows per block bound the N and operand buffers.
+// The fused weighting of the tensor-core update applies (two terms, default
+// pipeline shape, not switched off).
+bool tc_fused(const rpa_ctx* c) {
+  return c->prm.precision == RPA_BF16X2 && c->tune[RPA_TUNE_TC_FUSE] == 1 && c->tune[RPA_TUNE_TC_PIPE] == 0;
+}
+
+// herk_tc_run with the context's knobs
+cudaError_t run_herk_tc(rpa_ctx* c, int64_t P, int NG, int nw, int terms, double2* chi, void* scr, size_t sb) {
+  return herk_tc_run(P, NG, nw, terms, tc_fused(c) ? 1 : 0, (int)c->tune[RPA_TUNE_TC_FOLD],
+                     (int)c->tune[RPA_TUNE_TC_FLUSH], (int)c->tune[RPA_TUNE_TC_PIPE], c->tune[RPA_TUNE_TC_WAIT_US],
+                     (int)c->tune[RPA_TUNE_TC_STALL] - 1, chi, scr, sb, c->dev_err, c->stream);
+}
+
 int rows_per_block(const rpa_ctx* c, int nL, int nR, int NG, int nw) {
   const int64_t NGpad = (NG + 127) / 128 * 128;
-  // tensor-core operands: NGpad * 2P * terms * 2 B * (nw + 2); pair densities: P * NG * 8-16 B
+  // tensor-core operands: NGpad * 2P * terms * 2 B * (nw + 2), or with the
+  // fused weighting NGpad * 2P * (2 terms * 2 B * 2 + 4 B); pair densities: P * NG * 8-16 B
   const int64_t budget = c->tune[RPA_TUNE_OPERAND_MB] << 20;
   const int64_t terms = c->prm.precision == RPA_BF16X3 ? 3 : 2;
-  int64_t pmax = budget / (NGpad * 4 * terms * (nw + 2));
+  int64_t pmax = tc_fused(c) ? budget / (NGpad * 24) : budget / (NGpad * 4 * terms * (nw + 2));
   if (c->prm.precision == RPA_FP64 || c->prm.precision == RPA_FP32) pmax = budget / (16 * (int64_t)NG);
   int64_t rows = std::max<int64_t>(1, pmax / std::max(1, nR));
   return (int)std::min<int64_t>(rows, nL);
@@ -542,10 +596,27 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
     StageTimer tm(c, 1, 2);
     CUDA_OK(c, launch_twiddle_matrix<T>((c2<T>*)p_twA, N1, glo[0], n1, c->stream));
     CUDA_OK(c, launch_twiddle_matrix<T>((c2<T>*)p_twB, N2, glo[1], n2, c->stream));
+    // stages B and C fused when a slab of the middle-axis output fits in
+    // shared memory and the sphere is ordered by g1 (Miller order)
+    int OB = c->tune[RPA_TUNE_PD_FUSE] == 1 ? pd_stageBC_slab<T>(n1, n2, N2, N3) : 0;
+    for (int i = 1; OB > 0 && i < NG; ++i)
+      if (gfft[3 * i] < gfft[3 * (i - 1)]) OB = 0;
+    void* p_g1s = nullptr;
+    if (OB > 0) {
+      if ((st = workspace(c, "pd_g1start", sizeof(int) * (size_t)(n1 + 1), &p_g1s)) != RPA_OK) return st;
+      CUDA_OK(c, launch_g1start((const int*)p_gfft, NG, glo[0], n1, (int*)p_g1s, c->stream));
+    }
     for (int64_t p0 = 0; p0 < P; p0 += PC) {
       const int np = (int)std::min<int64_t>(PC, P - p0);
       CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d, nR,
                                      p0, np, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
+      if (OB > 0) {
+        CUDA_OK(c, launch_pd_stageBC<T>((const c2<T>*)p_T1, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
+                                        (const int*)p_gfft, (const int*)p_g1s, OB, NG, glo[0], glo[1],
+                                        1.0 / (double)Nr, p0, (c2<T>*)p_N, c->stream));
+        tm.add_launches(2);
+        continue;
+      }
       CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                      c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
@@ -582,8 +653,10 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
     void* p_y = nullptr;
     const size_t ob = sizeof(double2) * (size_t)optical_scratch_elems(nL, nR, sk.npw, pawo ? Q.KPo : 0);
     if ((st = workspace(c, "optical_scratch", ob, &p_y)) != RPA_OK) return st;
+    const double* sd;
+    if ((st = optical_s(c, Q, Q.k_of[t], &sd)) != RPA_OK) return st;
     StageTimer tm(c, 1, pawo ? 3 : 2);
-    CUDA_OK(c, launch_optical_head<T>(sk.C, sk.npw, Q.s_d[Q.k_of[t]], pawo ? sk.P : nullptr, Q.KPo, Q.Qn_d,
+    CUDA_OK(c, launch_optical_head<T>(sk.C, sk.npw, sd, pawo ? sk.P : nullptr, Q.KPo, Q.Qn_d,
                                       (double2*)p_y, Lsub, nL, skp.R_d, nR, sk.eps_d, NG, Q.ig0, (c2<T>*)p_N,
                                       c->stream));
   }
@@ -615,15 +688,16 @@ rpa_status chi_block(rpa_ctx* c, QPt& Q, int t, const double* omega_d, int nw, d
     } else {
       const int terms = prec == RPA_BF16X3 ? 3 : 2;
       void* scr = nullptr;
-      const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
+      const int fused = tc_fused(c) ? 1 : 0;
+      const size_t sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms, fused);
       if (sb && (st = workspace(c, "herk_tc", sb, &scr)) != RPA_OK) return st;
       {
-        StageTimer tm(c, 5, 2);
-        CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms, scr, sb, c->stream));
+        StageTimer tm(c, 5, fused ? 1 : 2);
+        CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms, fused, scr, sb,
+                                   c->stream));
       }
       StageTimer tm(c, 2, 1);
-      CUDA_OK(c, herk_tc_run(B.P, B.NG, nw, terms, (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH],
-                             (int)c->tune[RPA_TUNE_TC_PIPE], chi, scr, sb, c->dev_err, c->stream));
+      CUDA_OK(c, run_herk_tc(c, B.P, B.NG, nw, terms, chi, scr, sb));
     }
   }
   return RPA_OK;
@@ -666,6 +740,7 @@ rpa_status chi_tc_pipeline(rpa_ctx* c, QPt& Q, const double* omega_d, int nw, do
     CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
   const int terms = c->prm.precision == RPA_BF16X3 ? 3 : 2;
+  const int fused = tc_fused(c) ? 1 : 0;
   struct Pending {
     int64_t P = 0;
     int NG = 0;
@@ -688,8 +763,7 @@ rpa_status chi_tc_pipeline(rpa_ctx* c, QPt& Q, const double* omega_d, int nw, do
     CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_prep[b.slot], 0));
     {
       StageTimer tm(c, 2, 1);
-      CUDA_OK(c, herk_tc_run(b.P, b.NG, nw, terms, (int)c->tune[RPA_TUNE_TC_FOLD], (int)c->tune[RPA_TUNE_TC_FLUSH],
-                             (int)c->tune[RPA_TUNE_TC_PIPE], chi, b.scr, b.sb, c->dev_err, c->stream));
+      CUDA_OK(c, run_herk_tc(c, b.P, b.NG, nw, terms, chi, b.scr, b.sb));
     }
     CUDA_OK(c, cudaEventRecord(c->ev_herk[b.slot], c->stream));
     herk_done[b.slot] = true;
@@ -705,7 +779,7 @@ rpa_status chi_tc_pipeline(rpa_ctx* c, QPt& Q, const double* omega_d, int nw, do
       cur.P = B.P;
       cur.NG = B.NG;
       cur.slot = slot;
-      cur.sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms);
+      cur.sb = herk_tc_scratch_bytes(B.P, B.NG, nw, terms, fused);
       if (cur.sb && (st = workspace(c, slot ? "herk_tc1" : "herk_tc", cur.sb, &cur.scr)) != RPA_OK) return st;
       CUDA_OK(c, cudaEventRecord(c->ev_pd[slot], c->stream));
       CUDA_OK(c, cudaStreamWaitEvent(c->stream2, c->ev_pd[slot], 0));
@@ -713,8 +787,8 @@ rpa_status chi_tc_pipeline(rpa_ctx* c, QPt& Q, const double* omega_d, int nw, do
       if (herk_done[slot]) CUDA_OK(c, cudaStreamWaitEvent(c->stream2, c->ev_herk[slot], 0));
       {
         StageTimer tm(c, 5, 2, c->stream2);
-        CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms, cur.scr, cur.sb,
-                                   c->stream2));
+        CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, nw, terms, fused, cur.scr,
+                                   cur.sb, c->stream2));
       }
       CUDA_OK(c, cudaEventRecord(c->ev_prep[slot], c->stream2));
       if (have_prev && (st = run_herk(prev)) != RPA_OK) return st;
@@ -849,6 +923,7 @@ rpa_status build_chi(rpa_ctx* c, int iq, int nw, const double* omega_host, doubl
 struct AdjState {
   std::map<int, void*> ubar;      // per set: dE/du grids [nb][Nr] in working precision
   std::map<int, double2*> gP;     // per set: dE/dP accumulators [nb][KP] (FP64)
+  std::map<int, double2*> gCo;    // per set: dE/dC through the optical head [nb][npw] (FP64), if any
 };
 
 template <typename T>
@@ -878,6 +953,21 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
   } else {
     CUDA_OK(c, launch_nbar<T>(B.N, B.P, NG, B.w, Gam, nw, Nbar, c->stream));
     tm.add_launches(1);
+  }
+  if (Q.optical) {
+    // the G = 0 column came from the head (Eqs. 12-13): its adjoint runs
+    // through the dipole matrix, then that column is cleared for the
+    // transform and PAW adjoints below (q = 0: the same set at k and k+q)
+    const bool pawo = Q.Qn_d && sk.P;
+    void* p_oa;
+    const size_t ob = sizeof(double2) * (size_t)optical_adj_scratch_elems(nL, nR, pawo ? Q.KPo : 0);
+    if ((st = workspace(c, "optical_adj", ob, &p_oa)) != RPA_OK) return st;
+    const double* sd;
+    if ((st = optical_s(c, Q, Q.k_of[t], &sd)) != RPA_OK) return st;
+    CUDA_OK(c, launch_optical_adjoint<T>(Nbar, NG, Q.ig0, B.Lsub, nL, skp.R_d, nR, sk.eps_d, sk.C, sk.npw,
+                                         sd, pawo ? sk.P : nullptr, Q.KPo, Q.Qn_d, (double2*)p_oa,
+                                         A.gCo[Q.k_of[t]], A.gP[Q.k_of[t]], c->stream));
+    tm.add_launches(pawo ? 7 : 3);
   }
   if (B.KP > 0) {
     if ((st = workspace(c, "paw_y", sizeof(c2<T>) * (size_t)nL * B.KP * NG, &p_y)) != RPA_OK) return st;
@@ -978,10 +1068,18 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
         if (std::find(touched.begin(), touched.end(), id) == touched.end()) touched.push_back(id);
   }
   const int64_t Nr = (int64_t)c->tg[0] * c->tg[1] * c->tg[2];
+  bool optical = false;
+  for (int i = 0; i < nq; ++i) optical = optical || c->qpts[iqs[i]].optical;
   for (int id : touched) {
     OrbSet& s = c->sets[id];
     if ((st = build_grids(c, s)) != RPA_OK) return st;
     void* p;
+    if (optical) {
+      const std::string ko = "gCo" + std::to_string(id);
+      if ((st = workspace(c, ko.c_str(), sizeof(double2) * (size_t)s.nb * s.npw, &p)) != RPA_OK) return st;
+      CUDA_OK(c, cudaMemsetAsync(p, 0, sizeof(double2) * (size_t)s.nb * s.npw, c->stream));
+      A.gCo[id] = (double2*)p;
+    }
     const std::string key = "ubar" + std::to_string(id);
     if ((st = workspace(c, key.c_str(), sizeof(c2<T>) * (size_t)s.nb * Nr, &p)) != RPA_OK) return st;
     CUDA_OK(c, cudaMemsetAsync(p, 0, sizeof(c2<T>) * (size_t)s.nb * Nr, c->stream));
@@ -1038,8 +1136,18 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     nl = 0;
     {
       StageTimer tm(c, 3, 0);
-      CUDA_OK(c, run_gamma((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y, (double2*)p_W,
-                           (double2*)p_G64, (float2*)p_G32, c->stream, &nl));
+      // (1 - M)^-1: FP64 in the FP64 mode and with RPA_TUNE_GAMMA = 0; in the
+      // mixed modes float-float products (2) or the FP32 product form (1)
+      const int64_t gm = sizeof(T) == 8 ? 0 : c->tune[RPA_TUNE_GAMMA];
+      if (gm == 0)
+        CUDA_OK(c, run_gamma((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y,
+                             (double2*)p_W, (double2*)p_G64, (float2*)p_G32, c->stream, &nl));
+      else if (gm == 2)
+        CUDA_OK(c, run_gamma_ff((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y,
+                                (double2*)p_W, (double2*)p_G64, (float2*)p_G32, c->stream, &nl));
+      else
+        CUDA_OK(c, run_gamma_mixed((const double2*)p_work, chi, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y,
+                                   (double2*)p_W, (double2*)p_G64, (float2*)p_G32, c->stream, &nl));
       tm.add_launches(nl);
     }
     if (dchi && dchi[i]) {
@@ -1079,6 +1187,7 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
       CUDA_OK(c, cudaMemsetAsync(p, 0, sizeof(double2) * (size_t)os.nb * os.npw, c->stream));
       if (A.ubar.count(id))
         if ((st = ubar_to_dC<T>(c, os, (const c2<T>*)A.ubar[id], (double2*)p)) != RPA_OK) return st;
+      if (A.gCo.count(id)) CUDA_OK(c, launch_add_c128((double2*)p, A.gCo[id], (int64_t)os.nb * os.npw, c->stream));
       const bool dev = is_device_ptr(dC[s]);
       CUDA_OK(c, cudaMemcpyAsync(dC[s], p, sizeof(double2) * (size_t)os.nb * os.npw,
                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
@@ -1292,6 +1401,24 @@ rpa_status rpa_set_orbitals(rpa_ctx* c, int32_t kidx, const double k_red[3], int
   // a call returns), and the upload is complete when this call returns.  If
   // it fails (a CUDA error), the set kidx is dropped rather than kept.
   auto old_it = c->sets.find(kidx);
+  {
+    // the optical limit's q^.(k+Q) of this set follows its plane waves
+    const bool same_pw = old_it != c->sets.end() && old_it->second.miller == s.miller &&
+                         old_it->second.k[0] == s.k[0] && old_it->second.k[1] == s.k[1] && old_it->second.k[2] == s.k[2];
+    if (!same_pw) {
+      bool synced = false;
+      for (auto& qp : c->qpts) {
+        auto si = qp.second.s_d.find(kidx);
+        if (si == qp.second.s_d.end()) continue;
+        if (!synced) {
+          CUDA_OK(c, cudaStreamSynchronize(c->stream));  // earlier work may still read it
+          synced = true;
+        }
+        dev_free(si->second);
+        qp.second.s_d.erase(si);
+      }
+    }
+  }
   if (old_it != c->sets.end()) {
     OrbSet& o = old_it->second;
     if (o.nb == nbands && o.npw == npw) {
@@ -1650,22 +1777,11 @@ rpa_status rpa_set_optical(rpa_ctx* c, int32_t iq, const double* qdir, int32_t n
     CUDA_OK(c, cudaMemcpy(Q.Qn_d, Qn.data(), sizeof(double2) * Qn.size(), cudaMemcpyHostToDevice));
     Q.KPo = KP;
   }
-  // q^.(k+Q) of every plane wave of every set used by iq (Cartesian, B rows)
-  const double* B = c->B;
+  // q^.(k+Q) of every plane wave of every set used by iq
+  for (int d = 0; d < 3; ++d) Q.qhat[d] = qh[d];
   for (int id : Q.k_of) {
-    if (Q.s_d.count(id)) continue;
-    const OrbSet& os = c->sets[id];
-    std::vector<double> sv(os.npw);
-    for (int g = 0; g < os.npw; ++g) {
-      const double r[3] = {os.k[0] + os.miller[3 * g], os.k[1] + os.miller[3 * g + 1], os.k[2] + os.miller[3 * g + 2]};
-      double acc = 0.0;
-      for (int d = 0; d < 3; ++d) acc += qh[d] * (r[0] * B[d] + r[1] * B[3 + d] + r[2] * B[6 + d]);
-      sv[g] = acc;
-    }
-    double* sd = nullptr;
-    if ((st = dev_alloc(c, (void**)&sd, sizeof(double) * os.npw)) != RPA_OK) return st;
-    Q.s_d[id] = sd;
-    CUDA_OK(c, cudaMemcpy(sd, sv.data(), sizeof(double) * os.npw, cudaMemcpyHostToDevice));
+    const double* sd;
+    if ((st = optical_s(c, Q, id, &sd)) != RPA_OK) return st;
   }
   Q.ig0 = ig0;
   Q.v[ig0] = 4.0 * M_PI;
@@ -1862,12 +1978,207 @@ rpa_status rpa_energy_enqueue(rpa_ctx* c, int32_t nq, const int32_t* iqs) {
   return energy_enqueue(c, nq, iqs, c->nw_set, c->omega_d);
 }
 
+// ---- persistent batched launch of many instances (the graph's form)
+// A unit is one (context, q-point) of the batch; a job is one k-block of a
+// unit (rows [a0, a1) of transition t).  Consecutive jobs are packed into
+// groups under an operand budget and the persistent kernel's job limit; per
+// group: the pair densities and operand preparation of every job into a
+// graph-owned pool, one persistent rank-k launch over all of the group's
+// jobs, then the log-det of every unit whose last job was in the group.
+struct BatchUnit {
+  int ctx = 0, iq = 0, pos = 0;   // context index, q-point, position in its context's result arrays
+  int job_begin = 0, job_end = 0; // jobs [begin, end)
+  int g_first = 0, g_last = 0;    // groups of its first and last job
+};
+struct BatchJobPlan {
+  int unit = 0, t = 0, a0 = 0, a1 = 0;
+  int64_t P = 0;
+  int NG = 0;
+  size_t sb = 0;      // operand bytes
+  size_t off = 0;     // offset in the pool
+};
+
 struct rpa_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
   int device = 0;
+  // persistent batched form
+  bool persist = false;
+  std::vector<BatchUnit> units;
+  std::vector<BatchJobPlan> jobs;
+  std::vector<std::pair<int, int>> groups;  // jobs [first, second)
+  void* pool = nullptr;
+  size_t pool_bytes = 0;
+  int* dev = nullptr;          // [0] item counter, [1] error flag
+  int** err_dst = nullptr;     // every context's error flag (device array)
 };
+
+namespace {
+
+// Units, jobs and groups of a batch (host only; sizes from the contexts' state).
+rpa_status plan_batch(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int32_t* nq, const int32_t* iqs) {
+  g->units.clear();
+  g->jobs.clear();
+  g->groups.clear();
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    rpa_ctx* c = ctxs[i];
+    const int nw = c->nw_set;
+    for (int u = 0; u < nq[i]; ++u) {
+      const int iq = iqs[off + u];
+      QPt& Q = c->qpts[iq];
+      BatchUnit U;
+      U.ctx = i;
+      U.iq = iq;
+      U.pos = u;
+      U.job_begin = (int)g->jobs.size();
+      for (size_t t = 0; t < Q.k_of.size(); ++t) {
+        const int nL = (int)c->sets[Q.k_of[t]].L.size(), nR = (int)c->sets[Q.kq_of[t]].R.size();
+        const int rows = rows_per_block(c, nL, nR, Q.NG, nw);
+        for (int a0 = 0; a0 < nL; a0 += rows) {
+          BatchJobPlan J;
+          J.unit = (int)g->units.size();
+          J.t = (int)t;
+          J.a0 = a0;
+          J.a1 = std::min(nL, a0 + rows);
+          J.P = (int64_t)(J.a1 - a0) * nR;
+          J.NG = Q.NG;
+          if (J.P == 0) continue;
+          J.sb = (herk_tc_scratch_bytes(J.P, J.NG, nw, 2, tc_fused(c) ? 1 : 0) + 255) / 256 * 256;
+          g->jobs.push_back(J);
+        }
+      }
+      U.job_end = (int)g->jobs.size();
+      g->units.push_back(U);
+    }
+    off += nq[i];
+  }
+  // groups: consecutive jobs under the budget (a larger job forms its own group)
+  const size_t budget = (size_t)ctxs[0]->tune[RPA_TUNE_BATCH_MB] << 20;
+  const int maxj = herk_tc_batch_max_jobs();
+  size_t used = 0;
+  int first = 0;
+  for (int j = 0; j < (int)g->jobs.size(); ++j) {
+    BatchJobPlan& J = g->jobs[j];
+    if (j > first && (used + J.sb > budget || j - first >= maxj)) {
+      g->groups.push_back({first, j});
+      first = j;
+      used = 0;
+    }
+    J.off = used;
+    used += J.sb;
+    g->pool_bytes = std::max(g->pool_bytes, used);
+  }
+  if (!g->jobs.empty() || g->groups.empty()) g->groups.push_back({first, (int)g->jobs.size()});
+  auto group_of = [&](int j) {
+    for (int k = 0; k < (int)g->groups.size(); ++k)
+      if (j < g->groups[k].second) return k;
+    return (int)g->groups.size() - 1;
+  };
+  for (BatchUnit& U : g->units) {
+    U.g_first = group_of(U.job_begin);
+    U.g_last = U.job_end > U.job_begin ? group_of(U.job_end - 1) : U.g_first;
+  }
+  return RPA_OK;
+}
+
+// All device work of the batch on the shared stream (capturable).
+rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int32_t* nq, const int32_t* iqs) {
+  rpa_status st;
+  cudaStream_t s = ctxs[0]->stream;
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    rpa_ctx* c = ctxs[i];
+    ++c->stamp;
+    choose_transform_grid(c, iqs + off, nq[i]);
+    void *p_ld, *p_tr, *p_fl;
+    if ((st = workspace(c, "res_ld", sizeof(double) * (size_t)nq[i] * c->nw_set, &p_ld)) != RPA_OK) return st;
+    if ((st = workspace(c, "res_tr", sizeof(double) * (size_t)nq[i] * c->nw_set, &p_tr)) != RPA_OK) return st;
+    if ((st = workspace(c, "res_flag", sizeof(int) * (size_t)nq[i], &p_fl)) != RPA_OK) return st;
+    CUDA_OK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
+    c->enq_iqs.assign(iqs + off, iqs + off + nq[i]);
+    off += nq[i];
+  }
+  rpa_ctx* c0 = ctxs[0];
+  CUDA_OK(c0, cudaMemsetAsync(g->dev + 1, 0, sizeof(int), s));
+  std::vector<double2*> chi(g->units.size(), nullptr);
+  for (int gi = 0; gi < (int)g->groups.size(); ++gi) {
+    // units starting here: chi0 cleared, grids of their sets built
+    for (size_t u = 0; u < g->units.size(); ++u) {
+      const BatchUnit& U = g->units[u];
+      if (U.g_first != gi) continue;
+      rpa_ctx* c = ctxs[U.ctx];
+      QPt& Q = c->qpts[U.iq];
+      const std::string key = "chiq" + std::to_string(U.iq);
+      void* p;
+      const size_t bytes = sizeof(double2) * (size_t)c->nw_set * Q.NG * Q.NG;
+      if ((st = workspace(c, key.c_str(), bytes, &p)) != RPA_OK) return st;
+      CUDA_OK(c, cudaMemsetAsync(p, 0, bytes, s));
+      chi[u] = (double2*)p;
+      for (size_t t = 0; t < Q.k_of.size(); ++t) {
+        if ((st = build_grids(c, c->sets[Q.k_of[t]])) != RPA_OK) return st;
+        if ((st = build_grids(c, c->sets[Q.kq_of[t]])) != RPA_OK) return st;
+      }
+    }
+    // pair densities and operands of the group's jobs, then one persistent launch
+    const int jb = g->groups[gi].first, je = g->groups[gi].second;
+    std::vector<int64_t> P;
+    std::vector<int> NG, nw;
+    std::vector<void*> scr;
+    std::vector<size_t> sb;
+    std::vector<double2*> chis;
+    std::vector<int> unit_of;
+    int fused = -1;
+    for (int j = jb; j < je; ++j) {
+      const BatchJobPlan& J = g->jobs[j];
+      const BatchUnit& U = g->units[J.unit];
+      rpa_ctx* c = ctxs[U.ctx];
+      QPt& Q = c->qpts[U.iq];
+      Block<float> B;
+      if ((st = pairs_block<float>(c, Q, J.t, J.a0, J.a1, c->omega_d, c->nw_set, B, 0)) != RPA_OK) return st;
+      const int fz = tc_fused(c) ? 1 : 0;
+      if (fused >= 0 && fz != fused) return fail(c, RPA_ERR_ARG, "the contexts of a batch differ in RPA_TUNE_TC_FUSE");
+      fused = fz;
+      void* p = (char*)g->pool + J.off;
+      CUDA_OK(c, herk_tc_prepare((const float2*)B.N, B.P, B.NG, (const float*)B.w, c->nw_set, 2, fz, p, J.sb, s));
+      P.push_back(J.P);
+      NG.push_back(J.NG);
+      nw.push_back(c->nw_set);
+      scr.push_back(p);
+      sb.push_back(J.sb);
+      chis.push_back(chi[J.unit]);
+      unit_of.push_back(J.unit);
+    }
+    if (!P.empty())
+      CUDA_OK(c0, herk_tc_batch_run((int)P.size(), P.data(), NG.data(), nw.data(), scr.data(), sb.data(),
+                                    unit_of.data(), chis.data(), fused, (int)c0->tune[RPA_TUNE_TC_FOLD],
+                                    (int)c0->tune[RPA_TUNE_TC_FLUSH], c0->tune[RPA_TUNE_TC_WAIT_US], g->dev,
+                                    g->dev + 1, s));
+    // log-dets of the units that end here
+    for (size_t u = 0; u < g->units.size(); ++u) {
+      const BatchUnit& U = g->units[u];
+      if (U.g_last != gi) continue;
+      rpa_ctx* c = ctxs[U.ctx];
+      QPt& Q = c->qpts[U.iq];
+      const int nw_ = c->nw_set;
+      void* p_work;
+      if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw_, Q.NG), &p_work)) != RPA_OK)
+        return st;
+      const LogdetStreams* la;
+      if ((st = logdet_streams(c, &la)) != RPA_OK) return st;
+      int64_t nl = 0;
+      CUDA_OK(c, run_logdet(chi[u], Q.v_d, nw_, Q.NG, (double2*)p_work,
+                            (double*)c->ws["res_ld"].p + (size_t)U.pos * nw_,
+                            (double*)c->ws["res_tr"].p + (size_t)U.pos * nw_, (int*)c->ws["res_flag"].p + U.pos,
+                            ff_logdet(c), s, &nl, la));
+    }
+  }
+  // a bounded wait that gave up reaches every context's flag
+  CUDA_OK(c0, launch_or_flags(g->dev + 1, g->err_dst, n, s));
+  return RPA_OK;
+}
+}  // namespace
 
 rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq, const int32_t* iqs, rpa_graph** out) {
   if (!ctxs || n < 1 || !nq || !iqs || !out) return RPA_ERR_ARG;
@@ -1881,30 +2192,66 @@ rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq, 
   }
   cudaStream_t s = ctxs[0]->stream;
   if (cudaSetDevice(ctxs[0]->prm.device) != cudaSuccess) return RPA_ERR_CUDA;
-  // warm-up outside the capture: sizes every workspace and device table
   int64_t off = 0;
   for (int i = 0; i < n; ++i) {
-    rpa_status st = rpa_energy_enqueue(ctxs[i], nq[i], iqs + off);
-    if (st != RPA_OK) return st;
+    for (int u = 0; u < nq[i]; ++u)
+      if (rpa_status st = check_q_ready(ctxs[i], iqs[off + u]); st != RPA_OK) return st;
     off += nq[i];
   }
-  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ctxs[0], RPA_ERR_CUDA, "warm-up run failed");
+  // the persistent form: every context in the two-term split mode, not switched off
+  bool persist = ctxs[0]->tune[RPA_TUNE_BATCH_PERSIST] == 1;
+  for (int i = 0; i < n; ++i)
+    persist = persist && ctxs[i]->prm.precision == RPA_BF16X2 && ctxs[i]->tune[RPA_TUNE_TC_PIPE] == 0 &&
+              ctxs[i]->tune[RPA_TUNE_TC_FUSE] == ctxs[0]->tune[RPA_TUNE_TC_FUSE];
+  rpa_graph* g = new rpa_graph();
+  g->stream = s;
+  g->device = ctxs[0]->prm.device;
+  g->persist = persist;
+  auto bail = [&](rpa_status st) {
+    cudaGetLastError();
+    rpa_graph_destroy(g);
+    return st;
+  };
+  if (persist) {
+    plan_batch(g, ctxs, n, nq, iqs);
+    std::vector<int*> dst(n);
+    for (int i = 0; i < n; ++i) dst[i] = ctxs[i]->dev_err;
+    if (cudaMalloc(&g->dev, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&g->err_dst, sizeof(int*) * n) != cudaSuccess ||
+        (g->pool_bytes && cudaMalloc(&g->pool, g->pool_bytes) != cudaSuccess))
+      return bail(fail(ctxs[0], RPA_ERR_OOM, "batched graph buffers (%zu bytes) could not be allocated", g->pool_bytes));
+    if (cudaMemcpy(g->err_dst, dst.data(), sizeof(int*) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(RPA_ERR_CUDA);
+  }
+  // warm-up outside the capture: sizes every workspace and device table
+  off = 0;
+  if (persist) {
+    if (rpa_status st = batched_enqueue(g, ctxs, n, nq, iqs); st != RPA_OK) return bail(st);
+  } else {
+    for (int i = 0; i < n; ++i) {
+      rpa_status st = rpa_energy_enqueue(ctxs[i], nq[i], iqs + off);
+      if (st != RPA_OK) return bail(st);
+      off += nq[i];
+    }
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctxs[0], RPA_ERR_CUDA, "warm-up run failed"));
   std::vector<bool> prof(n);
   for (int i = 0; i < n; ++i) {
     prof[i] = ctxs[i]->profiling;
     ctxs[i]->profiling = false;
   }
-  rpa_graph* g = new rpa_graph();
-  g->stream = s;
-  g->device = ctxs[0]->prm.device;
   rpa_status st = RPA_OK;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
     st = fail(ctxs[0], RPA_ERR_CUDA, "cudaStreamBeginCapture failed");
   } else {
     off = 0;
-    for (int i = 0; i < n && st == RPA_OK; ++i) {
-      st = rpa_energy_enqueue(ctxs[i], nq[i], iqs + off);
-      off += nq[i];
+    if (persist) {
+      st = batched_enqueue(g, ctxs, n, nq, iqs);
+    } else {
+      for (int i = 0; i < n && st == RPA_OK; ++i) {
+        st = rpa_energy_enqueue(ctxs[i], nq[i], iqs + off);
+        off += nq[i];
+      }
     }
     const cudaError_t e = cudaStreamEndCapture(s, &g->graph);
     if (st == RPA_OK && e != cudaSuccess) st = fail(ctxs[0], RPA_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
@@ -1932,6 +2279,9 @@ void rpa_graph_destroy(rpa_graph* g) {
   cudaSetDevice(g->device);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->pool) cudaFree(g->pool);
+  if (g->dev) cudaFree(g->dev);
+  if (g->err_dst) cudaFree(g->err_dst);
   delete g;
 }
 
@@ -1955,8 +2305,6 @@ rpa_status rpa_energy_backward(rpa_ctx* c, int32_t nq, const int32_t* iqs, const
   for (int i = 0; i < nq; ++i) {
     rpa_status st = check_q_ready(c, iqs[i]);
     if (st != RPA_OK) return st;
-    if (c->qpts[iqs[i]].optical)
-      return fail(c, RPA_ERR_STATE, "q-point %d uses the optical limit; its gradient is not available", iqs[i]);
   }
   choose_transform_grid(c, iqs, nq);
   rpa_status st;
@@ -1996,6 +2344,28 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_PAW_TC:
       if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "PAW product choice must be 0 or 1");
+      break;
+    case RPA_TUNE_TC_FUSE:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "fused weighting choice must be 0 or 1");
+      break;
+    case RPA_TUNE_PD_FUSE:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "fused pair-density stage choice must be 0 or 1");
+      break;
+    case RPA_TUNE_BATCH_PERSIST:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "batched launch choice must be 0 or 1");
+      break;
+    case RPA_TUNE_GAMMA:
+      if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "gradient precision choice must be 0, 1 or 2");
+      break;
+    case RPA_TUNE_BATCH_MB:
+      if (value < 1 || value > (1 << 22)) return fail(c, RPA_ERR_ARG, "batch group budget %lld MiB out of range", (long long)value);
+      break;
+    case RPA_TUNE_TC_WAIT_US:
+      if (value < 1000 || value > 60000000)
+        return fail(c, RPA_ERR_ARG, "wait limit %lld us out of range", (long long)value);
+      break;
+    case RPA_TUNE_TC_STALL:
+      if (value < 0 || value > (1 << 30)) return fail(c, RPA_ERR_ARG, "stall stage %lld out of range", (long long)value);
       break;
     case RPA_TUNE_OPERAND_MB:
       if (value < 16 || value > (1 << 20)) return fail(c, RPA_ERR_ARG, "operand budget %lld MB out of range", (long long)value);

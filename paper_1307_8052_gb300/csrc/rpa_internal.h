@@ -66,6 +66,19 @@ template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft,
                              int NG, int g1lo, int g2lo, double inv_nr, int64_t p0, c2<T>* Nout, cudaStream_t s);
 
+// Pair densities, stages B and C fused per (pair, slab of OB first-axis
+// outputs): the middle-axis DFT into shared memory, then the fastest axis on
+// the sphere points of the slab (g1start[o] = first sphere point with
+// g1 - g1lo >= o); bit-identical to stage B followed by stage C.
+// pd_stageBC_slab gives the slab height that fits (0: use stages B and C).
+template <typename T>
+cudaError_t launch_pd_stageBC(const c2<T>* T1, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
+                              const int* gfft, const int* g1start, int OB, int NG, int g1lo, int g2lo, double inv_nr,
+                              int64_t p0, c2<T>* Nout, cudaStream_t s);
+template <typename T>
+int pd_stageBC_slab(int n1, int n2, int N2, int N3);
+cudaError_t launch_g1start(const int* gfft, int NG, int g1lo, int n1, int* out, cudaStream_t s);
+
 // PAW term of a block: N[(a nR + b)][g] += sum_kp Pm[b][kp] R[a][kp][g].
 template <typename T>
 cudaError_t launch_paw_gemm(const c2<T>* R, const c2<T>* Pm, int KP, int nL, int nR, int NG, c2<T>* N,
@@ -110,6 +123,19 @@ template <typename T>
 cudaError_t launch_optical_head(const double2* C, int npw, const double* s, const double2* P, int KP,
                                 const double2* Qn, double2* scratch, const int* L, int nL, const int* R, int nR,
                                 const double* eps, int NG, int ig0, c2<T>* N, cudaStream_t st);
+
+// Adjoint of the optical head (k_optical.cu): the G = 0 column of Nbar flows
+// back through the dipole matrix into the FP64 gradients of C (gC [nb][npw])
+// and P (gP [nb][KP]) of the q = 0 point's orbital set, and is then cleared;
+// scratch holds optical_adj_scratch_elems(nL, nR, KP) complex FP64 elements.
+int64_t optical_adj_scratch_elems(int nL, int nR, int KP);
+template <typename T>
+cudaError_t launch_optical_adjoint(c2<T>* Nbar, int NG, int ig0, const int* L, int nL, const int* R, int nR,
+                                   const double* eps, const double2* C, int npw, const double* s, const double2* P,
+                                   int KP, const double2* Qn, double2* scratch, double2* gC, double2* gP,
+                                   cudaStream_t st);
+// dst[i] += src[i] (complex FP64)
+cudaError_t launch_add_c128(double2* dst, const double2* src, int64_t n, cudaStream_t st);
 
 // IBZ -> BZ symmetry (k_optical.cu): conjugation of coefficients, and rotation
 // of projections out[n][a][i] = sum_j D^a_ij P[n][src(a)][j] (conjugated if tr);

@@ -5,7 +5,7 @@ Gamma -> (0, 1/2, 1/2) (no umklapp) and (0, 1/2, 1/2) -> Gamma (umklapp (0, 1, 1
 16 occupied + 1200 empty bands per set, 3 x 13 PAW projectors, 16 frequencies:
 each launch of the rank-k kernel is exactly one launch of the bench's workload.
 
-Usage: python -m paper_1307_8052_gb300.profile_case [fold] [reps] [chi|energy] [precision]
+Usage: python -m paper_1307_8052_gb300.profile_case [fold] [reps] [chi|energy] [precision] [fuse]
 """
 from __future__ import annotations
 
@@ -22,6 +22,7 @@ def main(argv):
     reps = int(argv[2]) if len(argv) > 2 else 1
     mode = argv[3] if len(argv) > 3 else "chi"
     precision = argv[4] if len(argv) > 4 else "bf16x2"
+    fuse = int(argv[5]) if len(argv) > 5 else 1
     b.load()
     cell = np.eye(3) * 9.0
     ks = {0: np.zeros(3), 3: np.array([0.0, 0.5, 0.5])}
@@ -35,6 +36,7 @@ def main(argv):
     b.rpa_set_qpoint(ctx, 0, q, [0, 3], [3, 0], [[0, 0, 0], [0, 1, 1]])
     b.rpa_set_paw_Q(ctx, 0, paw.nproj, syn.paw_Q(paw, cell, q, b.rpa_gvectors(ctx, 0)))
     b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FOLD, fold)
+    b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FUSE, fuse)
     om, W = b.rpa_gauss_legendre(16)
     b.rpa_set_profiling(ctx, True)
     for _ in range(reps):
@@ -43,7 +45,7 @@ def main(argv):
         else:
             b.rpa_chi0(ctx, 0, om)
         ms, _ = b.rpa_get_profile(ctx)
-        print(f"{precision} fold {fold} stage ms {np.round(ms, 2).tolist()}", flush=True)
+        print(f"{precision} fold {fold} fuse {fuse} stage ms {np.round(ms, 2).tolist()}", flush=True)
     b.rpa_destroy(ctx)
 
 
