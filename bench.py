@@ -261,6 +261,8 @@ def run_ours(args):
                 b.rpa_set_optical(ctx, iq, OPTICAL_QDIR, p.paw.nproj, syn.paw_Qnabla(p.paw, p.config))
         if args.paw_tc:
             b.rpa_set_tuning(ctx, b.RPA_TUNE_PAW_TC, 1)
+        if args.tc_pair is not None:
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, args.tc_pair)
         return ctx, ngs
 
     # every rank loads every q-point of the step (the response spheres give the
@@ -620,6 +622,7 @@ def run_batched(args):
             b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FUSE, 0)
         b.rpa_set_tuning(ctxs[0], b.RPA_TUNE_BATCH_PERSIST, 1)
         t_pers, E_pers = graph_time()
+    free_gb = torch.cuda.mem_get_info()[0] / 1e9
     for ctx in ctxs:
         b.rpa_destroy(ctx)
     t_best = min(t for t in (t_graph, t_pers) if t is not None)
@@ -628,7 +631,7 @@ def run_batched(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": f"{len(ctxs)} (q, cell) instances, NG 400-3000, n_occ 8-120, n_unocc ~ NG, "
                                    "16 iw, 3x13 PAW, one CUDA graph", "NG": ngs, "pairs": pairs,
-                       "generation_s": gen_s, "flops": total},
+                       "generation_s": gen_s, "flops": total, "device_free_gb_at_end": free_gb},
             "sequential": {"value": total / t_seq / 1e12, "ms_per_step": t_seq * 1e3},
             "graph_per_instance": {"value": total / t_graph / 1e12, "ms_per_step": t_graph * 1e3},
             "graph_persistent": (None if t_pers is None else
@@ -660,8 +663,11 @@ def main():
     ap.add_argument("--slab-q", type=int, default=1, help="q-points per step of the slab workload")
     ap.add_argument("--paw-tc", action="store_true",
                     help="PAW product on the tensor cores (split modes; faster for many projectors, larger E_c error)")
+    ap.add_argument("--tc-pair", type=int, choices=[0, 1], default=None,
+                    help="rank-k launch paired over frequencies (TMA multicast of the shared operand); "
+                         "default: the library's")
     ap.add_argument("--instances", type=int, default=64)
-    ap.add_argument("--gamma", type=int, choices=[0, 1, 2], default=0,
+    ap.add_argument("--gamma", type=int, choices=[0, 1, 2], default=2,
                     help="--config backward: dE/dchi0 in FP64 (0), FP32 product form (1) or float-float (2)")
     args = ap.parse_args()
     if args.impl == "reference":

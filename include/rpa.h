@@ -361,16 +361,26 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      sequence of launches.  Bit-identical results.
  * RPA_TUNE_BATCH_MB    read from the first context of rpa_graph_create: the
  *                      rank-k operand memory (MiB) of one group of that
- *                      persistent form; default 16384.
+ *                      persistent form; default 16384.  An upper bound: where
+ *                      the pool cannot be allocated, rpa_graph_create halves
+ *                      it (down to the largest single k-block) and re-plans.
  * RPA_TUNE_GAMMA      dE/dchi0 = c_w v^1/2 [1 - (1 - M)^-1] v^1/2 of
  *                      rpa_energy_backward in RPA_FP32, RPA_BF16X2 and
- *                      RPA_BF16X3 (RPA_FP64 always uses FP64): 0 (default)
- *                      from the Cholesky factor in FP64; 2 the same products
- *                      in float-float on the FP32 pipe (about 44 bits); 1 the
+ *                      RPA_BF16X3 (RPA_FP64 always uses FP64): 0 from the
+ *                      Cholesky factor in FP64; 2 (default) the same products
+ *                      in float-float on the FP32 pipe (about 44 bits; the
+ *                      gradient error of the FP64 form); 1 the
  *                      FP32 form -c_w v^1/2 M (1 - M)^-1 v^1/2, fastest but
  *                      with ~1e-5 relative error in dE/dchi0 and ~3e-4 in
  *                      dE/dC and dE/dP on the bulk gradient workload (FP64:
  *                      <= 3e-6).
+ * RPA_TUNE_TC_PAIR    1: the stored-operand two-term rank-k kernel (RPA_BF16X2
+ *                      with RPA_TUNE_TC_FUSE = 0 and RPA_TUNE_TC_PIPE = 0)
+ *                      runs as clusters of two CTAs, one tile at two
+ *                      frequencies; the pair shares the unweighted operand
+ *                      tiles, each CTA loading half of them into both by TMA
+ *                      multicast.  Bit-identical to 0.  An odd number of
+ *                      frequencies runs unpaired.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -388,7 +398,8 @@ typedef enum {
   RPA_TUNE_BATCH_PERSIST = 12,
   RPA_TUNE_BATCH_MB = 13,
   RPA_TUNE_GAMMA = 14,
-  RPA_TUNE_COUNT = 15
+  RPA_TUNE_TC_PAIR = 15,
+  RPA_TUNE_COUNT = 16
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

@@ -12,6 +12,8 @@
 //  * Pair densities (Eq. 10): xbar(r) = (1/N_r) sum_G nbar(G) exp(+i (G+G0).r)
 //    by the transposed pruned transforms, ubar_m += xbar u_n,
 //    ubar_n += conj(xbar) u_m, and gC(Q) = sum_r exp(-i Q.r) ubar(r).
+#include <algorithm>
+
 #include "ff_math.cuh"
 #include "rpa_internal.h"
 
@@ -691,38 +693,89 @@ __global__ void __launch_bounds__(256) paw_adj_pk_kernel(const c2<T>* __restrict
   }
 }
 
-// gPkp[Ridx[b]][kp] += sum_aL sum_G Nbar[(aL, b)][G] conj(R[aL][kp][G])   (one block per (b, kp))
+// gPkp as a tiled product: for occupied band aL (grid z), part[aL][b][kp] =
+// sum_G Nbar[(aL, b)][G] conj(R[aL][kp][G]) over 32 b x 64 kp tiles, products
+// summed in T over G slices (32 in FP32, 16 in FP64) and the slices in FP64;
+// paw_adj_pkp_reduce adds the bands in order to gP[Ridx[b]].
 template <typename T>
-__global__ void __launch_bounds__(256) paw_adj_pkp_kernel(const c2<T>* __restrict__ Nbar, const c2<T>* __restrict__ R,
-                                                          int nL, int nR, int NG, int KP, const int* __restrict__ Ridx,
-                                                          double2* __restrict__ gP) {
-  __shared__ double red[2][256];
-  const int kp = blockIdx.x % KP;
-  const int b = blockIdx.x / KP;
-  double sx = 0.0, sy = 0.0;
-  for (int aL = 0; aL < nL; ++aL) {
-    const c2<T>* nb = Nbar + ((int64_t)aL * nR + b) * NG;
-    const c2<T>* rr = R + ((int64_t)aL * KP + kp) * NG;
-    for (int g = threadIdx.x; g < NG; g += blockDim.x) {
-      const c2<T> x = nb[g], y = rr[g];
-      sx += (double)x.x * y.x + (double)x.y * y.y;
-      sy += (double)x.y * y.x - (double)x.x * y.y;
+__global__ void __launch_bounds__(256) paw_adj_pkp_tile_kernel(const c2<T>* __restrict__ Nbar,
+                                                               const c2<T>* __restrict__ R, int nR, int NG, int KP,
+                                                               double2* __restrict__ part) {
+  constexpr int KT = sizeof(T) == 4 ? 32 : 16;
+  __shared__ c2<T> As[KT][33];
+  __shared__ c2<T> Bs[KT][65];
+  const int aL = blockIdx.z;
+  const int b0 = blockIdx.x * 32, k0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const c2<T>* nb = Nbar + ((int64_t)aL * nR) * NG;
+  const c2<T>* rr = R + ((int64_t)aL * KP) * NG;
+  double2 acc[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_double2(0.0, 0.0);
+  for (int g0 = 0; g0 < NG; g0 += KT) {
+#pragma unroll
+    for (int q = 0; q < 32 * KT / 256; ++q) {
+      const int e = threadIdx.x + 256 * q, bb = e / KT, kk = e % KT;
+      As[kk][bb] = (b0 + bb < nR && g0 + kk < NG) ? nb[(int64_t)(b0 + bb) * NG + g0 + kk] : mk<T>(0, 0);
     }
-  }
-  red[0][threadIdx.x] = sx;
-  red[1][threadIdx.x] = sy;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+#pragma unroll
+    for (int q = 0; q < 64 * KT / 256; ++q) {
+      const int e = threadIdx.x + 256 * q, cc = e / KT, kk = e % KT;
+      Bs[kk][cc] = (k0 + cc < KP && g0 + kk < NG) ? rr[(int64_t)(k0 + cc) * NG + g0 + kk] : mk<T>(0, 0);
     }
     __syncthreads();
+    c2<T> s[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s[r][c] = mk<T>(0, 0);
+#pragma unroll 8
+    for (int kk = 0; kk < KT; ++kk) {
+      c2<T> a[2], bv[4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac_cj<T>(s[r][c], a[r], bv[c]);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        acc[r][c].x += (double)s[r][c].x;
+        acc[r][c].y += (double)s[r][c].y;
+      }
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int b = b0 + ty + 16 * r, kp = k0 + tx + 16 * c;
+      if (b < nR && kp < KP) part[((int64_t)aL * nR + b) * KP + kp] = acc[r][c];
+    }
+}
+
+// gP[Ridx[b]][kp] += sum_aL part[aL][b][kp], bands in order
+__global__ void paw_adj_pkp_reduce_kernel(const double2* __restrict__ part, int nL, int nR, int KP,
+                                          const int* __restrict__ Ridx, double2* __restrict__ gP) {
+  const int64_t total = (int64_t)nR * KP;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(id / KP), kp = (int)(id % KP);
+    double sx = 0.0, sy = 0.0;
+    for (int aL = 0; aL < nL; ++aL) {
+      const double2 v = part[(int64_t)aL * total + id];
+      sx += v.x;
+      sy += v.y;
+    }
     double2* dst = gP + (int64_t)Ridx[b] * KP + kp;
-    dst->x += red[0][0];
-    dst->y += red[1][0];
+    dst->x += sx;
+    dst->y += sy;
   }
 }
 
@@ -730,21 +783,25 @@ template <typename T>
 cudaError_t launch_paw_adjoint(const c2<T>* Nbar, const c2<T>* R, const c2<T>* Pm, int nL, int nR, int NG, int KP,
                                const double2* Q, const int* atom_of_kp, const int* idx_in_atom, const int* atom_off,
                                const int64_t* q_off, const int* nproj, const int* Lidx, const int* Ridx, c2<T>* Ywork,
-                               double2* gPk, double2* gPkp, cudaStream_t s) {
+                               double2* part, double2* gPk, double2* gPkp, cudaStream_t s) {
   if ((int64_t)nL * nR * KP == 0) return cudaSuccess;
   paw_adj_y_kernel<T><<<gridx((int64_t)nL * KP * NG), 256, 0, s>>>(Nbar, nL, nR, NG, Pm, KP, Ywork);
   paw_adj_pk_kernel<T><<<nL * KP, 256, 0, s>>>(Ywork, NG, KP, Q, atom_of_kp, idx_in_atom, atom_off, q_off, nproj,
                                                 Lidx, gPk);
-  paw_adj_pkp_kernel<T><<<nR * KP, 256, 0, s>>>(Nbar, R, nL, nR, NG, KP, Ridx, gPkp);
+  paw_adj_pkp_tile_kernel<T><<<dim3((nR + 31) / 32, (KP + 63) / 64, nL), 256, 0, s>>>(Nbar, R, nR, NG, KP, part);
+  paw_adj_pkp_reduce_kernel<<<gridx((int64_t)nR * KP), 256, 0, s>>>(part, nL, nR, KP, Ridx, gPkp);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- pair-density adjoint
 // Stage C^T: T2bar[pl][o1][o2][j3] = (1/N_r) sum_{G in column (o1,o2)} Nbar[p][G] exp(+2 pi i g3 j3 / N3).
 // Column lists: col_start[n1*n2+1], col_g[k] = sphere index, col_g3[k] = g3 of that point.
+// Chunk pl -> pair p = p0 + (pl / mc) nR + pl % mc: mc consecutive unoccupied
+// bands of np / mc consecutive occupied bands.
 template <typename T>
 __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict__ Nbar, int NG, int64_t p0, int np,
-                                                         int ncol, int N3, const int* __restrict__ col_start,
+                                                         int mc, int nR, int ncol, int N3,
+                                                         const int* __restrict__ col_start,
                                                          const int* __restrict__ col_g, const int* __restrict__ col_g3,
                                                          double inv_nr, c2<T>* __restrict__ T2) {
   extern __shared__ unsigned char smem_raw[];
@@ -762,7 +819,7 @@ __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict
     const int64_t r = id / N3;
     const int col = (int)(r % ncol);
     const int pl = (int)(r / ncol);
-    const c2<T>* nb = Nbar + (p0 + pl) * NG;
+    const c2<T>* nb = Nbar + (p0 + (int64_t)(pl / mc) * nR + pl % mc) * NG;
     c2<T> acc = mk<T>(0, 0);
     for (int k = col_start[col]; k < col_start[col + 1]; ++k) {
       const int t = pmod_a((int64_t)col_g3[k] * j3, N3);
@@ -775,12 +832,14 @@ __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict
 }
 
 template <typename T>
-cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int ncol, int N3, const int* col_start,
-                              const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2, cudaStream_t s) {
+cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int mc, int nR, int ncol, int N3,
+                              const int* col_start, const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2,
+                              cudaStream_t s) {
   const int64_t total = (int64_t)np * ncol * N3;
   if (total == 0) return cudaSuccess;
-  adj_stageC_kernel<T><<<gridx(total), 256, N3 * sizeof(c2<T>), s>>>(Nbar, NG, p0, np, ncol, N3, col_start, col_g,
-                                                                     col_g3, inv_nr, T2);
+  if (mc < 1 || np % mc) return cudaErrorInvalidValue;
+  adj_stageC_kernel<T><<<gridx(total), 256, N3 * sizeof(c2<T>), s>>>(Nbar, NG, p0, np, mc, nR, ncol, N3, col_start,
+                                                                     col_g, col_g3, inv_nr, T2);
   return cudaGetLastError();
 }
 
@@ -849,6 +908,157 @@ cudaError_t launch_adj_un(const c2<T>* Xbar, int np, int64_t Nr, const c2<T>* Uk
   return cudaGetLastError();
 }
 
+// Stage A^T fused with both products, x-bar never stored: a chunk holds the
+// pairs (a0 + i, m0 + j), i < A occupied bands, j < mc unoccupied bands, as
+// T1[i mc + j][o1][j23].  A block owns 32 columns j23 (one per lane) and a
+// slice of the chunk's m; warp w owns the rows j1 = w, w + 4, ... .  Per pair
+// and row: x_i = sum_o1 T1[o1] tw[o1][j1]; ubar_m[j] += sum_i x_i u_{a0+i}[j]
+// (one read-modify-write per m and row for all A bands; distinct m per thread:
+// no race); the u_n terms conj(x_i) u_m[j] are summed over the block's m in
+// shared memory and written once per block as part[slice][i][j], which
+// adj_part_reduce adds to ubar_n in slice order (deterministic).
+constexpr int ADJA_WARPS = 4;
+
+template <typename T, int NI, int A>
+__global__ void __launch_bounds__(128) adj_stageA_fused_kernel(const c2<T>* __restrict__ T1, int mc, int n1, int N1,
+                                                               int N23, const c2<T>* __restrict__ tw,
+                                                               const c2<T>* __restrict__ Un0,
+                                                               const c2<T>* __restrict__ Un1,
+                                                               const c2<T>* __restrict__ Ukp,
+                                                               const int* __restrict__ Ridx, int m0,
+                                                               c2<T>* __restrict__ Ubar_kp, c2<T>* __restrict__ part) {
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tws = reinterpret_cast<c2<T>*>(smem_raw);  // [N1][NI], o1 beyond n1 zero
+  c2<T>* uns = tws + N1 * NI;                        // [A][N1][32] u_n of the block's columns
+  c2<T>* accs = uns + A * N1 * 32;                   // [A][N1][32] u_n terms of the block's m
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j23 = blockIdx.x * 32 + lane;
+  const int64_t Nr = (int64_t)N1 * N23;
+  for (int e = threadIdx.x; e < N1 * NI; e += blockDim.x) {
+    const int j1 = e / NI, o = e % NI;
+    tws[e] = o < n1 ? tw[o * N1 + j1] : mk<T>(0, 0);
+  }
+  for (int e = threadIdx.x; e < A * N1 * 32; e += blockDim.x) {
+    const int i = e / (N1 * 32), r = e % (N1 * 32), j1 = r >> 5, l = r & 31;
+    const int jj = blockIdx.x * 32 + l;
+    const c2<T>* un = i ? Un1 : Un0;
+    uns[e] = jj < N23 ? un[(int64_t)j1 * N23 + jj] : mk<T>(0, 0);
+    accs[e] = mk<T>(0, 0);
+  }
+  __syncthreads();
+  const int per = (mc + gridDim.y - 1) / gridDim.y;
+  const int jb = blockIdx.y * per, je = min(mc, jb + per);
+  if (j23 < N23) {
+    for (int j = jb; j < je; ++j) {
+      const int m = Ridx[m0 + j];
+      c2<T> t[A][NI];
+#pragma unroll
+      for (int i = 0; i < A; ++i) {
+        const c2<T>* src = T1 + ((int64_t)(i * mc + j) * n1) * N23 + j23;
+#pragma unroll
+        for (int o = 0; o < NI; ++o) t[i][o] = o < n1 ? src[(int64_t)o * N23] : mk<T>(0, 0);
+      }
+      const c2<T>* um = Ukp + (int64_t)m * Nr + j23;
+      c2<T>* ubm = Ubar_kp + (int64_t)m * Nr + j23;
+#pragma unroll 2
+      for (int j1 = warp; j1 < N1; j1 += ADJA_WARPS) {
+        const int64_t off = (int64_t)j1 * N23;
+        const c2<T> u = um[off];
+        c2<T> v = ubm[off];
+        const c2<T>* twj = tws + j1 * NI;
+#pragma unroll
+        for (int i = 0; i < A; ++i) {
+          c2<T> x = mk<T>(0, 0);
+#pragma unroll
+          for (int o = 0; o < NI; ++o) cmac<T>(x, t[i][o], twj[o]);
+          cmac<T>(v, x, uns[(i * N1 + j1) * 32 + lane]);
+          c2<T>& acc = accs[(i * N1 + j1) * 32 + lane];  // row j1 belongs to this warp alone
+          const c2<T> cu = cj_mul<T>(x, u);
+          acc.x += cu.x;
+          acc.y += cu.y;
+        }
+        ubm[off] = v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < A * N1 * 32; e += blockDim.x) {
+    const int i = e / (N1 * 32), r = e % (N1 * 32), j1 = r >> 5, l = r & 31;
+    const int jj = blockIdx.x * 32 + l;
+    if (jj < N23) part[((int64_t)blockIdx.y * A + i) * Nr + (int64_t)j1 * N23 + jj] = accs[e];
+  }
+}
+
+// ubar_n_i[j] += sum_s part[s][i][j], slices in order
+template <typename T>
+__global__ void adj_part_reduce_kernel(const c2<T>* __restrict__ part, int S, int A, int64_t Nr, c2<T>* __restrict__ Ub0,
+                                       c2<T>* __restrict__ Ub1) {
+  const int64_t total = (int64_t)A * Nr;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(id / Nr);
+    const int64_t j = id % Nr;
+    c2<T>* ub = (i ? Ub1 : Ub0) + j;
+    c2<T> acc = *ub;
+    for (int sl = 0; sl < S; ++sl) {
+      const c2<T> v = part[((int64_t)sl * A + i) * Nr + j];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    *ub = acc;
+  }
+}
+
+template <typename T>
+size_t adj_stageA_fused_smem(int N1, int n1, int A) {
+  const int ni = n1 <= 8 ? 8 : n1 <= 12 ? 12 : n1 <= 14 ? 14 : 16;
+  return sizeof(c2<T>) * ((size_t)N1 * ni + 2 * (size_t)A * N1 * 32);
+}
+
+// Slices of the chunk's m per column tile: about four blocks per SM in all.
+int adj_stageA_fused_slices(int mc, int N23) {
+  const int gx = (N23 + 31) / 32;
+  return std::max(1, std::min(mc, (4 * 152 + gx - 1) / gx));
+}
+
+template <typename T, int NI, int A>
+static cudaError_t adj_fused_launch(const c2<T>* T1, int mc, int n1, int N1, int N23, const c2<T>* tw,
+                                    const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
+                                    c2<T>* Ubar_kp, c2<T>* part, int S, size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(adj_stageA_fused_kernel<T, NI, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  adj_stageA_fused_kernel<T, NI, A><<<dim3((N23 + 31) / 32, S), 32 * ADJA_WARPS, smem, s>>>(
+      T1, mc, n1, N1, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part);
+  return cudaGetLastError();
+}
+
+// A in {1, 2}, n1 <= 16, shared memory within 200 KB (adj_stageA_fused_smem);
+// part holds S * A * N1 * N23 elements, S = adj_stageA_fused_slices(mc, N23).
+template <typename T>
+cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int N1, int N23, const c2<T>* tw,
+                                    const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
+                                    c2<T>* Ubar_kp, c2<T>* Ubar_n0, c2<T>* Ubar_n1, c2<T>* part, cudaStream_t s) {
+  if (mc == 0 || N23 == 0 || N1 == 0) return cudaSuccess;
+  const size_t smem = adj_stageA_fused_smem<T>(N1, n1, A);
+  if ((A != 1 && A != 2) || n1 < 1 || n1 > 16 || smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int S = adj_stageA_fused_slices(mc, N23);
+  cudaError_t e;
+#define ADJA_CASE(NI_)                                                                                          \
+  e = A == 2 ? adj_fused_launch<T, NI_, 2>(T1, mc, n1, N1, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part, S, smem, s) \
+             : adj_fused_launch<T, NI_, 1>(T1, mc, n1, N1, N23, tw, Un0, Un0, Ukp, Ridx, m0, Ubar_kp, part, S, smem, s)
+  if (n1 <= 8) ADJA_CASE(8);
+  else if (n1 <= 12) ADJA_CASE(12);
+  else if (n1 <= 14) ADJA_CASE(14);
+  else ADJA_CASE(16);
+#undef ADJA_CASE
+  if (e != cudaSuccess) return e;
+  const int64_t Nr = (int64_t)N1 * N23;
+  adj_part_reduce_kernel<T><<<gridx(A * Nr), 256, 0, s>>>(part, S, A, Nr, Ubar_n0, A == 2 ? Ubar_n1 : Ubar_n0);
+  return cudaGetLastError();
+}
+
 // Twiddles of the transposed transforms: tw[jc][o][jj] = exp(+2 pi i (lo + o)(16 jc + jj) / N)
 // (layout of the stage-B kernel with input axis o and 16 outputs j per chunk), and
 // the plain matrix tw[o][j] used by stage A^T.
@@ -912,10 +1122,14 @@ cudaError_t launch_gather_box(const c2<T>* box, int nb, int npw, const int* pos,
   template cudaError_t launch_nbar<T>(const c2<T>*, int64_t, int, const T*, const c2<T>*, int, c2<T>*, cudaStream_t);  \
   template cudaError_t launch_paw_adjoint<T>(const c2<T>*, const c2<T>*, const c2<T>*, int, int, int, int,             \
                                              const double2*, const int*, const int*, const int*, const int64_t*,       \
-                                             const int*, const int*, const int*, c2<T>*, double2*, double2*,           \
+                                             const int*, const int*, const int*, c2<T>*, double2*, double2*, double2*, \
                                              cudaStream_t);                                                            \
-  template cudaError_t launch_adj_stageC<T>(const c2<T>*, int, int64_t, int, int, int, const int*, const int*,         \
-                                            const int*, double, c2<T>*, cudaStream_t);                                 \
+  template cudaError_t launch_adj_stageC<T>(const c2<T>*, int, int64_t, int, int, int, int, int, const int*,          \
+                                            const int*, const int*, double, c2<T>*, cudaStream_t);                     \
+  template size_t adj_stageA_fused_smem<T>(int, int, int);                                                             \
+  template cudaError_t launch_adj_stageA_fused<T>(const c2<T>*, int, int, int, int, int, const c2<T>*, const c2<T>*,   \
+                                                  const c2<T>*, const c2<T>*, const int*, int, c2<T>*, c2<T>*, c2<T>*, \
+                                                  c2<T>*, cudaStream_t);                                               \
   template cudaError_t launch_adj_stageA<T>(const c2<T>*, int, int, int, int, const c2<T>*, const c2<T>*,              \
                                             const c2<T>*, const int*, int, int64_t, c2<T>*, c2<T>*, cudaStream_t);     \
   template cudaError_t launch_adj_un<T>(const c2<T>*, int, int64_t, const c2<T>*, const int*, int, int64_t, c2<T>*,    \

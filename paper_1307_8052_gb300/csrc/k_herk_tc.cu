@@ -155,6 +155,27 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Multicast form: the tile lands at the same shared-memory offset in every CTA
+// of ctaMask and completes bytes on the mbarrier at the same offset in each.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int k, int row,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(k), "r"(row), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of every CTA of the cluster
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // UMMA shared-memory descriptor of a K-major tile: 8-row core groups of
 // 8 * row-bytes; layout code 2 = 128-byte swizzle (BK = 64), 4 = 64-byte (BK = 32).
 template <int BK>
@@ -183,6 +204,14 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// arrive once on the mbarrier at this offset in every CTA of ctaMask when the
+// issued products are done
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "h"(mask)
                : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -262,7 +291,13 @@ struct GemmArgs {
   int64_t out_batch;  // elements between the outputs of consecutive batches
 };
 
-template <int TERMS, int BK, int STAGES, bool GEMM, bool FUSED>
+// CL = 2: the CTAs of a cluster pair are the same tile at frequencies 2c and
+// 2c + 1, whose B operand (X, Z: unweighted) is the same.  Each loads every
+// other B tile of a stage for both (TMA multicast), so a CTA fetches its A
+// tiles and half of B; a stage slot is reused once the products of both CTAs
+// have read it (each MMA commit arrives on the slot's barrier in both CTAs).
+// Same loads, products and order as CL = 1: chi0 is bit-identical.
+template <int TERMS, int BK, int STAGES, bool GEMM, bool FUSED, int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     herk_tc_kernel(const __grid_constant__ Maps maps, int NG, int NGpad, int nk, int fold, int flush, double2* __restrict__ chi,
                    int* __restrict__ err, const GemmArgs ga, const Ctl ctl) {
@@ -270,6 +305,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   constexpr int TILE_BYTES = C::TILE_BYTES;
   constexpr int AST = C::AST;
   static_assert(!FUSED || (TERMS == 2 && BK == 64 && !GEMM), "fused weighting: two terms, 64-element stages");
+  static_assert(CL == 1 || (CL == 2 && !GEMM && !FUSED), "B multicast: the stored-operand rank-k form only");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES);  // stage (fused: B rows) landed
@@ -299,7 +335,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int s = 0; s < AST; ++s) {
       mbar_init(&conv[s], CONV_WARPS);
@@ -321,6 +357,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // the peer's barriers are initialised before any multicast reaches them
+  if constexpr (CL > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -368,12 +406,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int t = 0; t < TERMS; ++t) tma_load_2d(at + t * TILE_BYTES, &maps.a[t], &full[s], k, arow);
         }
         unsigned char* bt = C::b_ptr(smem, s);
+        if constexpr (CL > 1) {
+          // rank 0 the X tiles, rank 1 the Z tiles, each for both CTAs
+          const uint32_t r = cluster_rank();
 #pragma unroll
-        for (int t = 0; t < TERMS; ++t) {
-          tma_load_2d(bt + (2 * t) * TILE_BYTES, &maps.x[t], &full[s], k, brow);
-          tma_load_2d(bt + (2 * t + 1) * TILE_BYTES, &maps.z[t], &full[s], k, brow);
+          for (int t = 0; t < TERMS; ++t)
+            tma_load_2d_mc(bt + (2 * t + r) * TILE_BYTES, r ? &maps.z[t] : &maps.x[t], &full[s], k, brow, 0x3);
+        } else {
+#pragma unroll
+          for (int t = 0; t < TERMS; ++t) {
+            tma_load_2d(bt + (2 * t) * TILE_BYTES, &maps.x[t], &full[s], k, brow);
+            tma_load_2d(bt + (2 * t + 1) * TILE_BYTES, &maps.z[t], &full[s], k, brow);
+          }
         }
         issued = kb + 1;
+      }
+      // pair: both CTAs' products have released the last issued slots, so no
+      // arrival from the peer is still on its way to this CTA's barriers
+      if constexpr (CL > 1) {
+        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+          if (!mbar_wait_timer(&empty[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 7);
       }
       // every load already issued must land before the CTA may exit, also when
       // another role aborts after this loop ended: the last STAGES (AST)
@@ -432,7 +484,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             umma(d, da[2], db[0], idesc, 1u);
           }
         }
-        umma_commit(&empty[s]);
+        if constexpr (CL > 1)
+          umma_commit_mc(&empty[s], 0x3);
+        else
+          umma_commit(&empty[s]);
         if (FUSED) umma_commit(&emptyA[sa]);
         if ((kb % fold) == fold - 1 || kb == nk - 1) umma_commit(&tfull[b]);
       }
@@ -597,6 +652,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // neither CTA of a pair exits while the other may still address it
+  if constexpr (CL > 1) cluster_sync_all();
   tc_fence_after();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -1281,7 +1338,7 @@ size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int terms, int fused) {
 
 template <int TERMS, int BK, int STAGES, bool FUSED>
 static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpad, int64_t Kpad, int fold64, int flush,
-                               double2* chi, int* err, const tc::Ctl& ctl, cudaStream_t s) {
+                               double2* chi, int* err, const tc::Ctl& ctl, cudaStream_t s, bool pair = false) {
   using namespace tc;
   using C = Cfg<TERMS, BK, STAGES, FUSED>;
   static_assert(C::SMEM_BYTES <= 227 * 1024, "shared-memory ring too large");
@@ -1290,10 +1347,33 @@ static cudaError_t launch_gemm(const tc::Maps& maps, dim3 grid, int NG, int NGpa
   // with three terms (six products per element) a unit is 32 elements, so a
   // fold holds the same number of truncating tensor-core accumulations
   const int fold = TERMS == 3 ? fold64 * (32 / BK) : fold64 * (64 / BK);
-  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<TERMS, BK, STAGES, false, FUSED>,
+  if constexpr (!FUSED && TERMS == 2 && BK == 64) {
+    if (pair) {
+      // clusters of two frequencies sharing the B tiles (grid.y even)
+      if (grid.y % 2) return cudaErrorInvalidValue;
+      auto kern = herk_tc_kernel<TERMS, BK, STAGES, false, false, 2>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg;
+      memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.dynamicSmemBytes = C::SMEM_BYTES;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 1;
+      attr[0].val.clusterDim.y = 2;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, kern, maps, NG, NGpad, nk, fold, flush, chi, err, GemmArgs{}, ctl);
+    }
+  }
+  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel<TERMS, BK, STAGES, false, FUSED, 1>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  herk_tc_kernel<TERMS, BK, STAGES, false, FUSED><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(
+  herk_tc_kernel<TERMS, BK, STAGES, false, FUSED, 1><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(
       maps, NG, NGpad, nk, fold, flush, chi, err, GemmArgs{}, ctl);
   return cudaGetLastError();
 }
@@ -1352,8 +1432,8 @@ cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt
 }
 
 cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fused, int fold_stages, int flush_folds, int pipe,
-                        int64_t wait_us, int stall_stage, double2* chi, void* scratch, size_t scratch_bytes, int* err,
-                        cudaStream_t s) {
+                        int pair, int64_t wait_us, int stall_stage, double2* chi, void* scratch, size_t scratch_bytes,
+                        int* err, cudaStream_t s) {
   using namespace tc;
   if (P == 0 || NG == 0 || nw == 0) return cudaSuccess;
   fused = fused && terms == 2 && pipe == 0;
@@ -1391,7 +1471,8 @@ cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fused, int fol
     return launch_gemm<2, 32, 4, false>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s);
   if (fused)
     return launch_gemm<2, 64, 2, true>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s);
-  return launch_gemm<2, 64, 2, false>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s);
+  return launch_gemm<2, 64, 2, false>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s,
+                                      pair && nw % 2 == 0);
 }
 
 // Controls of the batched-product launches: the default wait limit, no stall.
@@ -1597,17 +1678,17 @@ cudaError_t nbar_tc_run(const float2* N, const float* wgt, int64_t P, int NG, in
   cudaError_t e;
   if (terms == 3) {
     using C = Cfg<3, 32, 3>;
-    if ((e = cudaFuncSetAttribute(herk_tc_kernel<3, 32, 3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<3, 32, 3, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   C::SMEM_BYTES)) != cudaSuccess)
       return e;
-    herk_tc_kernel<3, 32, 3, true, false><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+    herk_tc_kernel<3, 32, 3, true, false, 1><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
                                                                            ga, gemm_ctl());
   } else {
     using C = Cfg<2, 64, 2>;
-    if ((e = cudaFuncSetAttribute(herk_tc_kernel<2, 64, 2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<2, 64, 2, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   C::SMEM_BYTES)) != cudaSuccess)
       return e;
-    herk_tc_kernel<2, 64, 2, true, false><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+    herk_tc_kernel<2, 64, 2, true, false, 1><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
                                                                            ga, gemm_ctl());
   }
   return cudaGetLastError();
@@ -1672,17 +1753,17 @@ cudaError_t paw_tc_run(const float2* Pm, const float2* R, int KP, int nL, int nR
   cudaError_t e;
   if (terms == 3) {
     using C = Cfg<3, 32, 3>;
-    if ((e = cudaFuncSetAttribute(herk_tc_kernel<3, 32, 3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<3, 32, 3, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   C::SMEM_BYTES)) != cudaSuccess)
       return e;
-    herk_tc_kernel<3, 32, 3, true, false><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+    herk_tc_kernel<3, 32, 3, true, false, 1><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
                                                                            ga, gemm_ctl());
   } else {
     using C = Cfg<2, 64, 2>;
-    if ((e = cudaFuncSetAttribute(herk_tc_kernel<2, 64, 2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(herk_tc_kernel<2, 64, 2, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   C::SMEM_BYTES)) != cudaSuccess)
       return e;
-    herk_tc_kernel<2, 64, 2, true, false><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
+    herk_tc_kernel<2, 64, 2, true, false, 1><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(maps, NG, NGpad, nk, 1, 1, nullptr, err,
                                                                            ga, gemm_ctl());
   }
   return cudaGetLastError();

@@ -23,8 +23,8 @@ namespace rpa {
 cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt, int nw, int split_terms, int fused,
                             void* scratch, size_t scratch_bytes, cudaStream_t s);
 cudaError_t herk_tc_run(int64_t P, int NG, int nw, int split_terms, int fused, int fold_stages, int flush_folds, int pipe,
-                        int64_t wait_us, int stall_stage, double2* chi, void* scratch, size_t scratch_bytes, int* err,
-                        cudaStream_t s);
+                        int pair, int64_t wait_us, int stall_stage, double2* chi, void* scratch, size_t scratch_bytes,
+                        int* err, cudaStream_t s);
 size_t herk_tc_scratch_bytes(int64_t P, int NG, int nw, int split_terms, int fused);
 // persistent launch of many two-term k-blocks (k_herk_tc.cu)
 int herk_tc_batch_max_jobs();
@@ -57,10 +57,18 @@ template <typename T>
 cudaError_t launch_paw_adjoint(const c2<T>* Nbar, const c2<T>* R, const c2<T>* Pm, int nL, int nR, int NG, int KP,
                                const double2* Q, const int* atom_of_kp, const int* idx_in_atom, const int* atom_off,
                                const int64_t* q_off, const int* nproj, const int* Lidx, const int* Ridx, c2<T>* Ywork,
-                               double2* gPk, double2* gPkp, cudaStream_t s);
+                               double2* part, double2* gPk, double2* gPkp, cudaStream_t s);
 template <typename T>
-cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int ncol, int N3, const int* col_start,
-                              const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2, cudaStream_t s);
+cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int mc, int nR, int ncol, int N3,
+                              const int* col_start, const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2,
+                              cudaStream_t s);
+template <typename T>
+size_t adj_stageA_fused_smem(int N1, int n1, int A);
+int adj_stageA_fused_slices(int mc, int N23);
+template <typename T>
+cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int N1, int N23, const c2<T>* tw,
+                                    const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
+                                    c2<T>* Ubar_kp, c2<T>* Ubar_n0, c2<T>* Ubar_n1, c2<T>* part, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_stageA(const c2<T>* T1, int np, int n1, int N1, int N23, const c2<T>* tw, const c2<T>* Un,
                               const c2<T>* Ukp, const int* Ridx, int nR, int64_t p0, c2<T>* Ubar_kp, c2<T>* Xbar,
@@ -162,7 +170,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 0};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 2, 0};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -475,7 +483,8 @@ bool tc_fused(const rpa_ctx* c) {
 // herk_tc_run with the context's knobs
 cudaError_t run_herk_tc(rpa_ctx* c, int64_t P, int NG, int nw, int terms, double2* chi, void* scr, size_t sb) {
   return herk_tc_run(P, NG, nw, terms, tc_fused(c) ? 1 : 0, (int)c->tune[RPA_TUNE_TC_FOLD],
-                     (int)c->tune[RPA_TUNE_TC_FLUSH], (int)c->tune[RPA_TUNE_TC_PIPE], c->tune[RPA_TUNE_TC_WAIT_US],
+                     (int)c->tune[RPA_TUNE_TC_FLUSH], (int)c->tune[RPA_TUNE_TC_PIPE], (int)c->tune[RPA_TUNE_TC_PAIR],
+                     c->tune[RPA_TUNE_TC_WAIT_US],
                      (int)c->tune[RPA_TUNE_TC_STALL] - 1, chi, scr, sb, c->dev_err, c->stream);
 }
 
@@ -970,11 +979,13 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
     tm.add_launches(pawo ? 7 : 3);
   }
   if (B.KP > 0) {
+    void* p_pp;
     if ((st = workspace(c, "paw_y", sizeof(c2<T>) * (size_t)nL * B.KP * NG, &p_y)) != RPA_OK) return st;
+    if ((st = workspace(c, "paw_pkp", sizeof(double2) * (size_t)nL * nR * B.KP, &p_pp)) != RPA_OK) return st;
     CUDA_OK(c, launch_paw_adjoint<T>(Nbar, B.R, B.Pm, nL, nR, NG, B.KP, Q.Q, B.atom_of, B.idx_in, B.atom_off,
-                                     B.q_off, B.nproj, B.Lsub, skp.R_d, (c2<T>*)p_y, A.gP[Q.k_of[t]],
-                                     A.gP[Q.kq_of[t]], c->stream));
-    tm.add_launches(3);
+                                     B.q_off, B.nproj, B.Lsub, skp.R_d, (c2<T>*)p_y, (double2*)p_pp,
+                                     A.gP[Q.k_of[t]], A.gP[Q.kq_of[t]], c->stream));
+    tm.add_launches(4);
   }
   // sphere points grouped by (g1, g2) column for the transposed fastest-axis transform
   const int ncol = n1 * n2;
@@ -1002,25 +1013,47 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
   if ((st = workspace(c, "tw_adjA", sizeof(c2<T>) * (size_t)n1 * N1, &p_twa)) != RPA_OK) return st;
   CUDA_OK(c, launch_twiddle_adj<T>((c2<T>*)p_twb, N2, B.glo[1], n2, 1, c->stream));
   CUDA_OK(c, launch_twiddle_adj<T>((c2<T>*)p_twa, N1, B.glo[0], n1, 0, c->stream));
-  // chunks never straddle an occupied band, so every chunk shares u_n
-  const int64_t PCb = std::max<int64_t>(1, std::min<int64_t>(B.PC, nR));
-  if ((st = workspace(c, "Xbar", sizeof(c2<T>) * (size_t)(PCb * Nr), &p_xbar)) != RPA_OK) return st;
   c2<T>* ub_k = (c2<T>*)A.ubar[Q.k_of[t]];
   c2<T>* ub_kp = (c2<T>*)A.ubar[Q.kq_of[t]];
-  for (int a = 0; a < nL; ++a) {
-    for (int m0 = 0; m0 < nR; m0 += (int)PCb) {
-      const int np = (int)std::min<int64_t>(PCb, nR - m0);
+  const int64_t PCb = std::max<int64_t>(1, std::min<int64_t>(B.PC, nR));
+  // Stage A^T fused with both products where it applies (x-bar stays on chip):
+  // chunks of two occupied bands x mc unoccupied bands (one ubar_m update
+  // for both), else one band; otherwise x-bar through memory, one band per chunk.
+  const bool fused = n1 <= 16 && adj_stageA_fused_smem<T>(N1, n1, 1) <= 200 * 1024;
+  const int Aw = fused && nL >= 2 && PCb >= 2 && adj_stageA_fused_smem<T>(N1, n1, 2) <= 200 * 1024 ? 2 : 1;
+  const int MC = (int)(PCb / Aw);
+  if (fused) {
+    const size_t pe = (size_t)adj_stageA_fused_slices(MC, (int)N23) * Aw * Nr;
+    if ((st = workspace(c, "adj_part", sizeof(c2<T>) * pe, &p_xbar)) != RPA_OK) return st;
+  } else if ((st = workspace(c, "Xbar", sizeof(c2<T>) * (size_t)(PCb * Nr), &p_xbar)) != RPA_OK) {
+    return st;
+  }
+  for (int a = 0; a < nL;) {
+    const int na = std::min(Aw, nL - a);
+    const c2<T>* un0 = (const c2<T>*)sk.U + (int64_t)sk.L[B.a0 + a] * Nr;
+    const c2<T>* un1 = (const c2<T>*)sk.U + (int64_t)sk.L[B.a0 + a + na - 1] * Nr;
+    for (int m0 = 0; m0 < nR; m0 += MC) {
+      const int mc = std::min(MC, nR - m0);
+      const int np = na * mc;
       const int64_t p0 = (int64_t)a * nR + m0;
-      CUDA_OK(c, launch_adj_stageC<T>(Nbar, NG, p0, np, ncol, N3, col_start, col_g, col_g3, 1.0 / (double)Nr, B.T2,
-                                      c->stream));
+      CUDA_OK(c, launch_adj_stageC<T>(Nbar, NG, p0, np, mc, nR, ncol, N3, col_start, col_g, col_g3,
+                                      1.0 / (double)Nr, B.T2, c->stream));
       CUDA_OK(c, launch_pd_stageB<T>(B.T2, B.T1, np, n1, n2, N3, (const c2<T>*)p_twb, N2, c->stream));
-      CUDA_OK(c, launch_adj_stageA<T>(B.T1, np, n1, N1, (int)N23, (const c2<T>*)p_twa,
-                                      (const c2<T>*)sk.U + (int64_t)sk.L[B.a0 + a] * Nr, (const c2<T>*)skp.U, skp.R_d, nR,
-                                      p0, ub_kp, (c2<T>*)p_xbar, c->stream));
-      CUDA_OK(c, launch_adj_un<T>((const c2<T>*)p_xbar, np, Nr, (const c2<T>*)skp.U, skp.R_d, nR, p0,
-                                  ub_k + (int64_t)sk.L[B.a0 + a] * Nr, c->stream));
+      if (fused) {
+        CUDA_OK(c, launch_adj_stageA_fused<T>(B.T1, na, mc, n1, N1, (int)N23, (const c2<T>*)p_twa, un0, un1,
+                                              (const c2<T>*)skp.U, skp.R_d, m0, ub_kp,
+                                              ub_k + (int64_t)sk.L[B.a0 + a] * Nr,
+                                              ub_k + (int64_t)sk.L[B.a0 + a + na - 1] * Nr, (c2<T>*)p_xbar,
+                                              c->stream));
+      } else {
+        CUDA_OK(c, launch_adj_stageA<T>(B.T1, np, n1, N1, (int)N23, (const c2<T>*)p_twa, un0, (const c2<T>*)skp.U,
+                                        skp.R_d, nR, p0, ub_kp, (c2<T>*)p_xbar, c->stream));
+        CUDA_OK(c, launch_adj_un<T>((const c2<T>*)p_xbar, np, Nr, (const c2<T>*)skp.U, skp.R_d, nR, p0,
+                                    ub_k + (int64_t)sk.L[B.a0 + a] * Nr, c->stream));
+      }
       tm.add_launches(4);
     }
+    a += na;
   }
   return RPA_OK;
 }
@@ -1137,7 +1170,7 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
     {
       StageTimer tm(c, 3, 0);
       // (1 - M)^-1: FP64 in the FP64 mode and with RPA_TUNE_GAMMA = 0; in the
-      // mixed modes float-float products (2) or the FP32 product form (1)
+      // mixed modes float-float products (2, default) or the FP32 product form (1)
       const int64_t gm = sizeof(T) == 8 ? 0 : c->tune[RPA_TUNE_GAMMA];
       if (gm == 0)
         CUDA_OK(c, run_gamma((const double2*)p_work, Q.v_d, (const double*)p_cw, nw, NG, (double2*)p_Y,
@@ -2017,10 +2050,12 @@ struct rpa_graph {
 namespace {
 
 // Units, jobs and groups of a batch (host only; sizes from the contexts' state).
-rpa_status plan_batch(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int32_t* nq, const int32_t* iqs) {
+rpa_status plan_batch(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int32_t* nq, const int32_t* iqs,
+                      size_t budget) {
   g->units.clear();
   g->jobs.clear();
   g->groups.clear();
+  g->pool_bytes = 0;
   int64_t off = 0;
   for (int i = 0; i < n; ++i) {
     rpa_ctx* c = ctxs[i];
@@ -2055,7 +2090,6 @@ rpa_status plan_batch(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int32_t* 
     off += nq[i];
   }
   // groups: consecutive jobs under the budget (a larger job forms its own group)
-  const size_t budget = (size_t)ctxs[0]->tune[RPA_TUNE_BATCH_MB] << 20;
   const int maxj = herk_tc_batch_max_jobs();
   size_t used = 0;
   int first = 0;
@@ -2110,7 +2144,8 @@ rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int3
       if (U.g_first != gi) continue;
       rpa_ctx* c = ctxs[U.ctx];
       QPt& Q = c->qpts[U.iq];
-      const std::string key = "chiq" + std::to_string(U.iq);
+      // a context's first q-point shares the chi0 buffer of its own evaluations
+      const std::string key = U.pos == 0 ? std::string("chi") : "chiq" + std::to_string(U.iq);
       void* p;
       const size_t bytes = sizeof(double2) * (size_t)c->nw_set * Q.NG * Q.NG;
       if ((st = workspace(c, key.c_str(), bytes, &p)) != RPA_OK) return st;
@@ -2213,13 +2248,26 @@ rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq, 
     return st;
   };
   if (persist) {
-    plan_batch(g, ctxs, n, nq, iqs);
     std::vector<int*> dst(n);
     for (int i = 0; i < n; ++i) dst[i] = ctxs[i]->dev_err;
     if (cudaMalloc(&g->dev, 2 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&g->err_dst, sizeof(int*) * n) != cudaSuccess ||
-        (g->pool_bytes && cudaMalloc(&g->pool, g->pool_bytes) != cudaSuccess))
-      return bail(fail(ctxs[0], RPA_ERR_OOM, "batched graph buffers (%zu bytes) could not be allocated", g->pool_bytes));
+        cudaMalloc((void**)&g->err_dst, sizeof(int*) * n) != cudaSuccess)
+      return bail(fail(ctxs[0], RPA_ERR_OOM, "batched graph buffers could not be allocated"));
+    // the operand budget is an upper bound: where the device has less free,
+    // halve it (more, smaller groups) down to the largest single job
+    size_t budget = (size_t)ctxs[0]->tune[RPA_TUNE_BATCH_MB] << 20;
+    for (;;) {
+      plan_batch(g, ctxs, n, nq, iqs, budget);
+      if (!g->pool_bytes || cudaMalloc(&g->pool, g->pool_bytes) == cudaSuccess) break;
+      cudaGetLastError();
+      g->pool = nullptr;
+      size_t largest = 0;
+      for (const BatchJobPlan& J : g->jobs) largest = std::max(largest, J.sb);
+      if (budget <= largest)
+        return bail(fail(ctxs[0], RPA_ERR_OOM, "batched graph operand pool (%zu bytes) could not be allocated",
+                         g->pool_bytes));
+      budget = std::max(budget / 2, largest);
+    }
     if (cudaMemcpy(g->err_dst, dst.data(), sizeof(int*) * n, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(RPA_ERR_CUDA);
   }
@@ -2356,6 +2404,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_GAMMA:
       if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "gradient precision choice must be 0, 1 or 2");
+      break;
+    case RPA_TUNE_TC_PAIR:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "paired rank-k launch must be 0 or 1");
       break;
     case RPA_TUNE_BATCH_MB:
       if (value < 1 || value > (1 << 22)) return fail(c, RPA_ERR_ARG, "batch group budget %lld MiB out of range", (long long)value);

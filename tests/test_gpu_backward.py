@@ -184,9 +184,12 @@ def test_config4_full_bands_mixed_against_fp64_gradient():
     dE/dchi0 of the FP32 and split-bfloat16 (bf16x2) modes against the FP64
     mode's gradient (itself checked against central differences and the
     oracle), errors relative to the largest entry, with dE/dchi0 formed in FP64
-    (default), on the FP32 pipe (RPA_TUNE_GAMMA = 1) and in float-float (2).  Measured on a
-    GB300: FP32 mode 4.3e-7 / 3.2e-7 / 5.8e-8 (dC / dP / dchi), bf16x2 2.9e-6 /
-    5.5e-7 / 2.2e-7; with the FP32 form 3e-4 / 4e-4 / 1.2e-5 in both."""
+    (RPA_TUNE_GAMMA = 0), on the FP32 pipe (1) and in float-float (2, the
+    default).  Measured on a GB300: FP32 mode 4.3e-7 / 3.2e-7 / 5.8e-8 (dC / dP
+    / dchi), bf16x2 2.9e-6 / 5.5e-7 / 2.2e-7 with the FP64 and the float-float
+    form alike; with the FP32 form 3e-4 / 4e-4 / 1.2e-5.  The float-float
+    gradient must also agree with the FP64-form gradient of the same mode far
+    below those errors."""
     full = syn.config1()
     iq = [i for i, qp in enumerate(full.qpoints) if np.allclose(qp.q_red, [0.5, 0.0, 0.0])][0]
     p = syn.Problem(full.name, 4, full.cell, full.grid, full.ecut_wf, full.ecut_chi, full.spin_factor,
@@ -214,3 +217,14 @@ def test_config4_full_bands_mixed_against_fp64_gradient():
               f"E {eE:.2e}, dC {eC:.2e}, dP {eP:.2e}, dchi {ech:.2e}")
         bE, bC, bP, bch = bounds[key]
         assert eE <= bE and eC <= bC and eP <= bP and ech <= bch, (key, eE, eC, eP, ech)
+    # float-float against FP64 products, same mode: only the Gamma products
+    # differ; dE/dchi0 itself to ~2^-44, dE/dC and dE/dP through the FP32
+    # rounding of Gamma that feeds the N-bar product (a last-bit flip here and
+    # there)
+    _, dCf, dPf, dchif = res[("bf16x2", 2)]
+    _, dCd, dPd, dchid = res[("bf16x2", 0)]
+    ech = _rel(dchif[0], dchid[0])
+    eCP = max(max(_rel(dCf[s], dCd[s]) for s in range(len(p.sets))),
+              max(_rel(dPf[s], dPd[s]) for s in range(len(p.sets))))
+    print(f"config-4 full bands bf16x2, float-float vs FP64 products: dchi {ech:.2e}, dC/dP {eCP:.2e}")
+    assert ech <= 1e-10 and eCP <= 1e-7, (ech, eCP)

@@ -1,6 +1,8 @@
 """The tensor-core rank-k update (Eq. 17) through the C ABI: the fused
 frequency weighting against the form that stores weighted operands for every
-frequency, and the bounded-wait failure path.
+frequency, the paired launch (two frequencies per cluster sharing the
+unweighted operand tiles by TMA multicast) against the unpaired one, and the
+bounded-wait failure path.
 
 The fused form (converter warps scale the staged FP32 pair densities by
 w_p(w) of Eq. 16 and split them inside the kernel) performs the same FP32
@@ -40,21 +42,24 @@ def _rel(a, ref):
     return np.abs(a - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("case", ["config0", "mesh_umklapp_paw", "bulk_subset"])
-def test_fused_weighting_bit_identical(case):
+def _case(case):
     # config 0: NG 139 (two row tiles, ragged), 240 pairs (not a multiple of 32);
     # a small mesh with umklapp and PAW; the bulk geometry (NG ~ 1200, ten row
     # tiles) on a band subset with two transitions
     if case == "config0":
-        p, iq, nw = syn.config0(), 0, 8
-    elif case == "mesh_umklapp_paw":
-        p, iq, nw = syn.small_problem(config_tag=95), 1, 5
-    else:
-        p = syn.config1(nocc=3, nunocc=70)
-        p.qpoints = [p.qpoints[3]]
-        p.qpoints[0].k_of, p.qpoints[0].kq_of = p.qpoints[0].k_of[:2], p.qpoints[0].kq_of[:2]
-        p.qpoints[0].G0 = p.qpoints[0].G0[:2]
-        iq, nw = 0, 16
+        return syn.config0(), 0, 8
+    if case == "mesh_umklapp_paw":
+        return syn.small_problem(config_tag=95), 1, 5
+    p = syn.config1(nocc=3, nunocc=70)
+    p.qpoints = [p.qpoints[3]]
+    p.qpoints[0].k_of, p.qpoints[0].kq_of = p.qpoints[0].k_of[:2], p.qpoints[0].kq_of[:2]
+    p.qpoints[0].G0 = p.qpoints[0].G0[:2]
+    return p, 0, 16
+
+
+@pytest.mark.parametrize("case", ["config0", "mesh_umklapp_paw", "bulk_subset"])
+def test_fused_weighting_bit_identical(case):
+    p, iq, nw = _case(case)
     om, W = o.frequency_grid(nw)
     ctx = _ctx(p, "bf16x2")
     try:
@@ -78,8 +83,32 @@ def test_fused_weighting_bit_identical(case):
         assert _rel(fused, o.chi0(p, iq, om, Q)) < 2e-5
 
 
-@pytest.mark.parametrize("precision,fuse", [("bf16x2", 1), ("bf16x2", 0), ("bf16x3", 0)])
-def test_bounded_wait_timeout_leaves_context_usable(precision, fuse):
+@pytest.mark.parametrize("case", ["config0", "mesh_umklapp_paw", "bulk_subset"])
+def test_paired_launch_bit_identical(case):
+    # 8 and 16 frequencies run paired; 5 (odd) falls back to the unpaired launch
+    p, iq, nw = _case(case)
+    om, W = o.frequency_grid(nw)
+    ctx = _ctx(p, "bf16x2")
+    try:
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FUSE, 0)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 0)
+        single = b.rpa_chi0(ctx, iq, om)
+        Es, ts = b.rpa_energy(ctx, [iq], [1.0], om, W)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 1)
+        paired = b.rpa_chi0(ctx, iq, om)
+        Ep, tp = b.rpa_energy(ctx, [iq], [1.0], om, W)
+        with pytest.raises(b.RpaError) as e:
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 2)
+        assert e.value.status == b.RPA_ERR_ARG
+    finally:
+        b.rpa_destroy(ctx)
+    assert np.array_equal(paired, single)
+    assert np.array_equal(tp, ts) and Ep == Es
+
+
+@pytest.mark.parametrize("precision,fuse,pair", [("bf16x2", 1, 0), ("bf16x2", 0, 0), ("bf16x2", 0, 1),
+                                                ("bf16x3", 0, 0)])
+def test_bounded_wait_timeout_leaves_context_usable(precision, fuse, pair):
     p = syn.config0()
     om, W = o.frequency_grid(p.nw)
     ref = o.chi0(p, 0, om)
@@ -87,6 +116,7 @@ def test_bounded_wait_timeout_leaves_context_usable(precision, fuse):
     ctx = _ctx(p, precision)
     try:
         b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FUSE, fuse)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, pair)
         with pytest.raises(b.RpaError) as e:
             b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_WAIT_US, 999)
         assert e.value.status == b.RPA_ERR_ARG
