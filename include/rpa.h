@@ -374,13 +374,15 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      with ~1e-5 relative error in dE/dchi0 and ~3e-4 in
  *                      dE/dC and dE/dP on the bulk gradient workload (FP64:
  *                      <= 3e-6).
- * RPA_TUNE_TC_PAIR    1: the stored-operand two-term rank-k kernel (RPA_BF16X2
- *                      with RPA_TUNE_TC_FUSE = 0 and RPA_TUNE_TC_PIPE = 0)
- *                      runs as clusters of two CTAs, one tile at two
- *                      frequencies; the pair shares the unweighted operand
- *                      tiles, each CTA loading half of them into both by TMA
- *                      multicast.  Bit-identical to 0.  An odd number of
- *                      frequencies runs unpaired.
+ * RPA_TUNE_TC_PAIR    the stored-operand two-term rank-k kernel (RPA_BF16X2
+ *                      with RPA_TUNE_TC_FUSE = 0 and RPA_TUNE_TC_PIPE = 0):
+ *                      0 one CTA per tile; 1 clusters of two CTAs, one tile
+ *                      at two frequencies, sharing the unweighted operand
+ *                      tiles by TMA multicast (an odd number of frequencies
+ *                      runs unpaired); 2 two-SM products (tcgen05
+ *                      cta_group::2, M = 256) over pairs of row tiles, each
+ *                      SM staging half of the unweighted operand.  All three
+ *                      give the same chi0 bit for bit.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,

@@ -266,9 +266,14 @@ __global__ void gamma_kernel(const double2* __restrict__ Wm, const double* __res
 // outputs FP64, each FP64 element split into hi + lo FP32 on load, every
 // complex multiply-add an exact FMA two-product with two-sum accumulation
 // (about 44 significant bits; the FP32 pipe instead of the FP64 one).
-// GRAM = false: C[z] = beta C[z] + alpha A[z] B[z] (A M x K, B K x N, row-major).
+// GRAM = false: C[z] = beta C[z] + alpha A[z] B[z] (A M x K, B K x N, row-major);
+// with tri, B is lower triangular (B[k][j] = 0 for k < j), so a column tile
+// starting at n0 sums k from n0.
 // GRAM = true:  W[z] = Y^H Y on lower-triangle tiles, k from the tile's first
 // row (Y lower triangular).
+// A BM x (4096 / BM) tile per block of 256 threads, 4 x 4 outputs a thread;
+// the FP64 elements of the next K slice are fetched into registers while the
+// current slice (split into hi + lo in shared memory) is multiplied.
 __device__ __forceinline__ void ffc_mac(float4& acc, float4 a, float4 b) {
   // re += a.re b.re - a.im b.im, im += a.re b.im + a.im b.re
   ff_mac(acc.x, acc.y, a.x, a.y, b.x, b.y);
@@ -277,63 +282,93 @@ __device__ __forceinline__ void ffc_mac(float4& acc, float4 a, float4 b) {
   ff_mac(acc.z, acc.w, a.z, a.w, b.x, b.y);
 }
 
-template <bool GRAM>
+template <bool GRAM, int BMt>
 __global__ void __launch_bounds__(256) gemm_ff_kernel(int M, int N, int K, double2 alpha, const double2* __restrict__ A,
                                                       int64_t lda, int64_t sA, const double2* __restrict__ B,
                                                       int64_t ldb, int64_t sB, double2 beta, double2* __restrict__ C,
-                                                      int64_t ldc, int64_t sC) {
-  __shared__ float4 As[ZK][ZT];
-  __shared__ float4 Bs[ZK][ZT];
+                                                      int64_t ldc, int64_t sC, int tri) {
+  constexpr int BNt = 4096 / BMt;
+  constexpr int TX = BNt / 4, TY = BMt / 4;  // thread grid TY x TX
+  constexpr int LA = ZK * BMt / 256, LB = ZK * BNt / 256;
+  static_assert(!GRAM || BMt == 64, "Gram tiles are square");
+  __shared__ float4 As[ZK][BMt + 1];
+  __shared__ float4 Bs[ZK][BNt];
   const int z = GRAM ? blockIdx.y : blockIdx.z;
   A += z * sA;
   B += z * sB;
   C += z * sC;
-  int m0, n0, kbeg = 0;
+  int m0, n0, kbeg;
   if constexpr (GRAM) {
     int ti, tj;
     lower_tile(blockIdx.x, ti, tj);
-    m0 = ti * ZT;
-    n0 = tj * ZT;
+    m0 = ti * BMt;
+    n0 = tj * BNt;
     kbeg = m0;  // Y[k][i] = 0 for k < i
   } else {
-    m0 = blockIdx.y * ZT;
-    n0 = blockIdx.x * ZT;
+    m0 = blockIdx.y * BMt;
+    n0 = blockIdx.x * BNt;
+    kbeg = tri ? n0 : 0;
   }
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  double2 pa[LA], pb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      double2 a = make_double2(0.0, 0.0);
+      if constexpr (GRAM) {
+        // A = Y^H: element (i = m0 + c, k) = conj(Y[k][i]), threads along i
+        const int kk = e / BMt, c = e % BMt;
+        if (k0 + kk < K && m0 + c < M) {
+          a = A[(int64_t)(k0 + kk) * lda + m0 + c];
+          a.y = -a.y;
+        }
+      } else {
+        // threads along k (rows of A are contiguous in k)
+        const int r = e / ZK, kk = e % ZK;
+        if (k0 + kk < K && m0 + r < M) a = A[(int64_t)(m0 + r) * lda + k0 + kk];
+      }
+      pa[q] = a;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int kk = e / BNt, c = e % BNt;
+      pb[q] = (k0 + kk < K && n0 + c < N) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : make_double2(0.0, 0.0);
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if constexpr (GRAM)
+        As[e / BMt][e % BMt] = ff_split(pa[q]);
+      else
+        As[e % ZK][e / ZK] = ff_split(pa[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      Bs[e / BNt][e % BNt] = ff_split(pb[q]);
+    }
+  };
   float4 acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (kbeg < K) fetch(kbeg);
   for (int k0 = kbeg; k0 < K; k0 += ZK) {
-#pragma unroll
-    for (int q = 0; q < (ZK * ZT) / 256; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int kk = e / ZT, c = e % ZT;
-      const bool kin = k0 + kk < K;
-      double2 a = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
-      if constexpr (GRAM) {
-        // A = Y^H: element (i = m0 + c, k) = conj(Y[k][i]); B = Y: (k, j = n0 + c)
-        if (kin && m0 + c < M) {
-          a = A[(int64_t)(k0 + kk) * lda + m0 + c];
-          a.y = -a.y;
-        }
-        if (kin && n0 + c < N) bv = B[(int64_t)(k0 + kk) * ldb + n0 + c];
-      } else {
-        if (kin && m0 + c < M) a = A[(int64_t)(m0 + c) * lda + k0 + kk];
-        if (kin && n0 + c < N) bv = B[(int64_t)(k0 + kk) * ldb + n0 + c];
-      }
-      As[kk][c] = ff_split(a);
-      Bs[kk][c] = ff_split(bv);
-    }
+    stash();
     __syncthreads();
+    if (k0 + ZK < K) fetch(k0 + ZK);
 #pragma unroll 4
     for (int kk = 0; kk < ZK; ++kk) {
       float4 a[4], b[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TY * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TX * c];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -345,7 +380,7 @@ __global__ void __launch_bounds__(256) gemm_ff_kernel(int M, int N, int K, doubl
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int m = m0 + ty + 16 * r, n = n0 + tx + 16 * c;
+      const int m = m0 + ty + TY * r, n = n0 + tx + TX * c;
       if (m >= M || n >= N || (GRAM && n > m)) continue;
       double2* p = C + (int64_t)m * ldc + n;
       const double2 a = ff_to_double(acc[r][c]);
@@ -364,24 +399,29 @@ cudaError_t run_gamma_ff(const double2* L, const double* v, const double* cw, in
   int64_t nl = 0;
   set_identity_kernel<double><<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Y, n, nw);
   ++nl;
+  // right-looking: solve a panel of FB rows, then take its contribution out
+  // of every row below it at once (a wide product with K = FB)
   for (int i0 = 0; i0 < n; i0 += FB) {
     const int b = (n - i0) < FB ? (n - i0) : FB;
-    if (i0 > 0) {
-      // Y[i0:i0+b, 0:i0] -= L[i0:i0+b, 0:i0] Y[0:i0, 0:i0]
-      dim3 grid((i0 + ZT - 1) / ZT, (b + ZT - 1) / ZT, nw);
-      gemm_ff_kernel<false><<<grid, 256, 0, s>>>(b, i0, i0, make_double2(-1.0, 0.0), L + (int64_t)i0 * n, n,
-                                                 (int64_t)n * n, Y, n, (int64_t)n * n, make_double2(1.0, 0.0),
-                                                 Y + (int64_t)i0 * n, n, (int64_t)n * n);
+    fwd_sub_diag_kernel<double><<<dim3((i0 + b + 63) / 64, nw), 64, 0, s>>>(L, Y, n, i0, b);
+    ++nl;
+    const int r0 = i0 + b;
+    if (r0 < n) {
+      // Y[r0:n, 0:r0] -= L[r0:n, i0:r0] Y[i0:r0, 0:r0]
+      dim3 grid((r0 + 63) / 64, (n - r0 + 63) / 64, nw);
+      gemm_ff_kernel<false, 64><<<grid, 256, 0, s>>>(n - r0, r0, b, make_double2(-1.0, 0.0),
+                                                     L + (int64_t)r0 * n + i0, n, (int64_t)n * n, Y + (int64_t)i0 * n,
+                                                     n, (int64_t)n * n, make_double2(1.0, 0.0), Y + (int64_t)r0 * n, n,
+                                                     (int64_t)n * n, 0);
       ++nl;
     }
-    fwd_sub_diag_kernel<double><<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
-    ++nl;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const int nt = (n + ZT - 1) / ZT;
-  gemm_ff_kernel<true><<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(n, n, n, make_double2(1.0, 0.0), Y, n,
-                                                                    (int64_t)n * n, Y, n, (int64_t)n * n,
-                                                                    make_double2(0.0, 0.0), Wm, n, (int64_t)n * n);
+  const int nt = (n + 63) / 64;
+  gemm_ff_kernel<true, 64><<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(n, n, n, make_double2(1.0, 0.0), Y, n,
+                                                                        (int64_t)n * n, Y, n, (int64_t)n * n,
+                                                                        make_double2(0.0, 0.0), Wm, n, (int64_t)n * n,
+                                                                        0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_hermitian_fill(Wm, nw, n, s)) != cudaSuccess) return e;
   gamma_kernel<<<gridx((int64_t)nw * n * n), 256, 0, s>>>(Wm, v, cw, n, nw, G64, G32);
@@ -488,7 +528,7 @@ cudaError_t run_gamma_mixed(const double2* L, const double2* chi, const double* 
         return e;
       ++nl;
     }
-    fwd_sub_diag_kernel<float><<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L32, Y, n, i0, b);
+    fwd_sub_diag_kernel<float><<<dim3((i0 + b + 63) / 64, nw), 64, 0, s>>>(L32, Y, n, i0, b);
     ++nl;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -521,7 +561,7 @@ cudaError_t run_gamma(const double2* L, const double* v, const double* cw, int n
         return e;
       ++nl;
     }
-    fwd_sub_diag_kernel<double><<<dim3((i0 + b + 255) / 256, nw), 256, 0, s>>>(L, Y, n, i0, b);
+    fwd_sub_diag_kernel<double><<<dim3((i0 + b + 63) / 64, nw), 64, 0, s>>>(L, Y, n, i0, b);
     ++nl;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -795,23 +835,29 @@ cudaError_t launch_paw_adjoint(const c2<T>* Nbar, const c2<T>* R, const c2<T>* P
 
 // ---------------------------------------------------------------- pair-density adjoint
 // Stage C^T: T2bar[pl][o1][o2][j3] = (1/N_r) sum_{G in column (o1,o2)} Nbar[p][G] exp(+2 pi i g3 j3 / N3).
-// Column lists: col_start[n1*n2+1], col_g[k] = sphere index, col_g3[k] = g3 of that point.
+// Column lists: col_start[n1*n2+1], col_g[k] = sphere index, col_g3[k] = g3 mod N3 of that point.
 // Chunk pl -> pair p = p0 + (pl / mc) nR + pl % mc: mc consecutive unoccupied
-// bands of np / mc consecutive occupied bands.
+// bands of np / mc consecutive occupied bands.  With tab the twiddles sit in
+// shared memory as a table over (g3 mod N3, j3), so no term takes a modulus.
 template <typename T>
 __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict__ Nbar, int NG, int64_t p0, int np,
                                                          int mc, int nR, int ncol, int N3,
                                                          const int* __restrict__ col_start,
                                                          const int* __restrict__ col_g, const int* __restrict__ col_g3,
-                                                         double inv_nr, c2<T>* __restrict__ T2) {
+                                                         double inv_nr, int tab, c2<T>* __restrict__ T2) {
   extern __shared__ unsigned char smem_raw[];
-  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
-  for (int t = threadIdx.x; t < N3; t += blockDim.x) {
-    double s, c;
-    sincospi(2.0 * (double)t / (double)N3, &s, &c);
-    tw[t] = mk<T>((T)c, (T)s);
+  c2<T>* tw1 = reinterpret_cast<c2<T>*>(smem_raw);  // exp(2 pi i t / N3), t < N3
+  c2<T>* tw = tab ? tw1 + N3 : tw1;                   // tab: [g3 mod N3][j3]
+  for (int e = threadIdx.x; e < N3; e += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)e / (double)N3, &sn, &cs);
+    tw1[e] = mk<T>((T)cs, (T)sn);
   }
   __syncthreads();
+  if (tab) {
+    for (int e = threadIdx.x; e < N3 * N3; e += blockDim.x) tw[e] = tw1[((e / N3) * (e % N3)) % N3];
+    __syncthreads();
+  }
   const int64_t total = (int64_t)np * ncol * N3;
   const T scale = (T)inv_nr;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
@@ -821,9 +867,11 @@ __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict
     const int pl = (int)(r / ncol);
     const c2<T>* nb = Nbar + (p0 + (int64_t)(pl / mc) * nR + pl % mc) * NG;
     c2<T> acc = mk<T>(0, 0);
-    for (int k = col_start[col]; k < col_start[col + 1]; ++k) {
-      const int t = pmod_a((int64_t)col_g3[k] * j3, N3);
-      cmac<T>(acc, nb[col_g[k]], tw[t]);
+    const int kb = col_start[col], ke = col_start[col + 1];
+    if (tab) {
+      for (int k = kb; k < ke; ++k) cmac<T>(acc, nb[col_g[k]], tw[col_g3[k] * N3 + j3]);
+    } else {
+      for (int k = kb; k < ke; ++k) cmac<T>(acc, nb[col_g[k]], tw[(col_g3[k] * j3) % N3]);
     }
     acc.x *= scale;
     acc.y *= scale;
@@ -838,8 +886,12 @@ cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int
   const int64_t total = (int64_t)np * ncol * N3;
   if (total == 0) return cudaSuccess;
   if (mc < 1 || np % mc) return cudaErrorInvalidValue;
-  adj_stageC_kernel<T><<<gridx(total), 256, N3 * sizeof(c2<T>), s>>>(Nbar, NG, p0, np, mc, nR, ncol, N3, col_start,
-                                                                     col_g, col_g3, inv_nr, T2);
+  const int tab = (int64_t)N3 * (N3 + 1) * sizeof(c2<T>) <= 48 * 1024 ? 1 : 0;
+  const size_t smem = (tab ? (size_t)N3 * (N3 + 1) : (size_t)N3) * sizeof(c2<T>);
+  // a grid of eight blocks per SM amortises the table over many outputs
+  const int grid = std::min(gridx(total), 152 * 8);
+  adj_stageC_kernel<T><<<grid, 256, smem, s>>>(Nbar, NG, p0, np, mc, nR, ncol, N3, col_start, col_g, col_g3, inv_nr,
+                                               tab, T2);
   return cudaGetLastError();
 }
 

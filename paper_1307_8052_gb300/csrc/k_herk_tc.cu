@@ -660,6 +660,265 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- two-SM rank-k update
+// The stored-operand two-term form on CTA pairs (cta_group::2).  A pair is the
+// row tiles 2r (even CTA) and 2r + 1 (odd CTA) of one column tile and
+// frequency; one thread of the even CTA issues M = 256, N = 256, K = 16
+// products whose A rows come from both CTAs (128 each) and whose B operand is
+// split the same way: the even CTA holds the X rows (Re), the odd CTA the Z
+// rows (Im).  Each SM therefore stages and feeds the tensor core with half of
+// B, which leaves room for three 64 KB stages.  Every CTA loads its own tiles
+// and completes their bytes on the even CTA's stage barrier; the product
+// commits arrive on the stage and accumulator barriers of both CTAs, and each
+// CTA drains its own 128 accumulator rows.  Products, folds and flushes per
+// element are those of herk_tc_kernel.
+namespace tc2 {
+constexpr int BK = 64, STAGES = 3, TERMS = 2;
+constexpr int TILE_BYTES = BM * BK * 2;
+constexpr int STAGE_BYTES = 2 * TERMS * TILE_BYTES;  // A hi, lo; B half hi, lo
+constexpr int RING_BYTES = STAGES * STAGE_BYTES;
+constexpr int SMEM_BYTES = RING_BYTES + 1024 + 256;
+}  // namespace tc2
+
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+// the tile lands in this CTA; its bytes complete on the barrier at cluster address bar
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar, int k, int row) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(k), "r"(row)
+      : "memory");
+}
+__device__ __forceinline__ void umma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma2_commit_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)0x3)
+      : "memory");
+}
+__device__ __forceinline__ void umma2_commit_local(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// pair tile pt -> row pair r and column tile tj (tj <= 2r + 1, tj < nt)
+__device__ __forceinline__ void pair_tile(int pt, int nt, int& r, int& tj) {
+  r = 0;
+  while (true) {
+    const int cnt = min(2 * r + 2, nt);
+    if (pt < cnt) break;
+    pt -= cnt;
+    ++r;
+  }
+  tj = pt;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    herk_tc2_kernel(const __grid_constant__ Maps maps, int NG, int NGpad, int nk, int fold, int flush,
+                    double2* __restrict__ chi, int* __restrict__ err, const Ctl ctl) {
+  using namespace tc2;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING_BYTES);  // even CTA: stage landed in both
+  uint64_t* empty = full + 4;                                      // stage consumed (both CTAs)
+  uint64_t* tfull = empty + 4;                                     // accumulator buffer ready (both CTAs)
+  uint64_t* tempty = tfull + 2;                                    // even CTA: buffer drained by both
+  uint64_t* mma_done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int w = blockIdx.y;
+  int rp, tj;
+  pair_tile(blockIdx.x >> 1, NGpad / BM, rp, tj);
+  const int ti = 2 * rp + (int)rank;
+  const int i0 = ti * BM, j0 = tj * BN;
+  const int nfold = (nk + fold - 1) / fold;
+  const uint64_t wait_ns = ctl.wait_ns;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 2 * EPI_WARPS);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    // one warp of each CTA of the pair allocates the same columns in both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer (both CTAs)
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        if (kb == ctl.stall_stage) break;
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, abort_flag, wait_ns)) {
+          *abort_flag = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        if (rank == 0) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
+        const uint32_t fb = peer_addr(&full[s], 0);
+        unsigned char* st = smem + s * STAGE_BYTES;
+        const int k = kb * BK;
+#pragma unroll
+        for (int t = 0; t < TERMS; ++t) {
+          tma_load_2d_pair(st + t * TILE_BYTES, &maps.a[t], fb, k, w * NGpad + i0);
+          tma_load_2d_pair(st + (TERMS + t) * TILE_BYTES, rank ? &maps.z[t] : &maps.x[t], fb, k, j0);
+        }
+        issued = kb + 1;
+      }
+      // the even CTA's loads and products must land before it may exit; both
+      // wait until the pair's products released the last issued slots
+      if (rank == 0)
+        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+          if (!mbar_wait_timer(&full[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 7);
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        if (!mbar_wait_timer(&empty[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 7);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer (even CTA)
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = idesc_bf16(2 * BM, 2 * BN);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&full[s], (kb / STAGES) & 1, abort_flag, wait_ns)) {
+          *abort_flag = 1;
+          atomicExch(err, 2);
+          break;
+        }
+        const int f = kb / fold;
+        const int b = f & 1;
+        const bool first = (kb % fold) == 0;
+        if (first && f >= 2 && !mbar_wait(&tempty[b], ((f >> 1) - 1) & 1, abort_flag, wait_ns)) {
+          *abort_flag = 1;
+          atomicExch(err, 3);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t d = tmem + b * 256;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t koff = kk * 32;
+          const uint64_t a0 = kmajor_desc<BK>(st + koff), a1 = kmajor_desc<BK>(st + TILE_BYTES + koff);
+          const uint64_t b0 = kmajor_desc<BK>(st + 2 * TILE_BYTES + koff);
+          const uint64_t b1 = kmajor_desc<BK>(st + 3 * TILE_BYTES + koff);
+          const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+          umma2(d, a0, b0, idesc, acc);  // hi*hi
+          umma2(d, a0, b1, idesc, 1u);   // hi*lo
+          umma2(d, a1, b0, idesc, 1u);   // lo*hi
+        }
+        umma2_commit_both(&empty[s]);
+        if ((kb % fold) == fold - 1 || kb == nk - 1) umma2_commit_both(&tfull[b]);
+      }
+      umma2_commit_local(mma_done);
+      if (!mbar_wait_timer(mma_done, 0)) atomicExch(err, 5);
+    }
+  } else if (warp >= EPI_WARP0) {
+    // ------------------------------------------------------------ epilogue (both CTAs, own rows)
+    const int q = warp & 3;
+    const int cs = (warp - EPI_WARP0) >> 2;
+    const int row = q * 32 + lane;
+    const int gi = i0 + row;
+    const int cbase = cs * 32;
+    const int rlo = i0 + q * 32;
+    const bool active = rlo < NG && j0 + cbase < NG && j0 + cbase <= rlo + 31;
+    double2* crow = chi + ((int64_t)w * NG + gi) * NG + j0 + cbase;
+    const int ncol = (gi < NG) ? max(0, min(32, min(NG, gi + 1) - (j0 + cbase))) : 0;
+    float sre[32], sim[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) sre[c] = sim[c] = 0.f;
+#define RPA_TC2_FLUSH()                                     \
+  do {                                                      \
+    _Pragma("unroll") for (int c = 0; c < 32; ++c) {        \
+      if (c < ncol) {                                       \
+        double2 v = crow[c];                                \
+        v.x += (double)sre[c];                              \
+        v.y += (double)sim[c];                              \
+        crow[c] = v;                                        \
+      }                                                     \
+      sre[c] = 0.f;                                         \
+      sim[c] = 0.f;                                         \
+    }                                                       \
+  } while (0)
+    for (int f = 0; f < nfold; ++f) {
+      const int b = f & 1;
+      if (!warp_wait(&tfull[b], (f >> 1) & 1, abort_flag, wait_ns)) {
+        *abort_flag = 1;
+        atomicExch(err, 4);
+        break;
+      }
+      // one arrival per warp on the even CTA's barrier, after every lane's loads
+      if (!active) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(peer_addr(&tempty[b], 0));
+        continue;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + cbase;
+      float v[16];
+      tmem_ld16(base, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sre[c] = fmaf(1.f, v[c], sre[c]);
+      tmem_ld16(base + 16, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sre[16 + c] = fmaf(1.f, v[c], sre[16 + c]);
+      tmem_ld16(base + 128, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sim[c] = fmaf(1.f, v[c], sim[c]);
+      tmem_ld16(base + 144, v);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(peer_addr(&tempty[b], 0));
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sim[16 + c] = fmaf(1.f, v[c], sim[16 + c]);
+      if ((f + 1) % flush == 0) RPA_TC2_FLUSH();
+    }
+    if (active) RPA_TC2_FLUSH();
+#undef RPA_TC2_FLUSH
+  }
+  tc_fence_before();
+  __syncthreads();
+  // neither CTA exits (or frees its tensor memory) while the other may still address it
+  cluster_sync_all();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- persistent batched launch
 // Many rank-k blocks (k-blocks of several q-points and instances, each with
 // its own operands and K) in one persistent launch of two-term tiles.  A
@@ -1431,6 +1690,32 @@ cudaError_t herk_tc_prepare(const float2* N, int64_t P, int NG, const float* wgt
   return cudaGetLastError();
 }
 
+// The two-SM form: clusters of two CTAs over row-tile pairs.
+static cudaError_t launch_tc2(const tc::Maps& maps, int NG, int NGpad, int nw, int64_t Kpad, int fold, int flush,
+                              double2* chi, int* err, const tc::Ctl& ctl, cudaStream_t s) {
+  using namespace tc;
+  const int nt = NGpad / BM;
+  int npair = 0;
+  for (int r = 0; 2 * r < nt; ++r) npair += std::min(2 * r + 2, nt);
+  cudaError_t e = cudaFuncSetAttribute(herk_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc2::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(2 * npair, nw);
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = tc2::SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int nk = (int)(Kpad / tc2::BK);
+  return cudaLaunchKernelEx(&cfg, herk_tc2_kernel, maps, NG, NGpad, nk, fold, flush, chi, err, ctl);
+}
+
 cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fused, int fold_stages, int flush_folds, int pipe,
                         int pair, int64_t wait_us, int stall_stage, double2* chi, void* scratch, size_t scratch_bytes,
                         int* err, cudaStream_t s) {
@@ -1471,8 +1756,9 @@ cudaError_t herk_tc_run(int64_t P, int NG, int nw, int terms, int fused, int fol
     return launch_gemm<2, 32, 4, false>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s);
   if (fused)
     return launch_gemm<2, 64, 2, true>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s);
+  if (pair == 2) return launch_tc2(maps, NG, g.NGpad, nw, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s);
   return launch_gemm<2, 64, 2, false>(maps, grid, NG, g.NGpad, g.Kpad, fold_stages, flush_folds, chi, err, ctl, s,
-                                      pair && nw % 2 == 0);
+                                      pair == 1 && nw % 2 == 0);
 }
 
 // Controls of the batched-product launches: the default wait limit, no stall.

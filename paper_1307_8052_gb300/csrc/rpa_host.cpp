@@ -997,7 +997,7 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
     for (int i = 0; i < NG; ++i) {
       const int col = (B.gfft[3 * i] - B.glo[0]) * n2 + (B.gfft[3 * i + 1] - B.glo[1]);
       cg[fill[col]] = i;
-      cg3[fill[col]++] = B.gfft[3 * i + 2];
+      cg3[fill[col]++] = ((B.gfft[3 * i + 2] % N3) + N3) % N3;  // g3 mod N3
     }
   }
   const size_t cbytes = sizeof(int) * (cstart.size() + 2 * (size_t)NG);
@@ -2406,7 +2406,7 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "gradient precision choice must be 0, 1 or 2");
       break;
     case RPA_TUNE_TC_PAIR:
-      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "paired rank-k launch must be 0 or 1");
+      if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "paired rank-k launch must be 0, 1 or 2");
       break;
     case RPA_TUNE_BATCH_MB:
       if (value < 1 || value > (1 << 22)) return fail(c, RPA_ERR_ARG, "batch group budget %lld MiB out of range", (long long)value);

@@ -5,7 +5,7 @@ Gamma -> (0, 1/2, 1/2) (no umklapp) and (0, 1/2, 1/2) -> Gamma (umklapp (0, 1, 1
 16 occupied + 1200 empty bands per set, 3 x 13 PAW projectors, 16 frequencies:
 each launch of the rank-k kernel is exactly one launch of the bench's workload.
 
-Usage: python -m paper_1307_8052_gb300.profile_case [fold] [reps] [chi|energy] [precision] [fuse] [pair]
+Usage: python -m paper_1307_8052_gb300.profile_case [fold] [reps] [chi|energy] [precision] [fuse] [pair] [pipe]
 """
 from __future__ import annotations
 
@@ -24,6 +24,7 @@ def main(argv):
     precision = argv[4] if len(argv) > 4 else "bf16x2"
     fuse = int(argv[5]) if len(argv) > 5 else 1
     pair = int(argv[6]) if len(argv) > 6 else 0
+    pipe = int(argv[7]) if len(argv) > 7 else 0
     b.load()
     cell = np.eye(3) * 9.0
     ks = {0: np.zeros(3), 3: np.array([0.0, 0.5, 0.5])}
@@ -39,6 +40,7 @@ def main(argv):
     b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FOLD, fold)
     b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_FUSE, fuse)
     b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, pair)
+    b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PIPE, pipe)
     om, W = b.rpa_gauss_legendre(16)
     b.rpa_set_profiling(ctx, True)
     for _ in range(reps):
@@ -47,7 +49,7 @@ def main(argv):
         else:
             b.rpa_chi0(ctx, 0, om)
         ms, _ = b.rpa_get_profile(ctx)
-        print(f"{precision} fold {fold} fuse {fuse} pair {pair} stage ms {np.round(ms, 2).tolist()}", flush=True)
+        print(f"{precision} fold {fold} fuse {fuse} pair {pair} pipe {pipe} stage ms {np.round(ms, 2).tolist()}", flush=True)
     b.rpa_destroy(ctx)
 
 

@@ -83,9 +83,12 @@ def test_fused_weighting_bit_identical(case):
         assert _rel(fused, o.chi0(p, iq, om, Q)) < 2e-5
 
 
+@pytest.mark.parametrize("pair", [1, 2])
 @pytest.mark.parametrize("case", ["config0", "mesh_umklapp_paw", "bulk_subset"])
-def test_paired_launch_bit_identical(case):
-    # 8 and 16 frequencies run paired; 5 (odd) falls back to the unpaired launch
+def test_paired_launch_bit_identical(case, pair):
+    # pair 1: 8 and 16 frequencies run paired, 5 (odd) falls back to the
+    # unpaired launch; pair 2: two-SM products over row-tile pairs (config 0:
+    # one pair; the bulk subset: ten row tiles, five pairs)
     p, iq, nw = _case(case)
     om, W = o.frequency_grid(nw)
     ctx = _ctx(p, "bf16x2")
@@ -94,11 +97,11 @@ def test_paired_launch_bit_identical(case):
         b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 0)
         single = b.rpa_chi0(ctx, iq, om)
         Es, ts = b.rpa_energy(ctx, [iq], [1.0], om, W)
-        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 1)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, pair)
         paired = b.rpa_chi0(ctx, iq, om)
         Ep, tp = b.rpa_energy(ctx, [iq], [1.0], om, W)
         with pytest.raises(b.RpaError) as e:
-            b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 2)
+            b.rpa_set_tuning(ctx, b.RPA_TUNE_TC_PAIR, 3)
         assert e.value.status == b.RPA_ERR_ARG
     finally:
         b.rpa_destroy(ctx)
@@ -107,7 +110,7 @@ def test_paired_launch_bit_identical(case):
 
 
 @pytest.mark.parametrize("precision,fuse,pair", [("bf16x2", 1, 0), ("bf16x2", 0, 0), ("bf16x2", 0, 1),
-                                                ("bf16x3", 0, 0)])
+                                                ("bf16x2", 0, 2), ("bf16x3", 0, 0)])
 def test_bounded_wait_timeout_leaves_context_usable(precision, fuse, pair):
     p = syn.config0()
     om, W = o.frequency_grid(p.nw)
