@@ -556,7 +556,8 @@ def run_batched(args):
     build()
     b.load()
     t0 = time.perf_counter()
-    probs = [syn.config3_instance(i) for i in range(args.instances)]
+    rng_kw = {"ng_range": (400, 900), "nocc_range": (8, 32)} if args.small else {}
+    probs = [syn.config3_instance(i, **rng_kw) for i in range(args.instances)]
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     om, W = b.rpa_gauss_legendre(16, 1.0)
@@ -629,8 +630,9 @@ def run_batched(args):
     line = {"metric": METRIC + " (batched instances)", "value": total / t_best / 1e12, "unit": "TFLOP/s",
             "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": t_best * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"{len(ctxs)} (q, cell) instances, NG 400-3000, n_occ 8-120, n_unocc ~ NG, "
-                                   "16 iw, 3x13 PAW, one CUDA graph", "NG": ngs, "pairs": pairs,
+            "config": {"workload": f"{len(ctxs)} (q, cell) instances, "
+                                   + ("NG 400-900, n_occ 8-32" if args.small else "NG 400-3000, n_occ 8-120")
+                                   + ", n_unocc ~ NG, 16 iw, 3x13 PAW, one CUDA graph", "NG": ngs, "pairs": pairs,
                        "generation_s": gen_s, "flops": total, "device_free_gb_at_end": free_gb},
             "sequential": {"value": total / t_seq / 1e12, "ms_per_step": t_seq * 1e3},
             "graph_per_instance": {"value": total / t_graph / 1e12, "ms_per_step": t_graph * 1e3},
@@ -663,10 +665,12 @@ def main():
     ap.add_argument("--slab-q", type=int, default=1, help="q-points per step of the slab workload")
     ap.add_argument("--paw-tc", action="store_true",
                     help="PAW product on the tensor cores (split modes; faster for many projectors, larger E_c error)")
-    ap.add_argument("--tc-pair", type=int, choices=[0, 1], default=None,
+    ap.add_argument("--tc-pair", type=int, choices=[0, 1, 2], default=None,
                     help="rank-k launch paired over frequencies (TMA multicast of the shared operand); "
                          "default: the library's")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--small", action="store_true",
+                    help="--config batched: small instances only (NG 400-900, n_occ 8-32)")
     ap.add_argument("--gamma", type=int, choices=[0, 1, 2], default=2,
                     help="--config backward: dE/dchi0 in FP64 (0), FP32 product form (1) or float-float (2)")
     args = ap.parse_args()

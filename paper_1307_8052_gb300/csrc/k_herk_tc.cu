@@ -710,8 +710,11 @@ __device__ __forceinline__ void umma2_commit_local(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
+// arrive on a barrier of this CTA or its peer (cluster address); the ordering
+// the accumulator hand-back needs is the completed tensor-memory loads
+// (tcgen05.wait::ld and the fence before it), so CTA-scope release suffices
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // pair tile pt -> row pair r and column tile tj (tj <= 2r + 1, tj < nt)

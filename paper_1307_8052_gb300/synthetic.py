@@ -278,22 +278,23 @@ def spin_metal_problem(config_tag: int = 80, a: float = 6.0, grid=(12, 12, 12), 
                    len(kmesh), sets, qps, nw, paw)
 
 
-def config3_instance(i: int, nw: int = 16) -> Problem:
+def config3_instance(i: int, nw: int = 16, ng_range=(400, 3000), nocc_range=(8, 120)) -> Problem:
     """One (q, cell) instance of the batched workload: the bulk box of config 1
     (9 bohr, 40^3 grid, 20 Ha orbitals), Gamma k-point, q drawn from the
     {0, 1/2}^3 mesh without 0, response basis size NG ~ U[400, 3000] (the
     cutoff is set from the target count), n_occ ~ U[8, 120], n_unocc ~ NG,
-    3 PAW atoms x 13 projectors; seeds depend on the instance index."""
+    3 PAW atoms x 13 projectors; seeds depend on the instance index.  The
+    ranges of NG and n_occ are parameters (inclusive)."""
     tag = 300 + i
     rng = np.random.default_rng(seed_of(tag, 0, 9))
     a = 9.0
     cell = np.eye(3) * a
     mesh = [np.array(x, dtype=np.float64) * 0.5 for x in np.ndindex(2, 2, 2)][1:]
     q = mesh[int(rng.integers(len(mesh)))]
-    ng_target = int(rng.integers(400, 3001))
+    ng_target = int(rng.integers(ng_range[0], ng_range[1] + 1))
     vol = a ** 3
     ecut_chi = 0.5 * (6.0 * np.pi ** 2 * ng_target / vol) ** (2.0 / 3.0)
-    nocc = int(rng.integers(8, 121))
+    nocc = int(rng.integers(nocc_range[0], nocc_range[1] + 1))
     npw_min = min(len(wf_sphere(cell, [0, 0, 0], 20.0)), len(wf_sphere(cell, q, 20.0)))
     nunocc = int(min(ng_target, npw_min - nocc))
     sets = [make_orbitals(tag, 0, cell, [0.0, 0.0, 0.0], 20.0, nocc, nunocc),
