@@ -383,6 +383,12 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      cta_group::2, M = 256) over pairs of row tiles, each
  *                      SM staging half of the unweighted operand.  All three
  *                      give the same chi0 bit for bit.
+ * RPA_TUNE_PD_FACT    1 (default): the slowest and middle axes of the pair
+ *                      densities (Eq. 10) as two-level pruned DFTs, the axis
+ *                      N = (N / L) L with L in {3, 4, 5, 6, 8} (fewer complex
+ *                      multiply-adds per line where that saves a fifth or
+ *                      more, at most 16 outputs a line); 0: direct sums.
+ *                      The two agree to FP32 rounding.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -401,7 +407,8 @@ typedef enum {
   RPA_TUNE_BATCH_MB = 13,
   RPA_TUNE_GAMMA = 14,
   RPA_TUNE_TC_PAIR = 15,
-  RPA_TUNE_COUNT = 16
+  RPA_TUNE_PD_FACT = 16,
+  RPA_TUNE_COUNT = 17
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

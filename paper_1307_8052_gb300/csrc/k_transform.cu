@@ -438,6 +438,299 @@ cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2,
   }
 }
 
+// ---------------------------------------------------------------- factorised pruned DFT (stages A and B)
+// With N = r L, j = r m + j' (m < L, j' < r) and outputs g = lo + t (t < n):
+//   y_g = sum_j' w_N^(g j') sum_m x_(r m + j') w_L^(g m),   w_N = exp(-2 pi i / N),
+// and w_L^(g m) depends on g only through g mod L.  Per residue j' a thread
+// forms S_k' = sum_m x_(r m + j') w_L^((b + k') m) for the L classes
+// k' = 0..L-1 (b = lo mod L, so output t uses class t mod L, a compile-time
+// index), then adds w_N^(g j') S_(t mod L) into output t: N L + r n complex
+// multiply-adds per line instead of N n.  Table layout (FP64-accurate,
+// stored in T): [m][k'] = w_L^((b + k') m) for m, k' < L, then
+// [j'][t] = w_N^((lo + t) j') with a row stride of TS.
+template <typename T>
+__global__ void twiddle_factored_kernel(c2<T>* __restrict__ tw, int N, int L, int lo, int n) {
+  const int r = N / L;
+  const int b = pmod(lo, L);
+  const int total = L * L + r * TS;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int t;
+    bool on = true;
+    if (e < L * L) {
+      const int m = e / L, k = e % L;
+      t = pmod(-(int64_t)(b + k) * m, L) * r;  // w_L^x = w_N^(x r)
+    } else {
+      const int jr = (e - L * L) / TS, o = (e - L * L) % TS;
+      on = o < n;
+      t = pmod(-(int64_t)(lo + o) * jr, N);
+    }
+    double sn = 0.0, cs = 0.0;
+    if (on) sincospi(2.0 * (double)t / (double)N, &sn, &cs);
+    tw[e] = mk<T>((T)cs, (T)sn);
+  }
+}
+
+// The divisor L of N (3, 4, 5, 6 or 8) that minimises N L + (N / L) n, or 0 when the
+// factorised form saves less than a fifth of the direct N n.
+int factored_radix(int N, int n) {
+  int best = 0;
+  int64_t cost = (int64_t)N * n * 4 / 5;
+  for (int L : {3, 4, 5, 6, 8}) {
+    if (N % L || L > n) continue;
+    const int64_t c = (int64_t)N * L + (int64_t)(N / L) * n;
+    if (c < cost) {
+      cost = c;
+      best = L;
+    }
+  }
+  return best;
+}
+
+template <typename T>
+cudaError_t launch_twiddle_factored(c2<T>* tw, int N, int L, int lo, int n, cudaStream_t s) {
+  if (L < 2 || N % L || n > TS) return cudaErrorInvalidValue;
+  const int total = L * L + (N / L) * TS;
+  twiddle_factored_kernel<T><<<(total + 255) / 256, 256, 0, s>>>(tw, N, L, lo, n);
+  return cudaGetLastError();
+}
+template <typename T>
+__host__ __device__ constexpr int factored_table(int N, int L) {
+  return L * L + (N / L) * TS;
+}
+
+// Stage A in the factorised form: as pd_stageA_kernel (PP pairs per thread,
+// per-thread cp.async ring of PF slices), with the slices of a line streamed
+// residue by residue (slice s is j1 = r (s mod L) + s / L).
+template <typename T, int NO, int PP, int L>
+__global__ void __launch_bounds__(256) pd_stageA_fact_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
+                                                             int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
+                                                             const int* __restrict__ Ridx, int nR, int64_t p0, int np,
+                                                             const c2<T>* __restrict__ twg, int n1,
+                                                             c2<T>* __restrict__ T1) {
+  constexpr int PF = RING_PF;
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  const int r = N1 / L;
+  load_twiddle_matrix<T>(tw, twg, factored_table<T>(N1, L));
+  const c2<T>* wl = tw;           // [m][k']
+  const c2<T>* wr = tw + L * L;   // [j'][t], stride TS
+  const int ngrp = (np + PP - 1) / PP;
+  const int64_t total = (int64_t)ngrp * N23;
+  c2<T>* my = reinterpret_cast<c2<T>*>(smem_raw + ring_offset<T>((factored_table<T>(N1, L) + TS - 1) / TS)) +
+              threadIdx.x;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int j23 = (int)(id % N23);
+    const int grp = (int)(id / N23);
+    const c2<T>* un[PP];
+    const c2<T>* um[PP];
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+      const int pl = min(grp * PP + q, np - 1);
+      const int64_t p = p0 + pl;
+      un[q] = Uk + (int64_t)Lidx[p / nR] * Nr + j23;
+      um[q] = Ukp + (int64_t)Ridx[p % nR] * Nr + j23;
+    }
+    c2<T> acc[PP][NO], sk[PP][L];
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+#pragma unroll
+      for (int t = 0; t < NO; ++t) acc[q][t] = mk<T>(0, 0);
+#pragma unroll
+      for (int k = 0; k < L; ++k) sk[q][k] = mk<T>(0, 0);
+    }
+    auto issue = [&](int sl) {
+      const int st = sl % PF;
+      const int64_t j = (int64_t)((sl % L) * r + sl / L) * N23;
+#pragma unroll
+      for (int q = 0; q < PP; ++q) {
+        cp_async_elem<T>(my + (st * 2 * PP + 2 * q) * RING_THREADS, un[q] + j);
+        cp_async_elem<T>(my + (st * 2 * PP + 2 * q + 1) * RING_THREADS, um[q] + j);
+      }
+    };
+#pragma unroll
+    for (int sl = 0; sl < PF - 1; ++sl) {
+      if (sl < N1) issue(sl);
+      cp_async_commit();
+    }
+    for (int jr = 0; jr < r; ++jr) {
+#pragma unroll
+      for (int m = 0; m < L; ++m) {
+        const int sl = jr * L + m;
+        if (sl + PF - 1 < N1) issue(sl + PF - 1);
+        cp_async_commit();
+        cp_async_wait<PF - 1>();  // the group of slice sl has landed
+        const int st = sl % PF;
+#pragma unroll
+        for (int q = 0; q < PP; ++q) {
+          const c2<T> x =
+              cj_mul<T>(my[(st * 2 * PP + 2 * q) * RING_THREADS], my[(st * 2 * PP + 2 * q + 1) * RING_THREADS]);
+#pragma unroll
+          for (int k = 0; k < L; ++k) cmac<T>(sk[q][k], x, wl[m * L + k]);
+        }
+      }
+      const c2<T>* wj = wr + jr * TS;
+#pragma unroll
+      for (int t = 0; t < NO; ++t) {
+        const c2<T> f = wj[t];
+#pragma unroll
+        for (int q = 0; q < PP; ++q) cmac<T>(acc[q][t], sk[q][t % L], f);
+      }
+#pragma unroll
+      for (int q = 0; q < PP; ++q)
+#pragma unroll
+        for (int k = 0; k < L; ++k) sk[q][k] = mk<T>(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+      const int pl = grp * PP + q;
+      if (pl < np) {
+        c2<T>* dst = T1 + (int64_t)pl * n1 * N23 + j23;
+#pragma unroll
+        for (int t = 0; t < NO; ++t)
+          if (t < n1) dst[(int64_t)t * N23] = acc[q][t];
+      }
+    }
+  }
+}
+
+// Stage B in the factorised form (one row (pl, o1) and j3 per thread).
+template <typename T, int NO, int L>
+__global__ void __launch_bounds__(256) pd_stageB_fact_kernel(const c2<T>* __restrict__ T1, c2<T>* __restrict__ T2,
+                                                             int64_t rows, int N2, int N3,
+                                                             const c2<T>* __restrict__ twg, int n2) {
+  constexpr int PF = RING_PF;
+  extern __shared__ unsigned char smem_raw[];
+  c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+  const int r = N2 / L;
+  load_twiddle_matrix<T>(tw, twg, factored_table<T>(N2, L));
+  const c2<T>* wl = tw;
+  const c2<T>* wr = tw + L * L;
+  c2<T>* my = reinterpret_cast<c2<T>*>(smem_raw + ring_offset<T>((factored_table<T>(N2, L) + TS - 1) / TS)) +
+              threadIdx.x;
+  const int64_t total = rows * N3;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int j3 = (int)(id % N3);
+    const int64_t row = id / N3;  // (pl, o1)
+    const c2<T>* src = T1 + row * (int64_t)N2 * N3 + j3;
+    c2<T> acc[NO], sk[L];
+#pragma unroll
+    for (int t = 0; t < NO; ++t) acc[t] = mk<T>(0, 0);
+#pragma unroll
+    for (int k = 0; k < L; ++k) sk[k] = mk<T>(0, 0);
+#pragma unroll
+    for (int sl = 0; sl < PF - 1; ++sl) {
+      if (sl < N2) cp_async_elem<T>(my + sl * RING_THREADS, src + (int64_t)((sl % L) * r + sl / L) * N3);
+      cp_async_commit();
+    }
+    for (int jr = 0; jr < r; ++jr) {
+#pragma unroll
+      for (int m = 0; m < L; ++m) {
+        const int sl = jr * L + m;
+        const int sn = sl + PF - 1;
+        if (sn < N2) cp_async_elem<T>(my + (sn % PF) * RING_THREADS, src + (int64_t)((sn % L) * r + sn / L) * N3);
+        cp_async_commit();
+        cp_async_wait<PF - 1>();
+        const c2<T> x = my[(sl % PF) * RING_THREADS];
+#pragma unroll
+        for (int k = 0; k < L; ++k) cmac<T>(sk[k], x, wl[m * L + k]);
+      }
+      const c2<T>* wj = wr + jr * TS;
+#pragma unroll
+      for (int t = 0; t < NO; ++t) cmac<T>(acc[t], sk[t % L], wj[t]);
+#pragma unroll
+      for (int k = 0; k < L; ++k) sk[k] = mk<T>(0, 0);
+    }
+    c2<T>* dst = T2 + (row * n2) * N3 + j3;
+#pragma unroll
+    for (int t = 0; t < NO; ++t)
+      if (t < n2) dst[(int64_t)t * N3] = acc[t];
+  }
+}
+
+template <typename T, int NO, int L>
+static cudaError_t launch_stageA_fact_l(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
+                                        const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
+                                        const c2<T>* twf, int n1, c2<T>* T1, cudaStream_t s) {
+  constexpr int PP = sizeof(T) == 4 ? 2 : 1;
+  const int64_t total = (int64_t)((np + PP - 1) / PP) * N23;
+  if (total == 0) return cudaSuccess;
+  const int smem = ring_offset<T>((factored_table<T>(N1, L) + TS - 1) / TS) +
+                   RING_PF * 2 * PP * RING_THREADS * (int)sizeof(c2<T>);
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(pd_stageA_fact_kernel<T, NO, PP, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  pd_stageA_fact_kernel<T, NO, PP, L><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR,
+                                                                             p0, np, twf, n1, T1);
+  return cudaGetLastError();
+}
+
+template <typename T, int NO>
+static cudaError_t launch_stageA_fact_no(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
+                                         const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
+                                         const c2<T>* twf, int L, int n1, c2<T>* T1, cudaStream_t s) {
+  switch (L) {
+    case 3: return launch_stageA_fact_l<T, NO, 3>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
+    case 4: return launch_stageA_fact_l<T, NO, 4>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
+    case 5: return launch_stageA_fact_l<T, NO, 5>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
+    case 6: return launch_stageA_fact_l<T, NO, 6>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
+    case 8: return launch_stageA_fact_l<T, NO, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_pd_stageA_fact(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+                                  const int* Ridx, int nR, int64_t p0, int np, const c2<T>* twf, int L, int n1,
+                                  c2<T>* T1, cudaStream_t s) {
+  if (n1 > TS || L < 2 || N1 % L) return cudaErrorInvalidValue;
+  switch (width_for(n1)) {
+    case 8: return launch_stageA_fact_no<T, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
+    case 12: return launch_stageA_fact_no<T, 12>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
+    case 14: return launch_stageA_fact_no<T, 14>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
+    default: return launch_stageA_fact_no<T, 16>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
+  }
+}
+
+template <typename T, int NO, int L>
+static cudaError_t launch_stageB_fact_l(const c2<T>* T1, c2<T>* T2, int64_t rows, int N2, int N3, const c2<T>* twf,
+                                        int n2, cudaStream_t s) {
+  const int smem =
+      ring_offset<T>((factored_table<T>(N2, L) + TS - 1) / TS) + RING_PF * RING_THREADS * (int)sizeof(c2<T>);
+  pd_stageB_fact_kernel<T, NO, L><<<grid_for(rows * N3, 256), 256, smem, s>>>(T1, T2, rows, N2, N3, twf, n2);
+  return cudaGetLastError();
+}
+
+template <typename T, int NO>
+static cudaError_t launch_stageB_fact_no(const c2<T>* T1, c2<T>* T2, int64_t rows, int N2, int N3, const c2<T>* twf,
+                                         int L, int n2, cudaStream_t s) {
+  switch (L) {
+    case 3: return launch_stageB_fact_l<T, NO, 3>(T1, T2, rows, N2, N3, twf, n2, s);
+    case 4: return launch_stageB_fact_l<T, NO, 4>(T1, T2, rows, N2, N3, twf, n2, s);
+    case 5: return launch_stageB_fact_l<T, NO, 5>(T1, T2, rows, N2, N3, twf, n2, s);
+    case 6: return launch_stageB_fact_l<T, NO, 6>(T1, T2, rows, N2, N3, twf, n2, s);
+    case 8: return launch_stageB_fact_l<T, NO, 8>(T1, T2, rows, N2, N3, twf, n2, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_pd_stageB_fact(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* twf, int L,
+                                  int n2, cudaStream_t s) {
+  const int64_t rows = (int64_t)np * n1;
+  if (rows == 0) return cudaSuccess;
+  if (n2 > TS || L < 2 || N2 % L) return cudaErrorInvalidValue;
+  switch (width_for(n2)) {
+    case 8: return launch_stageB_fact_no<T, 8>(T1, T2, rows, N2, N3, twf, L, n2, s);
+    case 12: return launch_stageB_fact_no<T, 12>(T1, T2, rows, N2, N3, twf, L, n2, s);
+    case 14: return launch_stageB_fact_no<T, 14>(T1, T2, rows, N2, N3, twf, L, n2, s);
+    default: return launch_stageB_fact_no<T, 16>(T1, T2, rows, N2, N3, twf, L, n2, s);
+  }
+}
+
 // ---------------------------------------------------------------- pair density stage C
 template <typename T>
 __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict__ T2, int np, int n1, int n2, int N3,
@@ -814,6 +1107,12 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
   template cudaError_t launch_pd_stageB<T>(const c2<T>*, c2<T>*, int, int, int, int, const c2<T>*, int,          \
                                            cudaStream_t);                                                        \
   template cudaError_t launch_twiddle_matrix<T>(c2<T>*, int, int, int, cudaStream_t);                             \
+  template cudaError_t launch_twiddle_factored<T>(c2<T>*, int, int, int, int, cudaStream_t);                    \
+  template cudaError_t launch_pd_stageA_fact<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*,        \
+                                                const int*, int, int64_t, int, const c2<T>*, int, int, c2<T>*,    \
+                                                cudaStream_t);                                                    \
+  template cudaError_t launch_pd_stageB_fact<T>(const c2<T>*, c2<T>*, int, int, int, int, const c2<T>*, int, int,  \
+                                                cudaStream_t);                                                    \
   template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
                                            int, int64_t, int, const c2<T>*, int, c2<T>*, cudaStream_t);          \
   template cudaError_t launch_pd_stageBC<T>(const c2<T>*, int, int, int, int, const c2<T>*, int, const int*,     \

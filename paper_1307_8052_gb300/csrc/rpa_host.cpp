@@ -170,7 +170,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 2, 0};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 2, 0, 1};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -610,6 +610,18 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
     int OB = c->tune[RPA_TUNE_PD_FUSE] == 1 ? pd_stageBC_slab<T>(n1, n2, N2, N3) : 0;
     for (int i = 1; OB > 0 && i < NG; ++i)
       if (gfft[3 * i] < gfft[3 * (i - 1)]) OB = 0;
+    // the slowest and middle axes as two-level pruned DFTs where that saves work
+    const int LA = c->tune[RPA_TUNE_PD_FACT] == 1 && n1 <= 16 ? factored_radix(N1, n1) : 0;
+    const int LB = c->tune[RPA_TUNE_PD_FACT] == 1 && OB == 0 && n2 <= 16 ? factored_radix(N2, n2) : 0;
+    void *p_tfA = nullptr, *p_tfB = nullptr;
+    if (LA) {
+      if ((st = workspace(c, "twfA", sizeof(c2<T>) * (size_t)(LA * LA + (N1 / LA) * 16), &p_tfA)) != RPA_OK) return st;
+      CUDA_OK(c, launch_twiddle_factored<T>((c2<T>*)p_tfA, N1, LA, glo[0], n1, c->stream));
+    }
+    if (LB) {
+      if ((st = workspace(c, "twfB", sizeof(c2<T>) * (size_t)(LB * LB + (N2 / LB) * 16), &p_tfB)) != RPA_OK) return st;
+      CUDA_OK(c, launch_twiddle_factored<T>((c2<T>*)p_tfB, N2, LB, glo[1], n2, c->stream));
+    }
     void* p_g1s = nullptr;
     if (OB > 0) {
       if ((st = workspace(c, "pd_g1start", sizeof(int) * (size_t)(n1 + 1), &p_g1s)) != RPA_OK) return st;
@@ -617,8 +629,12 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
     }
     for (int64_t p0 = 0; p0 < P; p0 += PC) {
       const int np = (int)std::min<int64_t>(PC, P - p0);
-      CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d, nR,
-                                     p0, np, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
+      if (LA)
+        CUDA_OK(c, launch_pd_stageA_fact<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d,
+                                            nR, p0, np, (const c2<T>*)p_tfA, LA, n1, (c2<T>*)p_T1, c->stream));
+      else
+        CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d, nR,
+                                       p0, np, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
       if (OB > 0) {
         CUDA_OK(c, launch_pd_stageBC<T>((const c2<T>*)p_T1, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                         (const int*)p_gfft, (const int*)p_g1s, OB, NG, glo[0], glo[1],
@@ -626,8 +642,12 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
         tm.add_launches(2);
         continue;
       }
-      CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
-                                     c->stream));
+      if (LB)
+        CUDA_OK(c, launch_pd_stageB_fact<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_tfB, LB,
+                                            n2, c->stream));
+      else
+        CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
+                                       c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
                                      1.0 / (double)Nr, p0, (c2<T>*)p_N, c->stream));
       tm.add_launches(3);
@@ -2407,6 +2427,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_TC_PAIR:
       if (value < 0 || value > 2) return fail(c, RPA_ERR_ARG, "paired rank-k launch must be 0, 1 or 2");
+      break;
+    case RPA_TUNE_PD_FACT:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "factorised pair-density axes must be 0 or 1");
       break;
     case RPA_TUNE_BATCH_MB:
       if (value < 1 || value > (1 << 22)) return fail(c, RPA_ERR_ARG, "batch group budget %lld MiB out of range", (long long)value);

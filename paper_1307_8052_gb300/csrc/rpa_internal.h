@@ -56,6 +56,20 @@ cudaError_t launch_twiddle_matrix(c2<T>* tw, int N, int lo, int n, cudaStream_t 
 
 // Pair densities, stage B: pruned DFT along the middle axis,
 //   T2[pl][o1][o2][j3] = sum_j2 T1[pl][o1][j2][j3] exp(-2 pi i (g2lo+o2) j2 / N2).
+// Stages A and B with the N-point axis factorised as (N / L) x L (two-level
+// pruned DFT; factored_radix picks L, 0 = keep the direct form); the table
+// comes from launch_twiddle_factored (L^2 + (N / L) * 16 entries).
+int factored_radix(int N, int n);
+template <typename T>
+cudaError_t launch_twiddle_factored(c2<T>* tw, int N, int L, int lo, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pd_stageA_fact(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
+                                  const int* Ridx, int nR, int64_t p0, int np, const c2<T>* twf, int L, int n1,
+                                  c2<T>* T1, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pd_stageB_fact(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* twf, int L,
+                                  int n2, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* tw, int n2,
                              cudaStream_t s);

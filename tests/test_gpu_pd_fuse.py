@@ -40,6 +40,9 @@ def test_fused_pair_density_stages_bit_identical(case, precision):
     ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, precision)
     try:
         b.load_problem(ctx, p, paw_Q=lambda i, gm: syn.paw_Q(p.paw, p.cell, p.qpoints[i].q_red, gm))
+        # direct middle axis in both forms (the factorised one is a different sum)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_PD_FACT, 0)
+        b.rpa_set_tuning(ctx, b.RPA_TUNE_PD_FUSE, 1)
         fused = b.rpa_chi0(ctx, iq, om)
         b.rpa_set_tuning(ctx, b.RPA_TUNE_PD_FUSE, 0)
         split = b.rpa_chi0(ctx, iq, om)
