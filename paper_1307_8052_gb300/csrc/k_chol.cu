@@ -17,6 +17,8 @@
 // columns are written back in FP64, so the finished factor has one format.
 #include "ff_math.cuh"
 #include "rpa.h"
+#include <algorithm>
+
 #include "rpa_internal.h"
 
 namespace rpa {
@@ -82,16 +84,16 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 // I) are updated together; the logs are taken once at the end.
 // FF: the block is read in float-float form and the inverse is also written
 // in float-float form to Linv_ff; the factor always goes back in FP64.
+// Body for one matrix Aw (its logdet slot, flag and CB x CB inverse slices).
 template <bool FF>
-__global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A, int NG, int k0, int b,
-                                                        double* __restrict__ logdet, int* __restrict__ flag,
-                                                        double2* __restrict__ Linv, float4* __restrict__ Linv_ff) {
+__device__ __forceinline__ void chol_diag_body(double2* __restrict__ Aw, int NG, int k0, int b, double* ld_w,
+                                               int* __restrict__ flag, double2* __restrict__ Lw,
+                                               float4* __restrict__ Lffw) {
   __shared__ double2 L[CB][CB + 1];
   __shared__ double2 X[CB][CB + 1];  // right-hand side I, then L^-1
   __shared__ double piv_s[CB];
   __shared__ double dinv_s;
-  const int w = blockIdx.x, tid = threadIdx.x;
-  double2* Aw = A + (int64_t)w * NG * NG;
+  const int tid = threadIdx.x;
   for (int e = tid; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, j = e % CB;
     double2 a = make_double2(0.0, 0.0);
@@ -160,16 +162,24 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A,
     double ld = tid < b ? log(piv_s[tid]) : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
-    if (tid == 0) logdet[w] += ld;
+    if (tid == 0) *ld_w += ld;
   }
-  double2* Lw = Linv + (int64_t)w * CB * CB;
   for (int e = tid; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, j = e % CB;
     const double2 x = (i < b && j <= i) ? X[i][j] : make_double2(0.0, 0.0);
     Lw[e] = x;
-    if constexpr (FF) Linv_ff[(int64_t)w * CB * CB + e] = ff_split(x);
+    if constexpr (FF) Lffw[e] = ff_split(x);
     if (i < b && j <= i) Aw[(int64_t)(k0 + i) * NG + k0 + j] = L[i][j];
   }
+}
+
+template <bool FF>
+__global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A, int NG, int k0, int b,
+                                                        double* __restrict__ logdet, int* __restrict__ flag,
+                                                        double2* __restrict__ Linv, float4* __restrict__ Linv_ff) {
+  const int w = blockIdx.x;
+  chol_diag_body<FF>(A + (int64_t)w * NG * NG, NG, k0, b, logdet + w, flag, Linv + (int64_t)w * CB * CB,
+                     FF ? Linv_ff + (int64_t)w * CB * CB : nullptr);
 }
 
 // Panel below the diagonal block: X = A_panel L_kk^-H, i.e.
@@ -180,19 +190,18 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ A,
 // frequency, float-float) for the trailing update.
 constexpr int TROWS = 16;  // rows per triangular-solve CTA
 
+// Body for one matrix Aw, its inverse slices and its panel Pw ([NG][CB]), row tile bx.
 template <bool FF>
-__global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A, int NG, int k0, int b,
-                                                        const double2* __restrict__ Linv,
-                                                        const float4* __restrict__ Linv_ff, float4* __restrict__ Lp) {
+__device__ __forceinline__ void chol_trsm_body(double2* __restrict__ Aw, int NG, int k0, int b,
+                                               const double2* __restrict__ Lw, const float4* __restrict__ Lffw,
+                                               float4* __restrict__ Pw, int bx) {
   using E = typename std::conditional<FF, float4, double2>::type;
   __shared__ E Li[CB][CB + 1];
   __shared__ E X[TROWS][CB + 1];
-  const int w = blockIdx.y;
-  double2* Aw = A + (int64_t)w * NG * NG;
-  const int i0 = k0 + b + blockIdx.x * TROWS;
+  const int i0 = k0 + b + bx * TROWS;
   for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-    if constexpr (FF) Li[e / CB][e % CB] = Linv_ff[(int64_t)w * CB * CB + e];
-    else Li[e / CB][e % CB] = Linv[(int64_t)w * CB * CB + e];
+    if constexpr (FF) Li[e / CB][e % CB] = Lffw[e];
+    else Li[e / CB][e % CB] = Lw[e];
   }
   for (int e = threadIdx.x; e < TROWS * CB; e += blockDim.x) {
     const int r = e / CB, l = e % CB;
@@ -222,13 +231,23 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A,
       ff_norm(s.x, s.y);
       ff_norm(s.z, s.w);
       Aw[(int64_t)row * NG + k0 + j] = ff_to_double(s);
-      Lp[((int64_t)w * NG + row) * CB + j] = s;
+      Pw[(int64_t)row * CB + j] = s;
     } else {
       double2 s = make_double2(0.0, 0.0);
       for (int l = 0; l <= j; ++l) cmac_cj<double>(s, X[r][l], Li[j][l]);
       Aw[(int64_t)row * NG + k0 + j] = s;
     }
   }
+}
+
+template <bool FF>
+__global__ void __launch_bounds__(256) chol_trsm_kernel(double2* __restrict__ A, int NG, int k0, int b,
+                                                        const double2* __restrict__ Linv,
+                                                        const float4* __restrict__ Linv_ff, float4* __restrict__ Lp) {
+  const int w = blockIdx.y;
+  chol_trsm_body<FF>(A + (int64_t)w * NG * NG, NG, k0, b, Linv + (int64_t)w * CB * CB,
+                     FF ? Linv_ff + (int64_t)w * CB * CB : nullptr, FF ? Lp + (int64_t)w * NG * CB : nullptr,
+                     blockIdx.x);
 }
 
 __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
@@ -297,15 +316,12 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double2* __restrict__ 
 constexpr int UTF = 32;
 static_assert(UTF == CB, "the look-ahead strip of the trailing update is one panel wide");
 
-__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b, int s0,
-                                                               int strip, const float4* __restrict__ Lp) {
+// Body for one matrix (A_w in float-float form) and its panel Pw, tile (ti, tj) from s0.
+__device__ __forceinline__ void chol_update_ff_body(double2* __restrict__ A_w, int NG, int k0, int b, int s0, int ti,
+                                                    int tj, const float4* __restrict__ Pw) {
   __shared__ float4 Li[CB][UTF];
   __shared__ float4 Lj[CB][UTF];
-  const int w = blockIdx.y;
-  float4* Aw = reinterpret_cast<float4*>(A) + (int64_t)w * NG * NG;
-  const float4* Pw = Lp + (int64_t)w * NG * CB;
-  int ti = blockIdx.x, tj = 0;
-  if (!strip) tri_tile(blockIdx.x, ti, tj);
+  float4* Aw = reinterpret_cast<float4*>(A_w);
   const int r0 = s0 + ti * UTF, c0 = s0 + tj * UTF;
   for (int e = threadIdx.x; e < b * UTF; e += blockDim.x) {
     const int rr = e / b, l = e % b;
@@ -353,6 +369,15 @@ __global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restri
         *p = v;
       }
     }
+}
+
+__global__ void __launch_bounds__(64, 6) chol_update_ff_kernel(double2* __restrict__ A, int NG, int k0, int b, int s0,
+                                                               int strip, const float4* __restrict__ Lp) {
+  const int w = blockIdx.y;
+  int ti = blockIdx.x, tj = 0;
+  if (!strip) tri_tile(blockIdx.x, ti, tj);
+  // A holds 16-byte elements (double2, or float4 in float-float form)
+  chol_update_ff_body(A + (int64_t)w * NG * NG, NG, k0, b, s0, ti, tj, Lp + (int64_t)w * NG * CB);
 }
 
 __global__ void add_terms_kernel(const double* __restrict__ ld, const double* __restrict__ tr, int nw,
@@ -500,6 +525,115 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
       }
     }
     nl += rest > 0 ? 3 : 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (launches) *launches += nl;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- batched log-det
+// The float-float factorisation (one stream, no look-ahead) of many matrices of
+// different orders in one set of launches: matrix m of the batch is one
+// frequency of one instance, described by LdMat (its own work slices and
+// outputs).  Every launch covers all matrices; a CTA whose matrix is already
+// factorised, or whose tile lies outside it, returns at once.  Per matrix the
+// arithmetic and its order are those of run_logdet with the float-float
+// update (bit-identical).
+__global__ void chol_form_batch_kernel(const LdMat* __restrict__ d) {
+  const LdMat m = d[blockIdx.y];
+  const int64_t total = (int64_t)m.NG * m.NG;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *m.logdet = 0.0;
+    *m.flag = 0;  // every matrix of the instance writes 0 before any pivot is taken
+  }
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(id % m.NG), i = (int)(id / m.NG);
+    if (j > i) continue;
+    const double sc = sqrt(m.v[i]) * sqrt(m.v[j]);
+    const double2 c = m.chi[id];
+    double2 a = make_double2(-sc * c.x, -sc * c.y);
+    if (i == j) {
+      a.x += 1.0;
+      a.y = 0.0;
+    }
+    reinterpret_cast<float4*>(m.A)[id] = ff_split(a);
+  }
+}
+
+__global__ void trace_batch_kernel(const LdMat* __restrict__ d) {
+  __shared__ double red[256];
+  const LdMat m = d[blockIdx.x];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m.NG; i += blockDim.x) s += m.v[i] * m.chi[(int64_t)i * m.NG + i].x;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *m.trace = red[0];
+}
+
+__global__ void __launch_bounds__(256) chol_diag_batch_kernel(const LdMat* __restrict__ d, int k0) {
+  const LdMat m = d[blockIdx.x];
+  if (k0 >= m.NG) return;
+  chol_diag_body<true>(m.A, m.NG, k0, min(CB, m.NG - k0), m.logdet, m.flag, m.Linv, m.Linv_ff);
+}
+
+__global__ void __launch_bounds__(256) chol_trsm_batch_kernel(const LdMat* __restrict__ d, int k0) {
+  const LdMat m = d[blockIdx.y];
+  const int b = min(CB, m.NG - k0);
+  if (k0 + b >= m.NG || k0 + b + (int)blockIdx.x * TROWS >= m.NG) return;
+  chol_trsm_body<true>(m.A, m.NG, k0, b, m.Linv, m.Linv_ff, m.Lp, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(64, 6) chol_update_ff_batch_kernel(const LdMat* __restrict__ d, int k0) {
+  const LdMat m = d[blockIdx.y];
+  const int b = min(CB, m.NG - k0);
+  const int rest = m.NG - k0 - b;
+  if (rest <= 0) return;
+  const int nt = (rest + UTF - 1) / UTF;
+  if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  chol_update_ff_body(m.A, m.NG, k0, b, k0 + b, ti, tj, m.Lp);
+}
+
+// The slices of run_logdet's work buffer for frequency w (matrix, inverses, first panel).
+LdMat logdet_mat(double2* work, int nw, int NG, int w) {
+  LdMat m{};
+  double2* Linv = work + (int64_t)nw * NG * NG;
+  float4* Lff = reinterpret_cast<float4*>(Linv + (int64_t)nw * CB * CB);
+  float4* Lp = Lff + (int64_t)nw * CB * CB;
+  m.A = work + (int64_t)w * NG * NG;
+  m.Linv = Linv + (int64_t)w * CB * CB;
+  m.Linv_ff = Lff + (int64_t)w * CB * CB;
+  m.Lp = Lp + (int64_t)w * NG * CB;
+  m.NG = NG;
+  return m;
+}
+
+cudaError_t run_logdet_batch(const LdMat* d, int nmat, int maxNG, cudaStream_t s, int64_t* launches) {
+  if (nmat == 0 || maxNG == 0) return cudaSuccess;
+  int64_t nl = 0;
+  const int fx = (int)std::min<int64_t>(((int64_t)maxNG * maxNG + 255) / 256, 64);
+  chol_form_batch_kernel<<<dim3(fx, nmat), 256, 0, s>>>(d);
+  trace_batch_kernel<<<nmat, 256, 0, s>>>(d);
+  nl += 2;
+  cudaError_t e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int k0 = 0; k0 < maxNG; k0 += CB) {
+    const int b = std::min(CB, maxNG - k0);
+    const int rest = maxNG - k0 - b;
+    chol_diag_batch_kernel<<<nmat, 256, 0, s>>>(d, k0);
+    ++nl;
+    if (rest > 0) {
+      chol_trsm_batch_kernel<<<dim3((rest + TROWS - 1) / TROWS, nmat), 256, 0, s>>>(d, k0);
+      const int nt = (rest + UTF - 1) / UTF;
+      chol_update_ff_batch_kernel<<<dim3(nt * (nt + 1) / 2, nmat), 64, 0, s>>>(d, k0);
+      nl += 2;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (launches) *launches += nl;

@@ -2065,6 +2065,10 @@ struct rpa_graph {
   size_t pool_bytes = 0;
   int* dev = nullptr;          // [0] item counter, [1] error flag
   int** err_dst = nullptr;     // every context's error flag (device array)
+  // batched log-dets: per group, the matrix descriptors (device copy, written
+  // once before capture) and the host copy they were made from
+  std::vector<LdMat*> ld_dev;
+  std::vector<std::vector<LdMat>> ld_host;
 };
 
 namespace {
@@ -2156,6 +2160,17 @@ rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int3
   }
   rpa_ctx* c0 = ctxs[0];
   CUDA_OK(c0, cudaMemsetAsync(g->dev + 1, 0, sizeof(int), s));
+  // each context's log-det work buffer at its largest size up front, so its
+  // address (held by the batched log-det descriptors) never changes
+  {
+    std::vector<int64_t> need(n, 0);
+    for (const BatchUnit& U : g->units)
+      need[U.ctx] = std::max(need[U.ctx], logdet_work_elems(ctxs[U.ctx]->nw_set, ctxs[U.ctx]->qpts[U.iq].NG));
+    for (int i = 0; i < n; ++i) {
+      void* p;
+      if (need[i] && (st = workspace(ctxs[i], "chol", sizeof(double2) * (size_t)need[i], &p)) != RPA_OK) return st;
+    }
+  }
   std::vector<double2*> chi(g->units.size(), nullptr);
   for (int gi = 0; gi < (int)g->groups.size(); ++gi) {
     // units starting here: chi0 cleared, grids of their sets built
@@ -2210,7 +2225,11 @@ rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int3
                                     unit_of.data(), chis.data(), fused, (int)c0->tune[RPA_TUNE_TC_FOLD],
                                     (int)c0->tune[RPA_TUNE_TC_FLUSH], c0->tune[RPA_TUNE_TC_WAIT_US], g->dev,
                                     g->dev + 1, s));
-    // log-dets of the units that end here
+    // log-dets of the units that end here: the float-float ones of distinct
+    // contexts as one batched factorisation, the others one by one
+    std::vector<LdMat> mats;
+    std::vector<int> in_batch;
+    int maxNG = 0;
     for (size_t u = 0; u < g->units.size(); ++u) {
       const BatchUnit& U = g->units[u];
       if (U.g_last != gi) continue;
@@ -2220,13 +2239,51 @@ rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int3
       void* p_work;
       if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw_, Q.NG), &p_work)) != RPA_OK)
         return st;
+      double* ld = (double*)c->ws["res_ld"].p + (size_t)U.pos * nw_;
+      double* tr = (double*)c->ws["res_tr"].p + (size_t)U.pos * nw_;
+      int* fl = (int*)c->ws["res_flag"].p + U.pos;
+      const bool shared = std::find(in_batch.begin(), in_batch.end(), U.ctx) != in_batch.end();
+      if (ff_logdet(c) && !shared) {
+        for (int w = 0; w < nw_; ++w) {
+          LdMat m = logdet_mat((double2*)p_work, nw_, Q.NG, w);
+          m.chi = chi[u] + (int64_t)w * Q.NG * Q.NG;
+          m.v = Q.v_d;
+          m.logdet = ld + w;
+          m.trace = tr + w;
+          m.flag = fl;
+          mats.push_back(m);
+        }
+        in_batch.push_back(U.ctx);
+        maxNG = std::max(maxNG, Q.NG);
+        continue;
+      }
       const LogdetStreams* la;
       if ((st = logdet_streams(c, &la)) != RPA_OK) return st;
       int64_t nl = 0;
-      CUDA_OK(c, run_logdet(chi[u], Q.v_d, nw_, Q.NG, (double2*)p_work,
-                            (double*)c->ws["res_ld"].p + (size_t)U.pos * nw_,
-                            (double*)c->ws["res_tr"].p + (size_t)U.pos * nw_, (int*)c->ws["res_flag"].p + U.pos,
-                            ff_logdet(c), s, &nl, la));
+      CUDA_OK(c, run_logdet(chi[u], Q.v_d, nw_, Q.NG, (double2*)p_work, ld, tr, fl, ff_logdet(c), s, &nl, la));
+    }
+    if (!mats.empty()) {
+      if ((int)g->ld_dev.size() <= gi) {
+        g->ld_dev.resize(g->groups.size(), nullptr);
+        g->ld_host.resize(g->groups.size());
+      }
+      if (!g->ld_dev[gi]) {
+        // first (uncaptured) pass: the descriptors go to the device once
+        CUDA_OK(c0, cudaMalloc((void**)&g->ld_dev[gi], sizeof(LdMat) * mats.size()));
+        CUDA_OK(c0, cudaMemcpy(g->ld_dev[gi], mats.data(), sizeof(LdMat) * mats.size(), cudaMemcpyHostToDevice));
+        g->ld_host[gi] = mats;
+      } else {
+        const std::vector<LdMat>& h = g->ld_host[gi];
+        bool same = h.size() == mats.size();
+        for (size_t i = 0; same && i < h.size(); ++i)
+          same = h[i].A == mats[i].A && h[i].Linv == mats[i].Linv && h[i].Linv_ff == mats[i].Linv_ff &&
+                 h[i].Lp == mats[i].Lp && h[i].chi == mats[i].chi && h[i].v == mats[i].v &&
+                 h[i].logdet == mats[i].logdet && h[i].trace == mats[i].trace && h[i].flag == mats[i].flag &&
+                 h[i].NG == mats[i].NG;
+        if (!same) return fail(c0, RPA_ERR_STATE, "batched log-det buffers moved between the warm-up and the capture");
+      }
+      int64_t nl = 0;
+      CUDA_OK(c0, run_logdet_batch(g->ld_dev[gi], (int)mats.size(), maxNG, s, &nl));
     }
   }
   // a bounded wait that gave up reaches every context's flag
@@ -2348,6 +2405,8 @@ void rpa_graph_destroy(rpa_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->pool) cudaFree(g->pool);
+  for (LdMat* p : g->ld_dev)
+    if (p) cudaFree(p);
   if (g->dev) cudaFree(g->dev);
   if (g->err_dst) cudaFree(g->err_dst);
   delete g;

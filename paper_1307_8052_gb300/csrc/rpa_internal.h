@@ -163,6 +163,27 @@ cudaError_t launch_rotate_P(const double2* P, int nb, int KP, int natoms, const 
 // inverses of its diagonal blocks.
 int64_t logdet_work_elems(int nw, int NG);
 
+// One matrix of a batched float-float log-det (one frequency of one
+// instance): slices of that instance's run_logdet work buffer (the matrix, the
+// two CB x CB inverses, the first [NG][CB] panel) and its outputs.
+struct LdMat {
+  double2* A;
+  double2* Linv;
+  float4* Linv_ff;
+  float4* Lp;
+  const double2* chi;  // chi0 of this frequency [NG][NG]
+  const double* v;     // Coulomb kernel [NG]
+  double* logdet;      // ln det of this frequency
+  double* trace;       // tr(v chi0) of this frequency
+  int* flag;           // the instance's non-HPD flag
+  int NG;
+};
+// Float-float log-dets of nmat matrices (descriptors in device memory) in one
+// sequence of launches on s (no look-ahead); maxNG = the largest NG.
+cudaError_t run_logdet_batch(const LdMat* d, int nmat, int maxNG, cudaStream_t s, int64_t* launches);
+// LdMat of frequency w with the work-buffer slices filled in (outputs unset).
+LdMat logdet_mat(double2* work, int nw, int NG, int w);
+
 // Second stream and events of the look-ahead factorisation (float-float mode).
 struct LogdetStreams {
   cudaStream_t s2;
