@@ -296,10 +296,14 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  * RPA_TUNE_TC_FLUSH    folds between additions of the register running sums
  *                      to the FP64 chi0, in [1, 2^20]; default 256.
  * RPA_TUNE_PD_GRID     0 (default): wavefunctions and pair densities use,
- *                      per axis, the smallest grid on which the transform of
- *                      Eq. 10 has no aliasing for the transitions of the call
- *                      (never larger than params.grid); results equal the
- *                      plane-wave sums of Eq. 4 either way.  1: params.grid.
+ *                      per axis, a grid on which the transform of Eq. 10 has
+ *                      no aliasing for the transitions of the call: the
+ *                      smallest one, or with RPA_TUNE_PD_FACT = 1 the one of
+ *                      least pair-density work among the next eight sizes
+ *                      (a size that factorises can cost less than a smaller
+ *                      one), never larger than params.grid; results equal
+ *                      the plane-wave sums of Eq. 4 either way.
+ *                      1: params.grid.
  * RPA_TUNE_OPERAND_MB  device memory (MiB, >= 16) for the pair densities and
  *                      rank-k operands of one block of occupied bands; larger
  *                      pair sets are processed in several blocks.  Default 6144.

@@ -425,8 +425,10 @@ void choose_transform_grid(rpa_ctx* c, const int* iqs, int nq) {
     for (int d = 0; d < 3; ++d) c->tg[d] = c->prm.grid[d];
     return;
   }
+  int nout[3] = {1, 1, 1}, ngmax = 1;  // widest G+G0 extent per axis, largest sphere
   for (int i = 0; i < nq; ++i) {
     const QPt& Q = c->qpts[iqs[i]];
+    ngmax = std::max(ngmax, Q.NG);
     for (size_t t = 0; t < Q.k_of.size(); ++t) {
       const OrbSet& a = c->sets[Q.k_of[t]];
       const OrbSet& b = c->sets[Q.kq_of[t]];
@@ -440,10 +442,36 @@ void choose_transform_grid(rpa_ctx* c, const int* iqs, int nq) {
         int need = std::max(b.mhi[d] - a.mlo[d] - glo, ghi + a.mhi[d] - b.mlo[d]) + 1;
         need = std::max(need, std::max(a.mhi[d] - a.mlo[d] + 1, b.mhi[d] - b.mlo[d] + 1));
         c->tg[d] = std::max(c->tg[d], need);
+        nout[d] = std::max(nout[d], ghi - glo + 1);
       }
     }
   }
   for (int d = 0; d < 3; ++d) c->tg[d] = std::min(c->tg[d], c->prm.grid[d]);
+  if (c->tune[RPA_TUNE_PD_FACT] != 1) return;
+  // Any grid at least as large is alias-free too; among the next few sizes
+  // take the one with the least pair-density work per pair, counted in complex
+  // multiply-adds: the products and loads of stage A (2 per point), the
+  // slowest and middle axes (direct N n or factorised N L + (N / L) n per
+  // line) and the fastest-axis gather (NG N3).
+  auto axis = [](int N, int n) -> int64_t {
+    const int L = n <= 16 ? factored_radix(N, n) : 0;
+    return L ? (int64_t)N * L + (int64_t)(N / L) * n : (int64_t)N * n;
+  };
+  int best[3] = {c->tg[0], c->tg[1], c->tg[2]};
+  int64_t best_cost = -1;
+  for (int N1 = c->tg[0]; N1 <= std::min(c->tg[0] + 8, c->prm.grid[0]); ++N1)
+    for (int N2 = c->tg[1]; N2 <= std::min(c->tg[1] + 8, c->prm.grid[1]); ++N2)
+      for (int N3 = c->tg[2]; N3 <= std::min(c->tg[2] + 8, c->prm.grid[2]); ++N3) {
+        const int64_t cost = 2 * (int64_t)N1 * N2 * N3 + (int64_t)N2 * N3 * axis(N1, nout[0]) +
+                             (int64_t)nout[0] * N3 * axis(N2, nout[1]) + (int64_t)ngmax * N3;
+        if (best_cost < 0 || cost < best_cost) {
+          best_cost = cost;
+          best[0] = N1;
+          best[1] = N2;
+          best[2] = N3;
+        }
+      }
+  for (int d = 0; d < 3; ++d) c->tg[d] = best[d];
 }
 
 // ---- stages a2-a4 for one q-point: chi accumulates in FP64 lower triangle
