@@ -393,6 +393,11 @@ rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
  *                      multiply-adds per line where that saves a fifth or
  *                      more, at most 16 outputs a line); 0: direct sums.
  *                      The two agree to FP32 rounding.
+ * RPA_TUNE_LD_OVERLAP 1 (default): in rpa_energy / rpa_energy_enqueue with
+ *                      several q-points, the log-det of one q-point runs on
+ *                      a stream of its own beside chi0 of the next (same
+ *                      results); 0: one after the other on the context
+ *                      stream.
  * Out-of-range values return RPA_ERR_ARG and leave the setting unchanged. */
 typedef enum {
   RPA_TUNE_TC_FOLD = 0,
@@ -412,7 +417,8 @@ typedef enum {
   RPA_TUNE_GAMMA = 14,
   RPA_TUNE_TC_PAIR = 15,
   RPA_TUNE_PD_FACT = 16,
-  RPA_TUNE_COUNT = 17
+  RPA_TUNE_LD_OVERLAP = 17,
+  RPA_TUNE_COUNT = 18
 } rpa_tuning;
 rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
 

@@ -58,8 +58,8 @@ RPA_NSTAGES = 6  # profile stages: wf, pair densities, rank-k kernel, log-det, o
 (RPA_TUNE_TC_FOLD, RPA_TUNE_PAIR_CHUNK, RPA_TUNE_TC_FLUSH, RPA_TUNE_PD_GRID, RPA_TUNE_OPERAND_MB, RPA_TUNE_TC_PIPE,
  RPA_TUNE_LOGDET, RPA_TUNE_PAW_TC, RPA_TUNE_TC_FUSE, RPA_TUNE_TC_WAIT_US, RPA_TUNE_TC_STALL,
  RPA_TUNE_PD_FUSE, RPA_TUNE_BATCH_PERSIST, RPA_TUNE_BATCH_MB, RPA_TUNE_GAMMA,
- RPA_TUNE_TC_PAIR, RPA_TUNE_PD_FACT) = range(17)
-RPA_TUNE_COUNT = 17
+ RPA_TUNE_TC_PAIR, RPA_TUNE_PD_FACT, RPA_TUNE_LD_OVERLAP) = range(18)
+RPA_TUNE_COUNT = 18
 
 
 class RpaParams(ct.Structure):

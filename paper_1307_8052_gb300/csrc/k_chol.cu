@@ -480,7 +480,7 @@ static cudaError_t run_logdet_ff_lookahead(int nw, int NG, double2* work, double
 
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work, double* logdet,
                        double* trace, int* flag, bool ff_update, cudaStream_t s, int64_t* launches,
-                       const LogdetStreams* la) {
+                       const LogdetStreams* la, cudaEvent_t formed) {
   cudaError_t e;
   int64_t nl = 0;
   const int upd_smem = 2 * CB * UT * (int)sizeof(double2);
@@ -500,6 +500,7 @@ cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, doub
   trace_kernel<<<nw, 256, 0, s>>>(chi, v, NG, trace);
   nl += 2;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (formed && (e = cudaEventRecord(formed, s)) != cudaSuccess) return e;
   if (ff_update && la) {
     e = run_logdet_ff_lookahead(nw, NG, work, logdet, flag, *la, s, &nl);
     if (launches) *launches += nl;

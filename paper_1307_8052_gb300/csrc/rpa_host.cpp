@@ -157,6 +157,9 @@ struct rpa_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // second stream and events of the look-ahead Cholesky (float-float log-det)
   LogdetStreams ld{nullptr, nullptr, nullptr};
+  // stream of the log-dets that overlap the next q-point's chi0, and its events
+  cudaStream_t ld_stream = nullptr;
+  cudaEvent_t ev_chi = nullptr, ev_formed = nullptr, ev_ld = nullptr;
   double B[9] = {0};  // reciprocal rows
   double volume = 0.0;
   std::string err;
@@ -170,7 +173,7 @@ struct rpa_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 2, 0, 1};  // see rpa_tuning in rpa.h
+  int64_t tune[RPA_TUNE_COUNT] = {1, 0, 256, 0, 6144, 0, 2, 0, 0, 4000000, 0, 0, 1, 16384, 2, 0, 1, 1};  // see rpa_tuning in rpa.h
   double* omega_d = nullptr;  // frequencies of rpa_set_frequencies (device)
   int nw_set = 0;
   std::vector<int> enq_iqs;   // q-points of the last rpa_energy_enqueue
@@ -896,7 +899,23 @@ rpa_status energy_enqueue(rpa_ctx* c, int nq, const int* iqs, int nw, const doub
   if ((st = workspace(c, "res_tr", sizeof(double) * (size_t)nq * nw, &p_tr)) != RPA_OK) return st;
   if ((st = workspace(c, "res_flag", sizeof(int) * (size_t)nq, &p_fl)) != RPA_OK) return st;
   CUDA_OK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+  // The log-det of q-point i runs on its own stream beside chi0 of q-point
+  // i + 1, which may overwrite the chi0 buffer once that log-det has formed
+  // its matrix; the buffers are sized for the largest q-point first, so no
+  // reallocation waits for the device in between.
+  const bool overlap = c->tune[RPA_TUNE_LD_OVERLAP] == 1 && nq > 1;
+  if (overlap) {
+    int ngmax = 0;
+    for (int i = 0; i < nq; ++i) ngmax = std::max(ngmax, c->qpts[iqs[i]].NG);
+    void* p;
+    if ((st = workspace(c, "chi", sizeof(double2) * (size_t)nw * ngmax * ngmax, &p)) != RPA_OK) return st;
+    if ((st = workspace(c, "chol", sizeof(double2) * (size_t)logdet_work_elems(nw, ngmax), &p)) != RPA_OK) return st;
+    if (!c->ld_stream) CUDA_OK(c, cudaStreamCreateWithFlags(&c->ld_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&c->ev_chi, &c->ev_formed, &c->ev_ld})
+      if (!*e) CUDA_OK(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
   for (int i = 0; i < nq; ++i) {
+    if (overlap && i > 0) CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_formed, 0));
     double2* chi = nullptr;
     if ((st = build_chi_async(c, iqs[i], nw, omega_d, &chi)) != RPA_OK) return st;
     QPt& Q = c->qpts[iqs[i]];
@@ -905,10 +924,21 @@ rpa_status energy_enqueue(rpa_ctx* c, int nq, const int* iqs, int nw, const doub
     int64_t nl = 0;
     const LogdetStreams* la;
     if ((st = logdet_streams(c, &la)) != RPA_OK) return st;
-    StageTimer tm(c, 3, 0);
+    cudaStream_t ls = c->stream;
+    if (overlap) {
+      CUDA_OK(c, cudaEventRecord(c->ev_chi, c->stream));
+      CUDA_OK(c, cudaStreamWaitEvent(c->ld_stream, c->ev_chi, 0));
+      ls = c->ld_stream;
+    }
+    StageTimer tm(c, 3, 0, ls);
     CUDA_OK(c, run_logdet(chi, Q.v_d, nw, Q.NG, (double2*)p_work, (double*)p_ld + (size_t)i * nw,
-                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, ff_logdet(c), c->stream, &nl, la));
+                          (double*)p_tr + (size_t)i * nw, (int*)p_fl + i, ff_logdet(c), ls, &nl, la,
+                          overlap ? c->ev_formed : nullptr));
     tm.add_launches(nl);
+  }
+  if (overlap) {
+    CUDA_OK(c, cudaEventRecord(c->ev_ld, c->ld_stream));
+    CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_ld, 0));
   }
   c->enq_iqs.assign(iqs, iqs + nq);
   return RPA_OK;
@@ -1377,6 +1407,12 @@ void rpa_destroy(rpa_ctx* c) {
   }
   if (c->ld.ev_t) cudaEventDestroy(c->ld.ev_t);
   if (c->ld.ev_u) cudaEventDestroy(c->ld.ev_u);
+  if (c->ld_stream) {
+    cudaStreamSynchronize(c->ld_stream);
+    cudaStreamDestroy(c->ld_stream);
+  }
+  for (cudaEvent_t e : {c->ev_chi, c->ev_formed, c->ev_ld})
+    if (e) cudaEventDestroy(e);
   dev_free(c->dev_err);
   dev_free(c->omega_d);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -2517,6 +2553,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
       break;
     case RPA_TUNE_PD_FACT:
       if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "factorised pair-density axes must be 0 or 1");
+      break;
+    case RPA_TUNE_LD_OVERLAP:
+      if (value != 0 && value != 1) return fail(c, RPA_ERR_ARG, "log-det overlap must be 0 or 1");
       break;
     case RPA_TUNE_BATCH_MB:
       if (value < 1 || value > (1 << 22)) return fail(c, RPA_ERR_ARG, "batch group budget %lld MiB out of range", (long long)value);

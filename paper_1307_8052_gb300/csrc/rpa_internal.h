@@ -194,8 +194,10 @@ struct LogdetStreams {
 // per-w ln det in logdet, tr(v^1/2 chi v^1/2) in trace, pivot failure in flag.
 // ff_update evaluates the trailing updates in float-float arithmetic; with la
 // it also factorises the next panel beside the rest of the current update.
+// formed (optional) is recorded on s once chi has been read (matrix formed,
+// trace taken), after which the caller may reuse the chi buffer.
 cudaError_t run_logdet(const double2* chi, const double* v, int nw, int NG, double2* work,
                        double* logdet, double* trace, int* flag, bool ff_update, cudaStream_t s,
-                       int64_t* launches, const LogdetStreams* la = nullptr);
+                       int64_t* launches, const LogdetStreams* la = nullptr, cudaEvent_t formed = nullptr);
 
 }  // namespace rpa
