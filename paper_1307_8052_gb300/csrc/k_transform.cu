@@ -191,13 +191,21 @@ __host__ __device__ constexpr int ring_offset(int n) {
   return (int)(((size_t)n * TS * sizeof(c2<T>) + 15) / 16 * 16);
 }
 constexpr int RING_PF = 4;       // stages of the ring
+
+// Pair of chunk slot pl: a chunk holds nrow consecutive occupied rows of the
+// block and np / nrow consecutive unoccupied bands from p0 (row 0), rows
+// fastest, so neighbouring threads share an unoccupied band's grid; nrow = 1
+// is the contiguous range p0 + pl.
+__host__ __device__ inline int64_t chunk_pair(int pl, int64_t p0, int nrow, int nR) {
+  return (int64_t)(pl % nrow) * nR + p0 + pl / nrow;
+}
 constexpr int RING_THREADS = 256;
 
 template <typename T, int NO, int PP, int PF>
 __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
                                                         int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
                                                         const int* __restrict__ Ridx, int nR, int64_t p0, int np,
-                                                        const c2<T>* __restrict__ twg, int n1,
+                                                        int nrow, const c2<T>* __restrict__ twg, int n1,
                                                         c2<T>* __restrict__ T1) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
 #pragma unroll
       for (int q = 0; q < PP; ++q) {
         const int pl = min(grp * PP + q, np - 1);
-        const int64_t p = p0 + pl;
+        const int64_t p = chunk_pair(pl, p0, nrow, nR);
         un[q] = Uk + (int64_t)Lidx[p / nR] * Nr + j23;
         um[q] = Ukp + (int64_t)Ridx[p % nR] * Nr + j23;
       }
@@ -304,8 +312,8 @@ __global__ void __launch_bounds__(256) pd_stageA_kernel(const c2<T>* __restrict_
 
 template <typename T, int NO, int PF>
 static cudaError_t launch_stageA_pf(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                                    const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
-                                    cudaStream_t s) {
+                                    const int* Ridx, int nR, int64_t p0, int np, int nrow, const c2<T>* tw, int n1,
+                                    c2<T>* T1, cudaStream_t s) {
   constexpr int PP = sizeof(T) == 4 ? 2 : 1;
   const int64_t total = (int64_t)((np + PP - 1) / PP) * N23;
   if (total == 0) return cudaSuccess;
@@ -317,7 +325,7 @@ static cudaError_t launch_stageA_pf(const c2<T>* Uk, const c2<T>* Ukp, int64_t N
     if (e != cudaSuccess) return e;
   }
   pd_stageA_kernel<T, NO, PP, PF><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0,
-                                                                         np, tw, n1, T1);
+                                                                         np, nrow, tw, n1, T1);
   return cudaGetLastError();
 }
 
@@ -325,11 +333,11 @@ static cudaError_t launch_stageA_pf(const c2<T>* Uk, const c2<T>* Ukp, int64_t N
 // axes (table beyond 160 KB) fall back to one-slice register prefetch
 template <typename T, int NO>
 static cudaError_t launch_stageA_no(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                                    const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
-                                    cudaStream_t s) {
+                                    const int* Ridx, int nR, int64_t p0, int np, int nrow, const c2<T>* tw, int n1,
+                                    c2<T>* T1, cudaStream_t s) {
   if (ring_offset<T>(N1) <= 160 * 1024)
-    return launch_stageA_pf<T, NO, RING_PF>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
-  return launch_stageA_pf<T, NO, 1>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+    return launch_stageA_pf<T, NO, RING_PF>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, tw, n1, T1, s);
+  return launch_stageA_pf<T, NO, 1>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, tw, n1, T1, s);
 }
 
 // compute width: the smallest of 8, 12, 14, 16 that holds all outputs (16 with chunks beyond)
@@ -337,13 +345,14 @@ static inline int width_for(int n) { return n <= 8 ? 8 : n <= 12 ? 12 : n <= 14 
 
 template <typename T>
 cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                             const int* Ridx, int nR, int64_t p0, int np, const c2<T>* tw, int n1, c2<T>* T1,
+                             const int* Ridx, int nR, int64_t p0, int np, int nrow, const c2<T>* tw, int n1, c2<T>* T1,
                              cudaStream_t s) {
+  if (nrow < 1 || np % nrow) return cudaErrorInvalidValue;
   switch (width_for(n1)) {
-    case 8: return launch_stageA_no<T, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
-    case 12: return launch_stageA_no<T, 12>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
-    case 14: return launch_stageA_no<T, 14>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
-    default: return launch_stageA_no<T, 16>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, tw, n1, T1, s);
+    case 8: return launch_stageA_no<T, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, tw, n1, T1, s);
+    case 12: return launch_stageA_no<T, 12>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, tw, n1, T1, s);
+    case 14: return launch_stageA_no<T, 14>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, tw, n1, T1, s);
+    default: return launch_stageA_no<T, 16>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, tw, n1, T1, s);
   }
 }
 
@@ -505,7 +514,7 @@ template <typename T, int NO, int PP, int L>
 __global__ void __launch_bounds__(256) pd_stageA_fact_kernel(const c2<T>* __restrict__ Uk, const c2<T>* __restrict__ Ukp,
                                                              int64_t Nr, int N1, int N23, const int* __restrict__ Lidx,
                                                              const int* __restrict__ Ridx, int nR, int64_t p0, int np,
-                                                             const c2<T>* __restrict__ twg, int n1,
+                                                             int nrow, const c2<T>* __restrict__ twg, int n1,
                                                              c2<T>* __restrict__ T1) {
   constexpr int PF = RING_PF;
   extern __shared__ unsigned char smem_raw[];
@@ -527,7 +536,7 @@ __global__ void __launch_bounds__(256) pd_stageA_fact_kernel(const c2<T>* __rest
 #pragma unroll
     for (int q = 0; q < PP; ++q) {
       const int pl = min(grp * PP + q, np - 1);
-      const int64_t p = p0 + pl;
+      const int64_t p = chunk_pair(pl, p0, nrow, nR);
       un[q] = Uk + (int64_t)Lidx[p / nR] * Nr + j23;
       um[q] = Ukp + (int64_t)Ridx[p % nR] * Nr + j23;
     }
@@ -651,7 +660,7 @@ __global__ void __launch_bounds__(256) pd_stageB_fact_kernel(const c2<T>* __rest
 
 template <typename T, int NO, int L>
 static cudaError_t launch_stageA_fact_l(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
-                                        const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
+                                        const int* Lidx, const int* Ridx, int nR, int64_t p0, int np, int nrow,
                                         const c2<T>* twf, int n1, c2<T>* T1, cudaStream_t s) {
   constexpr int PP = sizeof(T) == 4 ? 2 : 1;
   const int64_t total = (int64_t)((np + PP - 1) / PP) * N23;
@@ -664,34 +673,34 @@ static cudaError_t launch_stageA_fact_l(const c2<T>* Uk, const c2<T>* Ukp, int64
     if (e != cudaSuccess) return e;
   }
   pd_stageA_fact_kernel<T, NO, PP, L><<<grid_for(total, 256), 256, smem, s>>>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR,
-                                                                             p0, np, twf, n1, T1);
+                                                                             p0, np, nrow, twf, n1, T1);
   return cudaGetLastError();
 }
 
 template <typename T, int NO>
 static cudaError_t launch_stageA_fact_no(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
-                                         const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
+                                         const int* Lidx, const int* Ridx, int nR, int64_t p0, int np, int nrow,
                                          const c2<T>* twf, int L, int n1, c2<T>* T1, cudaStream_t s) {
   switch (L) {
-    case 3: return launch_stageA_fact_l<T, NO, 3>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
-    case 4: return launch_stageA_fact_l<T, NO, 4>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
-    case 5: return launch_stageA_fact_l<T, NO, 5>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
-    case 6: return launch_stageA_fact_l<T, NO, 6>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
-    case 8: return launch_stageA_fact_l<T, NO, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, n1, T1, s);
+    case 3: return launch_stageA_fact_l<T, NO, 3>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, n1, T1, s);
+    case 4: return launch_stageA_fact_l<T, NO, 4>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, n1, T1, s);
+    case 5: return launch_stageA_fact_l<T, NO, 5>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, n1, T1, s);
+    case 6: return launch_stageA_fact_l<T, NO, 6>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, n1, T1, s);
+    case 8: return launch_stageA_fact_l<T, NO, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, n1, T1, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
 cudaError_t launch_pd_stageA_fact(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                                  const int* Ridx, int nR, int64_t p0, int np, const c2<T>* twf, int L, int n1,
-                                  c2<T>* T1, cudaStream_t s) {
-  if (n1 > TS || L < 2 || N1 % L) return cudaErrorInvalidValue;
+                                  const int* Ridx, int nR, int64_t p0, int np, int nrow, const c2<T>* twf, int L,
+                                  int n1, c2<T>* T1, cudaStream_t s) {
+  if (n1 > TS || L < 2 || N1 % L || nrow < 1 || np % nrow) return cudaErrorInvalidValue;
   switch (width_for(n1)) {
-    case 8: return launch_stageA_fact_no<T, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
-    case 12: return launch_stageA_fact_no<T, 12>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
-    case 14: return launch_stageA_fact_no<T, 14>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
-    default: return launch_stageA_fact_no<T, 16>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, twf, L, n1, T1, s);
+    case 8: return launch_stageA_fact_no<T, 8>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, L, n1, T1, s);
+    case 12: return launch_stageA_fact_no<T, 12>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, L, n1, T1, s);
+    case 14: return launch_stageA_fact_no<T, 14>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, L, n1, T1, s);
+    default: return launch_stageA_fact_no<T, 16>(Uk, Ukp, Nr, N1, N23, Lidx, Ridx, nR, p0, np, nrow, twf, L, n1, T1, s);
   }
 }
 
@@ -735,7 +744,8 @@ cudaError_t launch_pd_stageB_fact(const c2<T>* T1, c2<T>* T2, int np, int n1, in
 template <typename T>
 __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict__ T2, int np, int n1, int n2, int N3,
                                                         const int* __restrict__ gfft, int NG, int g1lo, int g2lo,
-                                                        double inv_nr, int64_t p0, c2<T>* __restrict__ Nout) {
+                                                        double inv_nr, int64_t p0, int nrow, int nR,
+                                                        c2<T>* __restrict__ Nout) {
   // Each thread handles one G and PG consecutive pairs (the fastest-axis DFT
   // of each pair; PG independent loads per step).
   constexpr int PG = 4;
@@ -757,7 +767,7 @@ __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict_
 #pragma unroll
     for (int q = 0; q < PG; ++q) {
       const int pl = min(grp * PG + q, np - 1);
-      pidx[q] = p0 + pl;
+      pidx[q] = chunk_pair(pl, p0, nrow, nR);
       src[q] = T2 + (((int64_t)pl * n1 + (g1 - g1lo)) * n2 + (g2 - g2lo)) * N3;
       acc[q] = mk<T>(0, 0);
     }
@@ -1003,11 +1013,12 @@ cudaError_t launch_paw_gemm(const c2<T>* R, const c2<T>* Pm, int KP, int nL, int
 
 template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft, int NG, int g1lo,
-                             int g2lo, double inv_nr, int64_t p0, c2<T>* Nout, cudaStream_t s) {
+                             int g2lo, double inv_nr, int64_t p0, int nrow, int nR, c2<T>* Nout, cudaStream_t s) {
   const int64_t total = (int64_t)((np + 3) / 4) * NG;
   if (total == 0) return cudaSuccess;
+  if (nrow < 1 || np % nrow) return cudaErrorInvalidValue;
   pd_stageC_kernel<T><<<grid_for(total, 256), 256, N3 * sizeof(c2<T>), s>>>(T2, np, n1, n2, N3, gfft, NG, g1lo, g2lo,
-                                                                          inv_nr, p0, Nout);
+                                                                          inv_nr, p0, nrow, nR, Nout);
   return cudaGetLastError();
 }
 
@@ -1109,17 +1120,17 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
   template cudaError_t launch_twiddle_matrix<T>(c2<T>*, int, int, int, cudaStream_t);                             \
   template cudaError_t launch_twiddle_factored<T>(c2<T>*, int, int, int, int, cudaStream_t);                    \
   template cudaError_t launch_pd_stageA_fact<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*,        \
-                                                const int*, int, int64_t, int, const c2<T>*, int, int, c2<T>*,    \
-                                                cudaStream_t);                                                    \
+                                                const int*, int, int64_t, int, int, const c2<T>*, int, int,       \
+                                                c2<T>*, cudaStream_t);                                            \
   template cudaError_t launch_pd_stageB_fact<T>(const c2<T>*, c2<T>*, int, int, int, int, const c2<T>*, int, int,  \
                                                 cudaStream_t);                                                    \
   template cudaError_t launch_pd_stageA<T>(const c2<T>*, const c2<T>*, int64_t, int, int, const int*, const int*, \
-                                           int, int64_t, int, const c2<T>*, int, c2<T>*, cudaStream_t);          \
+                                           int, int64_t, int, int, const c2<T>*, int, c2<T>*, cudaStream_t);     \
   template cudaError_t launch_pd_stageBC<T>(const c2<T>*, int, int, int, int, const c2<T>*, int, const int*,     \
                                              const int*, int, int, int, int, double, int64_t, c2<T>*, cudaStream_t); \
   template int pd_stageBC_slab<T>(int, int, int, int);                                                            \
   template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \
-                                           int64_t, c2<T>*, cudaStream_t);                                       \
+                                           int64_t, int, int, c2<T>*, cudaStream_t);                             \
   template cudaError_t launch_paw_gemm<T>(const c2<T>*, const c2<T>*, int, int, int, int, c2<T>*, cudaStream_t); \
   template cudaError_t launch_paw_R<T>(const double2*, int, const int*, int, const double2*, const int*,          \
                                        const int*, const int*, const int64_t*, const int*, int, c2<T>*,          \

@@ -658,14 +658,23 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
       if ((st = workspace(c, "pd_g1start", sizeof(int) * (size_t)(n1 + 1), &p_g1s)) != RPA_OK) return st;
       CUDA_OK(c, launch_g1start((const int*)p_gfft, NG, glo[0], n1, (int*)p_g1s, c->stream));
     }
-    for (int64_t p0 = 0; p0 < P; p0 += PC) {
-      const int np = (int)std::min<int64_t>(PC, P - p0);
+    // Chunks: with the split stages, every row of the block times a run of
+    // unoccupied bands, rows fastest, so that the threads of neighbouring
+    // pairs read the same unoccupied band's grid (read once per chunk rather
+    // than once per occupied band); with the fused stages B + C, contiguous
+    // pair ranges.
+    const int nrow = (OB == 0 && nL >= 2 && PC >= nL) ? nL : 1;
+    const int64_t cols = nrow > 1 ? PC / nrow : PC;
+    const int64_t span = nrow > 1 ? nR : P;
+    for (int64_t p0 = 0; p0 < span; p0 += cols) {
+      const int np = (int)(std::min<int64_t>(cols, span - p0) * nrow);
       if (LA)
         CUDA_OK(c, launch_pd_stageA_fact<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d,
-                                            nR, p0, np, (const c2<T>*)p_tfA, LA, n1, (c2<T>*)p_T1, c->stream));
+                                            nR, p0, np, nrow, (const c2<T>*)p_tfA, LA, n1, (c2<T>*)p_T1,
+                                            c->stream));
       else
         CUDA_OK(c, launch_pd_stageA<T>((const c2<T>*)sk.U, (const c2<T>*)skp.U, Nr, N1, (int)N23, Lsub, skp.R_d, nR,
-                                       p0, np, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
+                                       p0, np, nrow, (const c2<T>*)p_twA, n1, (c2<T>*)p_T1, c->stream));
       if (OB > 0) {
         CUDA_OK(c, launch_pd_stageBC<T>((const c2<T>*)p_T1, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                         (const int*)p_gfft, (const int*)p_g1s, OB, NG, glo[0], glo[1],
@@ -680,7 +689,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
         CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                        c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
-                                     1.0 / (double)Nr, p0, (c2<T>*)p_N, c->stream));
+                                     1.0 / (double)Nr, p0, nrow, nR, (c2<T>*)p_N, c->stream));
       tm.add_launches(3);
     }
     if (paw) {

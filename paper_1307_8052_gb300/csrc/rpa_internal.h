@@ -43,10 +43,12 @@ cudaError_t launch_scatter_box(const double2* C, int nb, int npw, const int* pos
                                c2<T>* out, cudaStream_t s);
 
 // Pair densities, stage A: fused conj(u_n) u_m product and pruned DFT along
-// the slowest grid axis.  Pairs p0 .. p0+np-1 of the rectangle L x R (a-major).
+// the slowest grid axis.  Chunk slot pl is pair (pl % nrow) * nR + p0 + pl / nrow
+// of the rectangle L x R (a-major): nrow rows of np / nrow columns from p0,
+// rows fastest; nrow = 1 is the contiguous range p0 .. p0+np-1.
 template <typename T>
 cudaError_t launch_pd_stageA(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23,
-                             const int* Lidx, const int* Ridx, int nR, int64_t p0, int np,
+                             const int* Lidx, const int* Ridx, int nR, int64_t p0, int np, int nrow,
                              const c2<T>* tw, int n1, c2<T>* T1, cudaStream_t s);
 
 // Twiddle matrices tw[oc][j][o] = exp(-2 pi i (lo + 16 oc + o) j / N) for the
@@ -64,8 +66,8 @@ template <typename T>
 cudaError_t launch_twiddle_factored(c2<T>* tw, int N, int L, int lo, int n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pd_stageA_fact(const c2<T>* Uk, const c2<T>* Ukp, int64_t Nr, int N1, int N23, const int* Lidx,
-                                  const int* Ridx, int nR, int64_t p0, int np, const c2<T>* twf, int L, int n1,
-                                  c2<T>* T1, cudaStream_t s);
+                                  const int* Ridx, int nR, int64_t p0, int np, int nrow, const c2<T>* twf, int L,
+                                  int n1, c2<T>* T1, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pd_stageB_fact(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2, int N3, const c2<T>* twf, int L,
                                   int n2, cudaStream_t s);
@@ -78,7 +80,8 @@ cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2,
 // points g = G + G0, 1/Nr normalisation, write N[p][NG].
 template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft,
-                             int NG, int g1lo, int g2lo, double inv_nr, int64_t p0, c2<T>* Nout, cudaStream_t s);
+                             int NG, int g1lo, int g2lo, double inv_nr, int64_t p0, int nrow, int nR, c2<T>* Nout,
+                             cudaStream_t s);
 
 // Pair densities, stages B and C fused per (pair, slab of OB first-axis
 // outputs): the middle-axis DFT into shared memory, then the fastest axis on
