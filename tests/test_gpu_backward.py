@@ -178,6 +178,50 @@ def test_config4_geometry_central_differences_fp64():
         b.rpa_destroy(ctx)
 
 
+def test_config4_full_bands_central_differences_fp64():
+    """The gradient workload at full size (16 + 1200 bands per set, all 8 k,
+    q = (1/2, 0, 0), NG ~ 1200, 16 frequencies, 3 x 13 projectors): the FP64
+    directional derivative along one random C direction and one random P
+    direction (all coefficients of a set) against the sixth-order central
+    difference with h = 1e-5.  Each FP64 energy at this size takes ~13 s, so
+    two directions (12 energies) are checked here; the 32-direction sweep runs
+    on the band subset above, and the mixed modes against this FP64 gradient
+    in the next test."""
+    full = syn.config1()
+    iq = [i for i, qp in enumerate(full.qpoints) if np.allclose(qp.q_red, [0.5, 0.0, 0.0])][0]
+    p = syn.Problem(full.name, 4, full.cell, full.grid, full.ecut_wf, full.ecut_chi, full.spin_factor,
+                    full.nk_bz, full.sets, [full.qpoints[iq]], 16, full.paw)
+    om, W = o.frequency_grid(p.nw)
+    ctx = _ctx(p, "fp64")
+    try:
+        E0, dC, dP, _ = _grad(ctx, p, om, W, [0])
+        rng = np.random.default_rng(5)
+        h = 1e-5
+        for s, which in ((1, "C"), (6, "P")):
+            base = getattr(p.sets[s], which).copy()
+            d = rng.standard_normal(base.shape) + 1j * rng.standard_normal(base.shape)
+            vals = []
+            for sign in (1, -1, 2, -2, 3, -3):
+                new = base + sign * h * d
+                if which == "C":
+                    b.rpa_set_orbitals(ctx, s, p.sets[s].k_red, p.sets[s].miller, new, p.sets[s].eps, p.sets[s].f)
+                    b.rpa_set_paw(ctx, s, p.paw.nproj, p.sets[s].P)
+                else:
+                    b.rpa_set_paw(ctx, s, p.paw.nproj, new)
+                vals.append(b.rpa_energy(ctx, [0], [p.qpoints[0].weight], om, W)[0])
+            b.rpa_set_orbitals(ctx, s, p.sets[s].k_red, p.sets[s].miller, p.sets[s].C, p.sets[s].eps, p.sets[s].f)
+            b.rpa_set_paw(ctx, s, p.paw.nproj, p.sets[s].P)
+            fd = (45.0 * (vals[0] - vals[1]) - 9.0 * (vals[2] - vals[3]) + (vals[4] - vals[5])) / (60.0 * h)
+            g = dC[s] if which == "C" else dP[s]
+            an = float(np.sum(np.conj(g) * d).real)
+            print(f"config-4 full bands, {which} of set {s}: analytic {an:.10e}, FD {fd:.10e}, "
+                  f"rel {abs(fd - an) / abs(an):.2e}")
+            # the bound of the band-subset test: 1e-6 plus the quotient's roundoff
+            assert abs(fd - an) <= 1e-6 * abs(an) + 1.83 * 1e-13 * abs(E0) / h, (which, s, fd, an)
+    finally:
+        b.rpa_destroy(ctx)
+
+
 def test_config4_full_bands_mixed_against_fp64_gradient():
     """The gradient workload at full size (16 + 1200 bands per set, all 8 k, q =
     (1/2, 0, 0), NG ~ 1200, 16 frequencies, 3 x 13 projectors): dE/dC, dE/dP and
