@@ -969,25 +969,19 @@ cudaError_t launch_adj_un(const c2<T>* Xbar, int np, int64_t Nr, const c2<T>* Uk
 // no race); the u_n terms conj(x_i) u_m[j] are summed over the block's m in
 // shared memory and written once per block as part[slice][i][j], which
 // adj_part_reduce adds to ubar_n in slice order (deterministic).
-// L > 0: the N1-point axis as (N1 / L) x L, j1 = r m + j' (r = N1 / L): warp w
-// owns the residues j' = w, w + 4, ... and all L rows of each; per residue
-// U_k = sum_{o1 = k mod L} T1[o1] exp(+2 pi i g j' / N1) (g = lo + o1), then
-// x_(r m + j') = sum_k U_k exp(+2 pi i (lo + k) m / L): r (n1 + L^2) complex
-// multiply-adds per line instead of N1 n1.
 constexpr int ADJA_WARPS = 4;
 
-template <typename T, int NI, int A, int L>
+template <typename T, int NI, int A>
 __global__ void __launch_bounds__(128) adj_stageA_fused_kernel(const c2<T>* __restrict__ T1, int mc, int n1, int N1,
-                                                               int lo, int N23, const c2<T>* __restrict__ tw,
+                                                               int N23, const c2<T>* __restrict__ tw,
                                                                const c2<T>* __restrict__ Un0,
                                                                const c2<T>* __restrict__ Un1,
                                                                const c2<T>* __restrict__ Ukp,
                                                                const int* __restrict__ Ridx, int m0,
                                                                c2<T>* __restrict__ Ubar_kp, c2<T>* __restrict__ part) {
   extern __shared__ unsigned char smem_raw[];
-  c2<T>* tws = reinterpret_cast<c2<T>*>(smem_raw);  // [N1][NI] (L > 0: rows j' < r), o1 beyond n1 zero
-  c2<T>* wls = tws + N1 * NI;                        // L > 0: [m][k] exp(+2 pi i (lo + k) m / L); 64 slots
-  c2<T>* uns = wls + 64;                             // [A][N1][32] u_n of the block's columns
+  c2<T>* tws = reinterpret_cast<c2<T>*>(smem_raw);  // [N1][NI], o1 beyond n1 zero
+  c2<T>* uns = tws + N1 * NI;                        // [A][N1][32] u_n of the block's columns
   c2<T>* accs = uns + A * N1 * 32;                   // [A][N1][32] u_n terms of the block's m
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j23 = blockIdx.x * 32 + lane;
@@ -995,15 +989,6 @@ __global__ void __launch_bounds__(128) adj_stageA_fused_kernel(const c2<T>* __re
   for (int e = threadIdx.x; e < N1 * NI; e += blockDim.x) {
     const int j1 = e / NI, o = e % NI;
     tws[e] = o < n1 ? tw[o * N1 + j1] : mk<T>(0, 0);
-  }
-  if constexpr (L > 0) {
-    const int b = pmod_a(lo, L);
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-      const int m = e / L, k = e % L;
-      double sn, cs;
-      sincospi(2.0 * (double)(((b + k) * m) % L) / (double)L, &sn, &cs);
-      wls[e] = mk<T>((T)cs, (T)sn);
-    }
   }
   for (int e = threadIdx.x; e < A * N1 * 32; e += blockDim.x) {
     const int i = e / (N1 * 32), r = e % (N1 * 32), j1 = r >> 5, l = r & 31;
@@ -1027,58 +1012,24 @@ __global__ void __launch_bounds__(128) adj_stageA_fused_kernel(const c2<T>* __re
       }
       const c2<T>* um = Ukp + (int64_t)m * Nr + j23;
       c2<T>* ubm = Ubar_kp + (int64_t)m * Nr + j23;
-      if constexpr (L == 0) {
 #pragma unroll 2
-        for (int j1 = warp; j1 < N1; j1 += ADJA_WARPS) {
-          const int64_t off = (int64_t)j1 * N23;
-          const c2<T> u = um[off];
-          c2<T> v = ubm[off];
-          const c2<T>* twj = tws + j1 * NI;
+      for (int j1 = warp; j1 < N1; j1 += ADJA_WARPS) {
+        const int64_t off = (int64_t)j1 * N23;
+        const c2<T> u = um[off];
+        c2<T> v = ubm[off];
+        const c2<T>* twj = tws + j1 * NI;
 #pragma unroll
-          for (int i = 0; i < A; ++i) {
-            c2<T> x = mk<T>(0, 0);
+        for (int i = 0; i < A; ++i) {
+          c2<T> x = mk<T>(0, 0);
 #pragma unroll
-            for (int o = 0; o < NI; ++o) cmac<T>(x, t[i][o], twj[o]);
-            cmac<T>(v, x, uns[(i * N1 + j1) * 32 + lane]);
-            c2<T>& acc = accs[(i * N1 + j1) * 32 + lane];  // row j1 belongs to this warp alone
-            const c2<T> cu = cj_mul<T>(x, u);
-            acc.x += cu.x;
-            acc.y += cu.y;
-          }
-          ubm[off] = v;
+          for (int o = 0; o < NI; ++o) cmac<T>(x, t[i][o], twj[o]);
+          cmac<T>(v, x, uns[(i * N1 + j1) * 32 + lane]);
+          c2<T>& acc = accs[(i * N1 + j1) * 32 + lane];  // row j1 belongs to this warp alone
+          const c2<T> cu = cj_mul<T>(x, u);
+          acc.x += cu.x;
+          acc.y += cu.y;
         }
-      } else {
-        const int r = N1 / L;
-        for (int jr = warp; jr < r; jr += ADJA_WARPS) {
-          const c2<T>* wrj = tws + jr * NI;
-          c2<T> U[A][L];
-#pragma unroll
-          for (int i = 0; i < A; ++i) {
-#pragma unroll
-            for (int k = 0; k < L; ++k) U[i][k] = mk<T>(0, 0);
-#pragma unroll
-            for (int o = 0; o < NI; ++o) cmac<T>(U[i][o % L], t[i][o], wrj[o]);
-          }
-#pragma unroll
-          for (int mm = 0; mm < L; ++mm) {
-            const int j1 = r * mm + jr;  // rows of this residue belong to this warp alone
-            const int64_t off = (int64_t)j1 * N23;
-            const c2<T> u = um[off];
-            c2<T> v = ubm[off];
-#pragma unroll
-            for (int i = 0; i < A; ++i) {
-              c2<T> x = mk<T>(0, 0);
-#pragma unroll
-              for (int k = 0; k < L; ++k) cmac<T>(x, U[i][k], wls[mm * L + k]);
-              cmac<T>(v, x, uns[(i * N1 + j1) * 32 + lane]);
-              c2<T>& acc = accs[(i * N1 + j1) * 32 + lane];
-              const c2<T> cu = cj_mul<T>(x, u);
-              acc.x += cu.x;
-              acc.y += cu.y;
-            }
-            ubm[off] = v;
-          }
-        }
+        ubm[off] = v;
       }
     }
   }
@@ -1112,7 +1063,7 @@ __global__ void adj_part_reduce_kernel(const c2<T>* __restrict__ part, int S, in
 template <typename T>
 size_t adj_stageA_fused_smem(int N1, int n1, int A) {
   const int ni = n1 <= 8 ? 8 : n1 <= 12 ? 12 : n1 <= 14 ? 14 : 16;
-  return sizeof(c2<T>) * ((size_t)N1 * ni + 64 + 2 * (size_t)A * N1 * 32);
+  return sizeof(c2<T>) * ((size_t)N1 * ni + 2 * (size_t)A * N1 * 32);
 }
 
 // Slices of the chunk's m per column tile: about four blocks per SM in all.
@@ -1121,46 +1072,24 @@ int adj_stageA_fused_slices(int mc, int N23) {
   return std::max(1, std::min(mc, (4 * 152 + gx - 1) / gx));
 }
 
-template <typename T, int NI, int A, int L>
-static cudaError_t adj_fused_launch_l(const c2<T>* T1, int mc, int n1, int N1, int lo, int N23, const c2<T>* tw,
-                                      const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
-                                      c2<T>* Ubar_kp, c2<T>* part, int S, size_t smem, cudaStream_t s) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(adj_stageA_fused_kernel<T, NI, A, L>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  adj_stageA_fused_kernel<T, NI, A, L><<<dim3((N23 + 31) / 32, S), 32 * ADJA_WARPS, smem, s>>>(
-      T1, mc, n1, N1, lo, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part);
-  return cudaGetLastError();
-}
-
-// the factorisation of the slowest axis the forward stages use (0: direct)
 template <typename T, int NI, int A>
-static cudaError_t adj_fused_launch(const c2<T>* T1, int mc, int n1, int N1, int lo, int N23, const c2<T>* tw,
+static cudaError_t adj_fused_launch(const c2<T>* T1, int mc, int n1, int N1, int N23, const c2<T>* tw,
                                     const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
                                     c2<T>* Ubar_kp, c2<T>* part, int S, size_t smem, cudaStream_t s) {
-  switch (factored_radix(N1, n1)) {
-#define ADJA_L(L_)                                                                                                 \
-  case L_:                                                                                                        \
-    return adj_fused_launch_l<T, NI, A, L_>(T1, mc, n1, N1, lo, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part, S, \
-                                            smem, s);
-    ADJA_L(3)
-    ADJA_L(4)
-    ADJA_L(5)
-    ADJA_L(6)
-    ADJA_L(8)
-#undef ADJA_L
-    default:
-      return adj_fused_launch_l<T, NI, A, 0>(T1, mc, n1, N1, lo, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part, S,
-                                             smem, s);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(adj_stageA_fused_kernel<T, NI, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
   }
+  adj_stageA_fused_kernel<T, NI, A><<<dim3((N23 + 31) / 32, S), 32 * ADJA_WARPS, smem, s>>>(
+      T1, mc, n1, N1, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part);
+  return cudaGetLastError();
 }
 
 // A in {1, 2}, n1 <= 16, shared memory within 200 KB (adj_stageA_fused_smem);
 // part holds S * A * N1 * N23 elements, S = adj_stageA_fused_slices(mc, N23).
 template <typename T>
-cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int N1, int lo, int N23, const c2<T>* tw,
+cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int N1, int N23, const c2<T>* tw,
                                     const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
                                     c2<T>* Ubar_kp, c2<T>* Ubar_n0, c2<T>* Ubar_n1, c2<T>* part, cudaStream_t s) {
   if (mc == 0 || N23 == 0 || N1 == 0) return cudaSuccess;
@@ -1169,10 +1098,8 @@ cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int 
   const int S = adj_stageA_fused_slices(mc, N23);
   cudaError_t e;
 #define ADJA_CASE(NI_)                                                                                          \
-  e = A == 2 ? adj_fused_launch<T, NI_, 2>(T1, mc, n1, N1, lo, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part, S,  \
-                                           smem, s)                                                                \
-             : adj_fused_launch<T, NI_, 1>(T1, mc, n1, N1, lo, N23, tw, Un0, Un0, Ukp, Ridx, m0, Ubar_kp, part, S,  \
-                                           smem, s)
+  e = A == 2 ? adj_fused_launch<T, NI_, 2>(T1, mc, n1, N1, N23, tw, Un0, Un1, Ukp, Ridx, m0, Ubar_kp, part, S, smem, s) \
+             : adj_fused_launch<T, NI_, 1>(T1, mc, n1, N1, N23, tw, Un0, Un0, Ukp, Ridx, m0, Ubar_kp, part, S, smem, s)
   if (n1 <= 8) ADJA_CASE(8);
   else if (n1 <= 12) ADJA_CASE(12);
   else if (n1 <= 14) ADJA_CASE(14);
@@ -1252,8 +1179,7 @@ cudaError_t launch_gather_box(const c2<T>* box, int nb, int npw, const int* pos,
   template cudaError_t launch_adj_stageC<T>(const c2<T>*, int, int64_t, int, int, int, int, int, const int*,          \
                                             const int*, const int*, double, c2<T>*, cudaStream_t);                     \
   template size_t adj_stageA_fused_smem<T>(int, int, int);                                                             \
-  template cudaError_t launch_adj_stageA_fused<T>(const c2<T>*, int, int, int, int, int, int, const c2<T>*,           \
-                                                  const c2<T>*,                                                      \
+  template cudaError_t launch_adj_stageA_fused<T>(const c2<T>*, int, int, int, int, int, const c2<T>*, const c2<T>*,   \
                                                   const c2<T>*, const c2<T>*, const int*, int, c2<T>*, c2<T>*, c2<T>*, \
                                                   c2<T>*, cudaStream_t);                                               \
   template cudaError_t launch_adj_stageA<T>(const c2<T>*, int, int, int, int, const c2<T>*, const c2<T>*,              \

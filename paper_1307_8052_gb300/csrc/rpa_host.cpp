@@ -66,7 +66,7 @@ template <typename T>
 size_t adj_stageA_fused_smem(int N1, int n1, int A);
 int adj_stageA_fused_slices(int mc, int N23);
 template <typename T>
-cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int N1, int lo, int N23, const c2<T>* tw,
+cudaError_t launch_adj_stageA_fused(const c2<T>* T1, int A, int mc, int n1, int N1, int N23, const c2<T>* tw,
                                     const c2<T>* Un0, const c2<T>* Un1, const c2<T>* Ukp, const int* Ridx, int m0,
                                     c2<T>* Ubar_kp, c2<T>* Ubar_n0, c2<T>* Ubar_n1, c2<T>* part, cudaStream_t s);
 template <typename T>
@@ -1127,7 +1127,7 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
                                       1.0 / (double)Nr, B.T2, c->stream));
       CUDA_OK(c, launch_pd_stageB<T>(B.T2, B.T1, np, n1, n2, N3, (const c2<T>*)p_twb, N2, c->stream));
       if (fused) {
-        CUDA_OK(c, launch_adj_stageA_fused<T>(B.T1, na, mc, n1, N1, B.glo[0], (int)N23, (const c2<T>*)p_twa, un0, un1,
+        CUDA_OK(c, launch_adj_stageA_fused<T>(B.T1, na, mc, n1, N1, (int)N23, (const c2<T>*)p_twa, un0, un1,
                                               (const c2<T>*)skp.U, skp.R_d, m0, ub_kp,
                                               ub_k + (int64_t)sk.L[B.a0 + a] * Nr,
                                               ub_k + (int64_t)sk.L[B.a0 + a + na - 1] * Nr, (c2<T>*)p_xbar,
