@@ -548,13 +548,18 @@ __global__ void __launch_bounds__(256) pd_stageA_fact_kernel(const c2<T>* __rest
 #pragma unroll
       for (int k = 0; k < L; ++k) sk[q][k] = mk<T>(0, 0);
     }
+    // rows-fastest chunks give a thread's pairs one unoccupied band: its grid
+    // is then fetched once per slice for all of them
+    bool one_m = true;
+#pragma unroll
+    for (int q = 1; q < PP; ++q) one_m = one_m && um[q] == um[0];
     auto issue = [&](int sl) {
       const int st = sl % PF;
       const int64_t j = (int64_t)((sl % L) * r + sl / L) * N23;
 #pragma unroll
       for (int q = 0; q < PP; ++q) {
         cp_async_elem<T>(my + (st * 2 * PP + 2 * q) * RING_THREADS, un[q] + j);
-        cp_async_elem<T>(my + (st * 2 * PP + 2 * q + 1) * RING_THREADS, um[q] + j);
+        if (q == 0 || !one_m) cp_async_elem<T>(my + (st * 2 * PP + 2 * q + 1) * RING_THREADS, um[q] + j);
       }
     };
 #pragma unroll
@@ -572,8 +577,9 @@ __global__ void __launch_bounds__(256) pd_stageA_fact_kernel(const c2<T>* __rest
         const int st = sl % PF;
 #pragma unroll
         for (int q = 0; q < PP; ++q) {
+          const int qm = one_m ? 0 : q;
           const c2<T> x =
-              cj_mul<T>(my[(st * 2 * PP + 2 * q) * RING_THREADS], my[(st * 2 * PP + 2 * q + 1) * RING_THREADS]);
+              cj_mul<T>(my[(st * 2 * PP + 2 * q) * RING_THREADS], my[(st * 2 * PP + 2 * qm + 1) * RING_THREADS]);
 #pragma unroll
           for (int k = 0; k < L; ++k) cmac<T>(sk[q][k], x, wl[m * L + k]);
         }
