@@ -69,9 +69,13 @@ __global__ void __launch_bounds__(256) herk_simt_kernel(const c2<T>* __restrict_
       hi[r][c][0] = hi[r][c][1] = lo[r][c][0] = lo[r][c][1] = 0.f;
     }
   int since_fold = 0;
-  for (int64_t k0 = 0; k0 < P; k0 += HK) {
+  // the next stage's elements are fetched into registers while the current
+  // stage is multiplied
+  constexpr int LQ = (HK * HT) / 256;
+  c2<T> pa[LQ], pb[LQ];
+  auto fetch = [&](int64_t k0) {
 #pragma unroll
-    for (int q = 0; q < (HK * HT) / 256; ++q) {
+    for (int q = 0; q < LQ; ++q) {
       const int e = threadIdx.x + 256 * q;
       const int kk = e / HT, cc = e % HT;
       const int64_t p = k0 + kk;
@@ -85,10 +89,24 @@ __global__ void __launch_bounds__(256) herk_simt_kernel(const c2<T>* __restrict_
         }
         if (c0 + cc < NG) b = N[p * NG + c0 + cc];
       }
-      As[kk][cc] = a;
-      Bs[kk][cc] = b;
+      pa[q] = a;
+      pb[q] = b;
+    }
+  };
+  // (FP32 only: the FP64 form is bound by the FP64 pipe and keeps its
+  // registers for two resident blocks)
+  constexpr bool PREFETCH = sizeof(T) == 4;
+  if (PREFETCH) fetch(0);
+  for (int64_t k0 = 0; k0 < P; k0 += HK) {
+    if (!PREFETCH) fetch(k0);
+#pragma unroll
+    for (int q = 0; q < LQ; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      As[e / HT][e % HT] = pa[q];
+      Bs[e / HT][e % HT] = pb[q];
     }
     __syncthreads();
+    if (PREFETCH && k0 + HK < P) fetch(k0 + HK);
 #pragma unroll
     for (int kk = 0; kk < HK; ++kk) {
       c2<T> av[4], bv[4];
