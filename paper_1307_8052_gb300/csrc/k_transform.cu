@@ -44,6 +44,23 @@ __device__ inline void fill_twiddles(c2<T>* tw, int N) {
   __syncthreads();
 }
 
+// tw[t] = exp(2 pi i t / N), t < N: the values fill_twiddles forms, once in
+// global memory for kernels with many short blocks
+template <typename T>
+__global__ void twiddle_line_kernel(c2<T>* __restrict__ tw, int N) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)N, &s, &c);
+    tw[t] = mk<T>((T)c, (T)s);
+  }
+}
+
+template <typename T>
+cudaError_t launch_twiddle_line(c2<T>* tw, int N, cudaStream_t s) {
+  twiddle_line_kernel<T><<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- generic axis DFT
 template <typename T, int TO>
 __global__ void __launch_bounds__(256) dft_axis_kernel(const c2<T>* __restrict__ in, c2<T>* __restrict__ out,
@@ -751,13 +768,19 @@ template <typename T>
 __global__ void __launch_bounds__(256) pd_stageC_kernel(const c2<T>* __restrict__ T2, int np, int n1, int n2, int N3,
                                                         const int* __restrict__ gfft, int NG, int g1lo, int g2lo,
                                                         double inv_nr, int64_t p0, int nrow, int nR,
-                                                        c2<T>* __restrict__ Nout) {
+                                                        const c2<T>* __restrict__ twg, c2<T>* __restrict__ Nout) {
   // Each thread handles one G and PG consecutive pairs (the fastest-axis DFT
   // of each pair; PG independent loads per step).
   constexpr int PG = 4;
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
-  fill_twiddles<T>(tw, N3);
+  if (twg) {
+    // the table of twiddle_line_kernel (the same values fill_twiddles forms)
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) tw[t] = twg[t];
+    __syncthreads();
+  } else {
+    fill_twiddles<T>(tw, N3);
+  }
   const int ngrp = (np + PG - 1) / PG;
   const int64_t total = (int64_t)ngrp * NG;
   const T scale = (T)inv_nr;
@@ -1019,12 +1042,13 @@ cudaError_t launch_paw_gemm(const c2<T>* R, const c2<T>* Pm, int KP, int nL, int
 
 template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft, int NG, int g1lo,
-                             int g2lo, double inv_nr, int64_t p0, int nrow, int nR, c2<T>* Nout, cudaStream_t s) {
+                             int g2lo, double inv_nr, int64_t p0, int nrow, int nR, const c2<T>* tw3, c2<T>* Nout,
+                             cudaStream_t s) {
   const int64_t total = (int64_t)((np + 3) / 4) * NG;
   if (total == 0) return cudaSuccess;
   if (nrow < 1 || np % nrow) return cudaErrorInvalidValue;
   pd_stageC_kernel<T><<<grid_for(total, 256), 256, N3 * sizeof(c2<T>), s>>>(T2, np, n1, n2, N3, gfft, NG, g1lo, g2lo,
-                                                                          inv_nr, p0, nrow, nR, Nout);
+                                                                          inv_nr, p0, nrow, nR, tw3, Nout);
   return cudaGetLastError();
 }
 
@@ -1136,7 +1160,8 @@ cudaError_t launch_pair_params(const double* ek, const double* fk, const double*
                                              const int*, int, int, int, int, double, int64_t, c2<T>*, cudaStream_t); \
   template int pd_stageBC_slab<T>(int, int, int, int);                                                            \
   template cudaError_t launch_pd_stageC<T>(const c2<T>*, int, int, int, int, const int*, int, int, int, double,    \
-                                           int64_t, int, int, c2<T>*, cudaStream_t);                             \
+                                           int64_t, int, int, const c2<T>*, c2<T>*, cudaStream_t);              \
+  template cudaError_t launch_twiddle_line<T>(c2<T>*, int, cudaStream_t);                                       \
   template cudaError_t launch_paw_gemm<T>(const c2<T>*, const c2<T>*, int, int, int, int, c2<T>*, cudaStream_t); \
   template cudaError_t launch_paw_R<T>(const double2*, int, const int*, int, const double2*, const int*,          \
                                        const int*, const int*, const int64_t*, const int*, int, c2<T>*,          \

@@ -653,6 +653,9 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
       if ((st = workspace(c, "twfB", sizeof(c2<T>) * (size_t)(LB * LB + (N2 / LB) * 16), &p_tfB)) != RPA_OK) return st;
       CUDA_OK(c, launch_twiddle_factored<T>((c2<T>*)p_tfB, N2, LB, glo[1], n2, c->stream));
     }
+    void* p_tw3;
+    if ((st = workspace(c, "tw3", sizeof(c2<T>) * (size_t)N3, &p_tw3)) != RPA_OK) return st;
+    CUDA_OK(c, launch_twiddle_line<T>((c2<T>*)p_tw3, N3, c->stream));
     void* p_g1s = nullptr;
     if (OB > 0) {
       if ((st = workspace(c, "pd_g1start", sizeof(int) * (size_t)(n1 + 1), &p_g1s)) != RPA_OK) return st;
@@ -689,7 +692,8 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
         CUDA_OK(c, launch_pd_stageB<T>((const c2<T>*)p_T1, (c2<T>*)p_T2, np, n1, N2, N3, (const c2<T>*)p_twB, n2,
                                        c->stream));
       CUDA_OK(c, launch_pd_stageC<T>((const c2<T>*)p_T2, np, n1, n2, N3, (const int*)p_gfft, NG, glo[0], glo[1],
-                                     1.0 / (double)Nr, p0, nrow, nR, (c2<T>*)p_N, c->stream));
+                                     1.0 / (double)Nr, p0, nrow, nR, (const c2<T>*)p_tw3, (c2<T>*)p_N,
+                                     c->stream));
       tm.add_launches(3);
     }
     if (paw) {

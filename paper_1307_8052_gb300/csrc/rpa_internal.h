@@ -80,8 +80,12 @@ cudaError_t launch_pd_stageB(const c2<T>* T1, c2<T>* T2, int np, int n1, int N2,
 // points g = G + G0, 1/Nr normalisation, write N[p][NG].
 template <typename T>
 cudaError_t launch_pd_stageC(const c2<T>* T2, int np, int n1, int n2, int N3, const int* gfft,
-                             int NG, int g1lo, int g2lo, double inv_nr, int64_t p0, int nrow, int nR, c2<T>* Nout,
-                             cudaStream_t s);
+                             int NG, int g1lo, int g2lo, double inv_nr, int64_t p0, int nrow, int nR,
+                             const c2<T>* tw3, c2<T>* Nout, cudaStream_t s);
+// tw[t] = exp(2 pi i t / N), t < N (FP64-accurate), for stage C's tw3 (or null:
+// every block forms its own).
+template <typename T>
+cudaError_t launch_twiddle_line(c2<T>* tw, int N, cudaStream_t s);
 
 // Pair densities, stages B and C fused per (pair, slab of OB first-axis
 // outputs): the middle-axis DFT into shared memory, then the fastest axis on
