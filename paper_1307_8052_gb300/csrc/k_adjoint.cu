@@ -844,14 +844,19 @@ __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict
                                                          int mc, int nR, int ncol, int N3,
                                                          const int* __restrict__ col_start,
                                                          const int* __restrict__ col_g, const int* __restrict__ col_g3,
-                                                         double inv_nr, int tab, c2<T>* __restrict__ T2) {
+                                                         double inv_nr, int tab, const c2<T>* __restrict__ twg,
+                                                         c2<T>* __restrict__ T2) {
   extern __shared__ unsigned char smem_raw[];
   c2<T>* tw1 = reinterpret_cast<c2<T>*>(smem_raw);  // exp(2 pi i t / N3), t < N3
   c2<T>* tw = tab ? tw1 + N3 : tw1;                   // tab: [g3 mod N3][j3]
   for (int e = threadIdx.x; e < N3; e += blockDim.x) {
-    double sn, cs;
-    sincospi(2.0 * (double)e / (double)N3, &sn, &cs);
-    tw1[e] = mk<T>((T)cs, (T)sn);
+    if (twg) {
+      tw1[e] = twg[e];  // the same values, formed once per block of pairs
+    } else {
+      double sn, cs;
+      sincospi(2.0 * (double)e / (double)N3, &sn, &cs);
+      tw1[e] = mk<T>((T)cs, (T)sn);
+    }
   }
   __syncthreads();
   if (tab) {
@@ -881,8 +886,8 @@ __global__ void __launch_bounds__(256) adj_stageC_kernel(const c2<T>* __restrict
 
 template <typename T>
 cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int mc, int nR, int ncol, int N3,
-                              const int* col_start, const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2,
-                              cudaStream_t s) {
+                              const int* col_start, const int* col_g, const int* col_g3, double inv_nr,
+                              const c2<T>* tw3, c2<T>* T2, cudaStream_t s) {
   const int64_t total = (int64_t)np * ncol * N3;
   if (total == 0) return cudaSuccess;
   if (mc < 1 || np % mc) return cudaErrorInvalidValue;
@@ -891,7 +896,7 @@ cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int
   // a grid of eight blocks per SM amortises the table over many outputs
   const int grid = std::min(gridx(total), 152 * 8);
   adj_stageC_kernel<T><<<grid, 256, smem, s>>>(Nbar, NG, p0, np, mc, nR, ncol, N3, col_start, col_g, col_g3, inv_nr,
-                                               tab, T2);
+                                               tab, tw3, T2);
   return cudaGetLastError();
 }
 
@@ -1177,7 +1182,7 @@ cudaError_t launch_gather_box(const c2<T>* box, int nb, int npw, const int* pos,
                                              const int*, const int*, const int*, c2<T>*, double2*, double2*, double2*, \
                                              cudaStream_t);                                                            \
   template cudaError_t launch_adj_stageC<T>(const c2<T>*, int, int64_t, int, int, int, int, int, const int*,          \
-                                            const int*, const int*, double, c2<T>*, cudaStream_t);                     \
+                                            const int*, const int*, double, const c2<T>*, c2<T>*, cudaStream_t);       \
   template size_t adj_stageA_fused_smem<T>(int, int, int);                                                             \
   template cudaError_t launch_adj_stageA_fused<T>(const c2<T>*, int, int, int, int, int, const c2<T>*, const c2<T>*,   \
                                                   const c2<T>*, const c2<T>*, const int*, int, c2<T>*, c2<T>*, c2<T>*, \

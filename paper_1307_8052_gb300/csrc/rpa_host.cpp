@@ -60,8 +60,8 @@ cudaError_t launch_paw_adjoint(const c2<T>* Nbar, const c2<T>* R, const c2<T>* P
                                double2* part, double2* gPk, double2* gPkp, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_stageC(const c2<T>* Nbar, int NG, int64_t p0, int np, int mc, int nR, int ncol, int N3,
-                              const int* col_start, const int* col_g, const int* col_g3, double inv_nr, c2<T>* T2,
-                              cudaStream_t s);
+                              const int* col_start, const int* col_g, const int* col_g3, double inv_nr,
+                              const c2<T>* tw3, c2<T>* T2, cudaStream_t s);
 template <typename T>
 size_t adj_stageA_fused_smem(int N1, int n1, int A);
 int adj_stageA_fused_slices(int mc, int N23);
@@ -493,6 +493,7 @@ struct Block {
   c2<T>* Pm = nullptr;               // [nR][KP]
   c2<T>* T1 = nullptr;               // transform scratch
   c2<T>* T2 = nullptr;
+  const c2<T>* tw3 = nullptr;         // [N3] exp(2 pi i t / N3) of the transform grid
   const int64_t* q_off = nullptr;    // PAW metadata (device)
   const int* atom_of = nullptr;
   const int* idx_in = nullptr;
@@ -628,7 +629,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
   PC = std::min<int64_t>(PC, P);
   if ((st = workspace(c, "pd_T1", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * N23), &p_T1)) != RPA_OK) return st;
   if ((st = workspace(c, "pd_T2", sizeof(c2<T>) * (size_t)(PC * (int64_t)n1 * n2 * N3), &p_T2)) != RPA_OK) return st;
-  void *p_twA, *p_twB;
+  void *p_twA, *p_twB, *p_tw3 = nullptr;
   const size_t twA_n = (size_t)((n1 + 15) / 16) * N1 * 16, twB_n = (size_t)((n2 + 15) / 16) * N2 * 16;
   if ((st = workspace(c, "twA", sizeof(c2<T>) * twA_n, &p_twA)) != RPA_OK) return st;
   if ((st = workspace(c, "twB", sizeof(c2<T>) * twB_n, &p_twB)) != RPA_OK) return st;
@@ -653,7 +654,6 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
       if ((st = workspace(c, "twfB", sizeof(c2<T>) * (size_t)(LB * LB + (N2 / LB) * 16), &p_tfB)) != RPA_OK) return st;
       CUDA_OK(c, launch_twiddle_factored<T>((c2<T>*)p_tfB, N2, LB, glo[1], n2, c->stream));
     }
-    void* p_tw3;
     if ((st = workspace(c, "tw3", sizeof(c2<T>) * (size_t)N3, &p_tw3)) != RPA_OK) return st;
     CUDA_OK(c, launch_twiddle_line<T>((c2<T>*)p_tw3, N3, c->stream));
     void* p_g1s = nullptr;
@@ -740,6 +740,7 @@ rpa_status pairs_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const double* 
   B.KP = KP;
   B.T1 = (c2<T>*)p_T1;
   B.T2 = (c2<T>*)p_T2;
+  B.tw3 = (const c2<T>*)p_tw3;
   B.PC = PC;
   return RPA_OK;
 }
@@ -1128,7 +1129,7 @@ rpa_status backward_block(rpa_ctx* c, QPt& Q, int t, int a0, int a1, const doubl
       const int np = na * mc;
       const int64_t p0 = (int64_t)a * nR + m0;
       CUDA_OK(c, launch_adj_stageC<T>(Nbar, NG, p0, np, mc, nR, ncol, N3, col_start, col_g, col_g3,
-                                      1.0 / (double)Nr, B.T2, c->stream));
+                                      1.0 / (double)Nr, B.tw3, B.T2, c->stream));
       CUDA_OK(c, launch_pd_stageB<T>(B.T2, B.T1, np, n1, n2, N3, (const c2<T>*)p_twb, N2, c->stream));
       if (fused) {
         CUDA_OK(c, launch_adj_stageA_fused<T>(B.T1, na, mc, n1, N1, (int)N23, (const c2<T>*)p_twa, un0, un1,
