@@ -154,10 +154,27 @@ rpa_status rpa_set_qpoint(rpa_ctx* ctx, int32_t iq, const double q_red[3],
                           int32_t nk, const int32_t* k_of, const int32_t* kq_of,
                           const int32_t* G0, int32_t* ng_out);
 
-/* Number of G vectors of q-point iq and (if miller_out != NULL) their Miller
- * indices miller_out[ng][3] in the library's order.  Host pointers. */
+/* The response sphere of q-point iq: the reciprocal lattice vectors G that
+ * index chi0_GG'(q) and v_G(q), |q+G|^2/2 <= E_cut (Sec. 2.1; Table 1 step 6
+ * gathers the pair densities onto them).  *ng receives NG and, if
+ * miller_out != NULL, miller_out[ng][3] their Miller indices in the order
+ * chi0, epsilon^-1 and the Q^a_ij input use (Miller-lexicographic, first
+ * index slowest).  Host pointers.  RPA_ERR_STATE if q-point iq is not set. */
 rpa_status rpa_gvectors(const rpa_ctx* ctx, int32_t iq, int32_t* ng,
                         int32_t* miller_out);
+
+/* The same sphere without a context or a GPU (host arithmetic only): for the
+ * lattice rows cell[9] (bohr), q_red[3] (reduced) and ecut_chi (Ha), *ng
+ * receives NG, miller_out[ng][3] (nullable) the Miller indices in the order
+ * rpa_set_qpoint builds for the same cell, q and cutoff, and v_out[ng]
+ * (nullable) the Coulomb kernel v_G = 4 pi / |q+G|^2 of Sec. 2.2, 0 where
+ * q + G = 0.  Call with cap = 0 and NULL outputs to size them; a non-NULL
+ * output with cap < NG is RPA_ERR_ARG (*ng is still set).  NG = 0 is a valid
+ * answer.  RPA_ERR_ARG for NULL cell/q_red/ng, a singular cell, non-finite q,
+ * ecut_chi <= 0 or a Miller search box over 2^28 points. */
+rpa_status rpa_response_sphere(const double cell[9], const double q_red[3],
+                               double ecut_chi, int32_t cap, int32_t* ng,
+                               int32_t* miller_out, double* v_out);
 
 /* PAW augmentation functions of q-point iq (Eq. 6, Q^a_ij(q+G)):
  * atom after atom a block Q[ni][ni][NG] (complex), G in rpa_gvectors order.

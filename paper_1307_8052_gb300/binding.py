@@ -36,6 +36,7 @@ SIGNATURES = {
     "rpa_set_paw": (_I, [_P, _I, _I, _P, _P]),
     "rpa_set_qpoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P]),
     "rpa_gvectors": (_I, [_P, _I, _P, _P]),
+    "rpa_response_sphere": (_I, [_P, _P, _D, _I, _P, _P, _P]),
     "rpa_set_paw_Q": (_I, [_P, _I, _I, _P, _P]),
     "rpa_set_optical": (_I, [_P, _I, _P, _I, _P, _P]),
     "rpa_set_orbitals_sym": (_I, [_P, _I, _I, _P, _P, _I, _I, _P, _P]),
@@ -182,6 +183,21 @@ def rpa_gvectors(ctx, iq) -> np.ndarray:
     out = np.zeros((ng.value, 3), dtype=np.int32)
     _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), out.ctypes.data_as(_P)))
     return out
+
+
+def rpa_response_sphere(cell, q_red, ecut_chi):
+    """Miller indices (NG, 3) int32 and Coulomb kernel (NG,) of the response
+    sphere, computed by the library on the host (no context, no GPU)."""
+    keep = []
+    pc = _ptr(np.asarray(cell, dtype=np.float64).reshape(9), np.float64, keep)
+    pq = _ptr(np.asarray(q_red, dtype=np.float64).reshape(3), np.float64, keep)
+    ng = ct.c_int32()
+    _check(None, lib().rpa_response_sphere(pc, pq, float(ecut_chi), 0, ct.byref(ng), None, None))
+    gm = np.zeros((ng.value, 3), dtype=np.int32)
+    v = np.zeros(ng.value)
+    _check(None, lib().rpa_response_sphere(pc, pq, float(ecut_chi), ng.value, ct.byref(ng),
+                                           gm.ctypes.data_as(_P), v.ctypes.data_as(_P)))
+    return gm, v
 
 
 def rpa_set_paw_Q(ctx, iq, nproj, Q):

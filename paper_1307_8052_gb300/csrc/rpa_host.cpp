@@ -91,6 +91,9 @@ constexpr int kMaxIndex = 4096;
 // twiddle matrices of the pruned transforms (grid axis x 16 outputs, complex
 // double) must fit in shared memory
 constexpr int kMaxGrid = 768;
+// Miller box searched for a response sphere (a cutoff far beyond any grid the
+// transforms accept is an argument error, not an hours-long host loop)
+constexpr double kMaxSphereBox = 1u << 28;
 
 struct DevBuf {
   void* p = nullptr;
@@ -296,6 +299,56 @@ void inv3(const double* m, double* out) {
   out[2] = (b * f - cc * e) / det;
   out[5] = -(a * f - cc * d) / det;
   out[8] = (a * e - b * d) / det;
+}
+
+double det3(const double* a) {
+  return a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+}
+
+// B = 2 pi inv(cell)^T: row i of B is column i of inv(cell), a_i . b_j = 2 pi delta_ij
+void reciprocal_basis(const double* cell, double* B) {
+  double inv[9];
+  inv3(cell, inv);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
+}
+
+// Response sphere of Sec. 2.1, {G : |q+G|^2/2 <= ecut}, in Miller-lexicographic
+// order (first index slowest), and the Coulomb kernel v_G = 4 pi / |q+G|^2
+// (0 where q + G = 0).  The Miller box is bounded by |q+G| <= sqrt(2 ecut)
+// through the column norms of inv(B), plus a margin of 2 for q.  False if
+// that box exceeds kMaxSphereBox points (or ecut is not finite).
+bool response_sphere(const double* B, const double* q, double ecut, std::vector<int>& gm, std::vector<double>& v) {
+  gm.clear();
+  v.clear();
+  const double rmax = std::sqrt(2.0 * ecut);
+  double Binv[9];
+  inv3(B, Binv);
+  int ext[3];
+  double box = 1.0;
+  for (int i = 0; i < 3; ++i) {
+    const double colnorm = std::sqrt(Binv[i] * Binv[i] + Binv[3 + i] * Binv[3 + i] + Binv[6 + i] * Binv[6 + i]);
+    const double e = std::ceil(rmax * colnorm) + 2.0;
+    if (!(e <= kMaxSphereBox)) return false;
+    ext[i] = (int)e;
+    box *= 2.0 * e + 1.0;
+  }
+  if (box > kMaxSphereBox) return false;
+  for (int g1 = -ext[0]; g1 <= ext[0]; ++g1)
+    for (int g2 = -ext[1]; g2 <= ext[1]; ++g2)
+      for (int g3 = -ext[2]; g3 <= ext[2]; ++g3) {
+        const double r[3] = {g1 + q[0], g2 + q[1], g3 + q[2]};
+        double w[3];
+        for (int cc = 0; cc < 3; ++cc) w[cc] = r[0] * B[cc] + r[1] * B[3 + cc] + r[2] * B[6 + cc];
+        const double k2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        if (0.5 * k2 <= ecut) {
+          gm.push_back(g1);
+          gm.push_back(g2);
+          gm.push_back(g3);
+          v.push_back((r[0] == 0.0 && r[1] == 0.0 && r[2] == 0.0) ? 0.0 : 4.0 * M_PI / k2);
+        }
+      }
+  return true;
 }
 
 // ---- profiling helpers (CUDA events on the context stream)
@@ -1349,9 +1402,7 @@ rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
     if (p->grid[i] < 2 || p->grid[i] > kMaxGrid) return RPA_ERR_ARG;
   if (!(p->ecut_chi > 0.0) || !(p->spin_factor > 0.0) || p->nk_bz < 1) return RPA_ERR_ARG;
   if (p->precision < RPA_FP64 || p->precision > RPA_BF16X3) return RPA_ERR_ARG;
-  const double* a = p->cell;
-  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
-                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  const double det = det3(p->cell);
   if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return RPA_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {
@@ -1362,11 +1413,7 @@ rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
   rpa_ctx* c = new rpa_ctx();
   c->prm = *p;
   c->volume = std::fabs(det);
-  double inv[9];
-  inv3(p->cell, inv);
-  // B = 2 pi inv(cell)^T : row i of B is column i of inv(cell)
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) c->B[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
+  reciprocal_basis(p->cell, c->B);
   if (p->stream) {
     c->stream = (cudaStream_t)p->stream;
   } else {
@@ -1767,30 +1814,9 @@ rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t
         return fail(c, RPA_ERR_STATE, "transition %d references orbital set %d that is not set", t, idx);
     }
   }
-  // response sphere {G : |q+G|^2/2 <= ecut}, lexicographic (first index slowest)
-  const double* B = c->B;
-  const double rmax = std::sqrt(2.0 * c->prm.ecut_chi);
-  double Binv[9];
-  inv3(B, Binv);
-  int ext[3];
-  for (int i = 0; i < 3; ++i) {
-    const double colnorm = std::sqrt(Binv[i] * Binv[i] + Binv[3 + i] * Binv[3 + i] + Binv[6 + i] * Binv[6 + i]);
-    ext[i] = (int)std::ceil(rmax * colnorm) + 2;
-  }
-  for (int g1 = -ext[0]; g1 <= ext[0]; ++g1)
-    for (int g2 = -ext[1]; g2 <= ext[1]; ++g2)
-      for (int g3 = -ext[2]; g3 <= ext[2]; ++g3) {
-        const double r[3] = {g1 + Q.q[0], g2 + Q.q[1], g3 + Q.q[2]};
-        double v[3];
-        for (int cc = 0; cc < 3; ++cc) v[cc] = r[0] * B[cc] + r[1] * B[3 + cc] + r[2] * B[6 + cc];
-        const double k2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        if (0.5 * k2 <= c->prm.ecut_chi) {
-          Q.gm.push_back(g1);
-          Q.gm.push_back(g2);
-          Q.gm.push_back(g3);
-          Q.v.push_back((r[0] == 0.0 && r[1] == 0.0 && r[2] == 0.0) ? 0.0 : 4.0 * M_PI / k2);
-        }
-      }
+  if (!response_sphere(c->B, Q.q, c->prm.ecut_chi, Q.gm, Q.v))
+    return fail(c, RPA_ERR_ARG, "response sphere: Miller box over %.0f points (ecut_chi %g)", kMaxSphereBox,
+                c->prm.ecut_chi);
   Q.NG = (int)Q.v.size();
   if (Q.NG == 0) return fail(c, RPA_ERR_ARG, "empty response sphere");
   // the Fourier route (Eq. 10) equals the plane-wave sum only without aliasing:
@@ -1846,6 +1872,25 @@ rpa_status rpa_gvectors(const rpa_ctx* c, int32_t iq, int32_t* ng, int32_t* mill
   if (it == c->qpts.end() || !it->second.valid) return RPA_ERR_STATE;
   *ng = it->second.NG;
   if (miller_out) memcpy(miller_out, it->second.gm.data(), sizeof(int32_t) * it->second.gm.size());
+  return RPA_OK;
+}
+
+rpa_status rpa_response_sphere(const double cell[9], const double q_red[3], double ecut_chi, int32_t cap, int32_t* ng,
+                               int32_t* miller_out, double* v_out) {
+  if (!cell || !q_red || !ng || cap < 0 || !(ecut_chi > 0.0)) return RPA_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(q_red[d])) return RPA_ERR_ARG;
+  const double det = det3(cell);
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return RPA_ERR_ARG;
+  double B[9];
+  reciprocal_basis(cell, B);
+  std::vector<int> gm;
+  std::vector<double> v;
+  if (!response_sphere(B, q_red, ecut_chi, gm, v)) return RPA_ERR_ARG;
+  *ng = (int32_t)v.size();
+  if ((miller_out || v_out) && cap < *ng) return RPA_ERR_ARG;
+  if (miller_out && !gm.empty()) memcpy(miller_out, gm.data(), sizeof(int32_t) * gm.size());
+  if (v_out && !v.empty()) memcpy(v_out, v.data(), sizeof(double) * v.size());
   return RPA_OK;
 }
 

@@ -313,6 +313,20 @@ def test_minimal_transform_grid_equals_caller_grid():
     assert _rel(a, o.chi0(p, 1, om, _oracle_Q(p, 1))) < TOL["fp64"]["chi"]
 
 
+def test_qpoint_sphere_is_the_host_sphere():
+    """rpa_set_qpoint's G list, read back through rpa_gvectors, is the sphere
+    rpa_response_sphere plans without a context (tested on the CPU against the
+    oracle), at every q-point of a mesh with umklapp."""
+    p = syn.small_problem(config_tag=95)
+    ctx = _ctx(p, "fp64", with_paw=False)
+    try:
+        for iq, qp in enumerate(p.qpoints):
+            gm, _ = b.rpa_response_sphere(p.cell, qp.q_red, p.ecut_chi)
+            assert np.array_equal(b.rpa_gvectors(ctx, iq), gm)
+    finally:
+        b.rpa_destroy(ctx)
+
+
 def test_not_hpd_is_reported_not_trapped():
     """Mirrored band energies (occupied above empty by the same gaps) flip the sign
     of chi0, so 1 - v^1/2 chi0 v^1/2 has eigenvalues below zero: the Cholesky
