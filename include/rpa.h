@@ -27,11 +27,15 @@
  *     r = sum_i (j_i / N_i) a_i.
  *   - Orbital coefficients follow Eq. 8: psi_nk(r) = Omega^-1/2 sum_Q C_nk(Q)
  *     exp(i (k+Q).r) with sum_Q |C_nk(Q)|^2 = 1.
- *   - Input pointers may be host or device (CUDA) memory; the library copies
- *     what it keeps and never retains a caller pointer after a call returns.
- *     Output pointers may be host or device memory; device outputs are written
- *     in order on the context's stream, host outputs are complete when the
- *     call returns.
+ *   - Bulk arrays documented "host or device" (C, P, Q, D, chi0 and
+ *     gradient outputs) may be host, managed or CUDA device memory; the
+ *     library copies what it keeps and never retains a caller pointer after a
+ *     call returns.  Device outputs are written in order on the context's
+ *     stream, host outputs are complete when the call returns.  Every other
+ *     pointer (index lists, frequencies, weights, small parameter arrays,
+ *     scalar outputs) is read or written by the host: pageable, pinned or
+ *     managed memory; CUDA device memory there is RPA_ERR_ARG.
+ *     rpa_logdet_noalloc, which takes device memory, states its own rule.
  *   - Every call returns an rpa_status; rpa_last_error() gives a message.
  *     No call aborts the process or traps on the device.  A context is not
  *     thread-safe: use one context per host thread.

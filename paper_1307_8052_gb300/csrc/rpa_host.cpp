@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <vector>
@@ -278,6 +279,33 @@ bool is_device_ptr(const void* p) {
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+// Arguments the host reads or writes itself (index lists, frequencies,
+// weights, small parameter arrays, scalar outputs) must be host-readable:
+// device memory there is an argument error, not a crash of the process.
+// Pageable, pinned and managed memory qualify; NULL is left to each call's
+// own null checks.
+bool host_readable(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type != cudaMemoryTypeDevice;
+}
+
+rpa_status host_args(rpa_ctx* c, std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (!host_readable(p)) return fail(c, RPA_ERR_ARG, "an argument the host reads or writes is device memory");
+  return RPA_OK;
+}
+
+#define HOST_ARGS(c, ...)                                  \
+  do {                                                     \
+    const rpa_status hs_ = host_args((c), {__VA_ARGS__});  \
+    if (hs_ != RPA_OK) return hs_;                         \
+  } while (0)
 
 rpa_status copy_in(rpa_ctx* c, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return RPA_OK;
@@ -1396,7 +1424,7 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
 extern "C" {
 
 rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
-  if (!p || !out) return RPA_ERR_ARG;
+  if (!p || !out || !host_readable(p) || !host_readable(out)) return RPA_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < 3; ++i)
     if (p->grid[i] < 2 || p->grid[i] > kMaxGrid) return RPA_ERR_ARG;
@@ -1532,6 +1560,7 @@ rpa_status rpa_set_orbitals(rpa_ctx* c, int32_t kidx, const double k_red[3], int
   if (nbands < 1 || npw < 1 || nbands > (1 << 20) || npw > (1 << 24))
     return fail(c, RPA_ERR_ARG, "bad sizes nbands=%d npw=%d", nbands, npw);
   if (!k_red || !miller || !C || !eps || !f) return fail(c, RPA_ERR_ARG, "null pointer argument");
+  HOST_ARGS(c, k_red, miller, eps, f);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   OrbSet s;
   s.valid = true;
@@ -1660,6 +1689,7 @@ rpa_status rpa_set_orbitals_sym(rpa_ctx* c, int32_t kidx, int32_t src, const int
   auto it = c->sets.find(src);
   if (it == c->sets.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "orbital set %d not set", src);
   if (!M) return fail(c, RPA_ERR_ARG, "null rotation");
+  HOST_ARGS(c, M, tau, atom_map);
   // M acts on reduced reciprocal coordinates; it must be unimodular and keep
   // lengths: M^T G M = G with the metric G = B B^T of the reciprocal rows
   const int64_t det = (int64_t)M[0] * (M[4] * M[8] - M[5] * M[7]) - (int64_t)M[1] * (M[3] * M[8] - M[5] * M[6]) +
@@ -1775,6 +1805,7 @@ rpa_status rpa_set_paw(rpa_ctx* c, int32_t kidx, int32_t natoms, const int32_t* 
   auto it = c->sets.find(kidx);
   if (it == c->sets.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "orbital set %d not set", kidx);
   if (natoms < 1 || natoms > 100000 || !nproj || !P) return fail(c, RPA_ERR_ARG, "bad PAW arguments");
+  HOST_ARGS(c, nproj);
   int KP = 0;
   for (int a = 0; a < natoms; ++a) {
     if (nproj[a] < 1 || nproj[a] > 64) return fail(c, RPA_ERR_ARG, "nproj[%d] = %d outside [1,64]", a, nproj[a]);
@@ -1800,6 +1831,7 @@ rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t
   if (!c) return RPA_ERR_ARG;
   if (iq < 0 || iq >= kMaxIndex) return fail(c, RPA_ERR_ARG, "iq %d out of range", iq);
   if (!q_red || nk < 1 || nk > kMaxIndex || !k_of || !kq_of || !G0) return fail(c, RPA_ERR_ARG, "bad q-point arguments");
+  HOST_ARGS(c, q_red, k_of, kq_of, G0, ng_out);
   QPt Q;
   Q.valid = true;
   for (int d = 0; d < 3; ++d) Q.q[d] = q_red[d];
@@ -1867,7 +1899,7 @@ rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t
 }
 
 rpa_status rpa_gvectors(const rpa_ctx* c, int32_t iq, int32_t* ng, int32_t* miller_out) {
-  if (!c || !ng) return RPA_ERR_ARG;
+  if (!c || !ng || !host_readable(ng) || !host_readable(miller_out)) return RPA_ERR_ARG;
   auto it = c->qpts.find(iq);
   if (it == c->qpts.end() || !it->second.valid) return RPA_ERR_STATE;
   *ng = it->second.NG;
@@ -1897,6 +1929,7 @@ rpa_status rpa_response_sphere(const double cell[9], const double q_red[3], doub
 rpa_status rpa_set_optical(rpa_ctx* c, int32_t iq, const double* qdir, int32_t natoms, const int32_t* nproj,
                            const double* Qg) {
   if (!c) return RPA_ERR_ARG;
+  HOST_ARGS(c, qdir, nproj, Qg);
   auto it = c->qpts.find(iq);
   if (it == c->qpts.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "q-point %d not set", iq);
   QPt& Q = it->second;
@@ -1971,6 +2004,7 @@ rpa_status rpa_set_paw_Q(rpa_ctx* c, int32_t iq, int32_t natoms, const int32_t* 
   auto it = c->qpts.find(iq);
   if (it == c->qpts.end() || !it->second.valid) return fail(c, RPA_ERR_STATE, "q-point %d not set", iq);
   if (natoms < 1 || natoms > 100000 || !nproj || !Qv) return fail(c, RPA_ERR_ARG, "bad PAW Q arguments");
+  HOST_ARGS(c, nproj);
   QPt& Q = it->second;
   int64_t tot = 0;
   for (int a = 0; a < natoms; ++a) {
@@ -2032,6 +2066,7 @@ rpa_status rpa_set_paw_Q(rpa_ctx* c, int32_t iq, int32_t natoms, const int32_t* 
 rpa_status rpa_epsilon_inv(rpa_ctx* c, int32_t iq, int32_t nw, const double* omega, double* out) {
   if (!c) return RPA_ERR_ARG;
   if (nw < 1 || nw > 4096 || !omega || !out) return fail(c, RPA_ERR_ARG, "bad rpa_epsilon_inv arguments");
+  HOST_ARGS(c, omega);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   prof_begin(c);
   ++c->stamp;
@@ -2077,6 +2112,7 @@ rpa_status rpa_epsilon_inv(rpa_ctx* c, int32_t iq, int32_t nw, const double* ome
 rpa_status rpa_chi0(rpa_ctx* c, int32_t iq, int32_t nw, const double* omega, double* chi_out) {
   if (!c) return RPA_ERR_ARG;
   if (nw < 1 || nw > 4096 || !omega || !chi_out) return fail(c, RPA_ERR_ARG, "bad rpa_chi0 arguments");
+  HOST_ARGS(c, omega);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   prof_begin(c);
   ++c->stamp;
@@ -2105,6 +2141,7 @@ rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* 
   if (!c) return RPA_ERR_ARG;
   if (nq < 1 || nq > kMaxIndex || !iqs || !wq || nw < 1 || nw > 4096 || !omega || !W || !Ec)
     return fail(c, RPA_ERR_ARG, "bad rpa_energy arguments");
+  HOST_ARGS(c, iqs, wq, omega, W, Ec, terms);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   prof_begin(c);
   ++c->stamp;
@@ -2126,6 +2163,7 @@ rpa_status rpa_energy(rpa_ctx* c, int32_t nq, const int32_t* iqs, const double* 
 rpa_status rpa_set_frequencies(rpa_ctx* c, int32_t nw, const double* omega) {
   if (!c) return RPA_ERR_ARG;
   if (nw < 1 || nw > 4096 || !omega) return fail(c, RPA_ERR_ARG, "bad frequency arguments");
+  HOST_ARGS(c, omega);
   for (int j = 0; j < nw; ++j)
     if (!std::isfinite(omega[j])) return fail(c, RPA_ERR_ARG, "omega[%d] not finite", j);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
@@ -2143,6 +2181,7 @@ rpa_status rpa_set_frequencies(rpa_ctx* c, int32_t nw, const double* omega) {
 rpa_status rpa_energy_enqueue(rpa_ctx* c, int32_t nq, const int32_t* iqs) {
   if (!c) return RPA_ERR_ARG;
   if (nq < 1 || nq > kMaxIndex || !iqs) return fail(c, RPA_ERR_ARG, "bad rpa_energy_enqueue arguments");
+  HOST_ARGS(c, iqs);
   if (!c->omega_d) return fail(c, RPA_ERR_STATE, "rpa_set_frequencies has not been called");
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   ++c->stamp;
@@ -2417,6 +2456,7 @@ rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int3
 
 rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq, const int32_t* iqs, rpa_graph** out) {
   if (!ctxs || n < 1 || !nq || !iqs || !out) return RPA_ERR_ARG;
+  if (!host_readable(ctxs) || !host_readable(nq) || !host_readable(iqs) || !host_readable(out)) return RPA_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || nq[i] < 1) return RPA_ERR_ARG;
@@ -2538,6 +2578,7 @@ void rpa_graph_destroy(rpa_graph* g) {
 rpa_status rpa_energy_collect(rpa_ctx* c, const double* wq, const double* W, double* Ec, double* terms) {
   if (!c) return RPA_ERR_ARG;
   if (!wq || !W || !Ec) return fail(c, RPA_ERR_ARG, "bad rpa_energy_collect arguments");
+  HOST_ARGS(c, wq, W, Ec, terms);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   return energy_collect(c, c->nw_set, wq, W, Ec, terms);
 }
@@ -2549,6 +2590,7 @@ rpa_status rpa_energy_backward(rpa_ctx* c, int32_t nq, const int32_t* iqs, const
   if (nq < 1 || nq > kMaxIndex || !iqs || !wq || nw < 1 || nw > 4096 || !omega || !W || nsets < 0 ||
       (nsets > 0 && !set_ids) || !std::isfinite(dEc))
     return fail(c, RPA_ERR_ARG, "bad rpa_energy_backward arguments");
+  HOST_ARGS(c, iqs, wq, omega, W, Ec, set_ids, dC, dP, dchi);
   CUDA_OK(c, cudaSetDevice(c->prm.device));
   prof_begin(c);
   ++c->stamp;
@@ -2637,7 +2679,7 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
 }
 
 rpa_status rpa_get_profile(const rpa_ctx* c, double* ms, int64_t* launches) {
-  if (!c) return RPA_ERR_ARG;
+  if (!c || !host_readable(ms) || !host_readable(launches)) return RPA_ERR_ARG;
   for (int i = 0; i < RPA_NSTAGES; ++i) {
     if (ms) ms[i] = c->prof_ms[i];
     if (launches) launches[i] = c->prof_launch[i];

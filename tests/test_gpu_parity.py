@@ -374,3 +374,68 @@ def test_state_and_argument_errors():
         assert e.value.status == b.RPA_ERR_ARG
     finally:
         b.rpa_destroy(ctx)
+
+
+def test_device_memory_in_host_arguments_is_an_argument_error():
+    """Frequencies, weights, index lists, small parameter arrays and scalar
+    outputs are read or written by the host: device memory there is
+    RPA_ERR_ARG (not a crash of the process), and the context stays usable."""
+    import ctypes as ct
+    import torch
+    p = syn.config0()
+    om, W = o.frequency_grid(4)
+    ctx = _ctx(p, "fp64")
+    try:
+        lib = b.lib()
+
+        def hp(a):
+            return a.ctypes.data_as(b._P)
+
+        def dp(t):
+            return ct.c_void_p(t.data_ptr())
+
+        om_h, W_h = np.ascontiguousarray(om), np.ascontiguousarray(W)
+        iq_h, wq_h = np.zeros(1, np.int32), np.ones(1)
+        om_d = torch.from_numpy(om_h).cuda()
+        iq_d = torch.zeros(1, dtype=torch.int32, device="cuda")
+        one_d = torch.ones(1, dtype=torch.float64, device="cuda")
+        ng = len(b.rpa_gvectors(ctx, 0))
+        out = np.zeros((len(om), ng, ng), dtype=np.complex128)
+        E = ct.c_double()
+        s, qp = p.sets[0], p.qpoints[0]
+        k_h = np.ascontiguousarray(s.k_red, dtype=np.float64)
+        m_h = np.ascontiguousarray(s.miller, dtype=np.int32)
+        C_h = np.ascontiguousarray(s.C, dtype=np.complex128)
+        e_h, f_h = np.ascontiguousarray(s.eps, dtype=np.float64), np.ascontiguousarray(s.f, dtype=np.float64)
+        q_h = np.ascontiguousarray(qp.q_red, dtype=np.float64)
+        ko_h, kq_h = np.ascontiguousarray(qp.k_of, dtype=np.int32), np.ascontiguousarray(qp.kq_of, dtype=np.int32)
+        G0_h = np.ascontiguousarray(np.asarray(qp.G0).reshape(-1, 3), dtype=np.int32)
+        nb, npw = C_h.shape
+        e_d, m_d, ko_d = (torch.from_numpy(a).cuda() for a in (e_h, m_h, ko_h))
+        st = {
+            "chi0 omega": lib.rpa_chi0(ctx, 0, len(om), dp(om_d), hp(out)),
+            "energy iqs": lib.rpa_energy(ctx, 1, dp(iq_d), hp(wq_h), len(om), hp(om_h), hp(W_h), ct.byref(E),
+                                         None),
+            "energy wq": lib.rpa_energy(ctx, 1, hp(iq_h), dp(one_d), len(om), hp(om_h), hp(W_h), ct.byref(E),
+                                        None),
+            "energy Ec": lib.rpa_energy(ctx, 1, hp(iq_h), hp(wq_h), len(om), hp(om_h), hp(W_h), dp(one_d), None),
+            "frequencies": lib.rpa_set_frequencies(ctx, len(om), dp(om_d)),
+            "orbitals eps": lib.rpa_set_orbitals(ctx, 7, hp(k_h), nb, npw, hp(m_h), hp(C_h), dp(e_d), hp(f_h)),
+            "orbitals miller": lib.rpa_set_orbitals(ctx, 7, hp(k_h), nb, npw, dp(m_d), hp(C_h), hp(e_h), hp(f_h)),
+            "qpoint k_of": lib.rpa_set_qpoint(ctx, 3, hp(q_h), len(ko_h), dp(ko_d), hp(kq_h), hp(G0_h), None),
+            "gvectors ng": lib.rpa_gvectors(ctx, 0, dp(iq_d), None),
+        }
+        assert all(v == b.RPA_ERR_ARG for v in st.values()), st
+        # nothing was changed, and device memory where the header allows it still works
+        with pytest.raises(b.RpaError) as e:
+            b.rpa_gvectors(ctx, 3)
+        assert e.value.status == b.RPA_ERR_STATE
+        Ed, _ = b.rpa_energy(ctx, [0], [1.0], om, W)
+        Er, _ = o.energy(p, om, W)
+        assert abs(Ed - Er) < TOL["fp64"]["ec"] * abs(Er)
+        chi_d = torch.zeros((len(om), ng, ng), dtype=torch.complex128, device="cuda")
+        b.rpa_chi0(ctx, 0, om, chi_d)
+        torch.cuda.synchronize()
+        assert _rel(chi_d.cpu().numpy(), o.chi0(p, 0, om)) < TOL["fp64"]["chi"]
+    finally:
+        b.rpa_destroy(ctx)
