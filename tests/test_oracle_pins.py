@@ -57,6 +57,28 @@ def test_gsphere_lattice_point_counts():
     assert key == sorted(key)
 
 
+def test_reciprocal_lattice_is_dual_to_the_cell():
+    """Plane waves e^{iG.r} of reciprocal lattice vectors are periodic on the
+    crystal lattice (G.R a multiple of 2 pi for every lattice vector R), for a
+    hexagonal and a triclinic cell whose lattice matrices are not symmetric;
+    the hexagonal one has six equal shortest G in its basal plane."""
+    hexa = np.array([[4.0, 0.0, 0.0], [-2.0, 2.0 * np.sqrt(3.0), 0.0], [0.0, 0.0, 2.5]])
+    tri = np.array([[7.0, 0.0, 0.0], [2.1, 6.4, 0.0], [-1.3, 1.7, 8.2]])
+    rng = np.random.default_rng(5)
+    for cell in (hexa, tri):
+        B = o.reciprocal(cell)
+        G = rng.integers(-4, 5, size=(40, 3)) @ B
+        R = rng.integers(-4, 5, size=(40, 3)) @ cell
+        assert np.abs(np.exp(1j * (G @ R.T)) - 1.0).max() < 1e-11
+        # half a lattice vector is not a period of every plane wave
+        assert np.abs(np.exp(1j * (G @ (0.5 * R.T))) - 1.0).max() > 1.0
+    b1 = 2.0 * np.pi / (4.0 * np.sqrt(3.0) / 2.0)   # |b1| of the hexagonal lattice
+    gm = o.g_sphere(hexa, [0, 0, 0], 0.5 * b1 ** 2 * 1.001)
+    assert len(gm) == 7
+    g2 = np.sum((gm @ o.reciprocal(hexa)) ** 2, 1)
+    assert np.allclose(np.sort(g2)[1:], b1 ** 2, rtol=1e-12)
+
+
 def test_coulomb_zero_only_at_q_plus_g_zero():
     cell = np.eye(3) * 10.0
     gm = o.g_sphere(cell, [0, 0, 0], 1.0)
@@ -200,6 +222,27 @@ def test_chi0_hermitian_negative_semidefinite_and_additive():
     assert np.abs(a + b - chi).max() <= 1e-14 * np.abs(chi).max()
 
 
+def test_chi0_is_a_bz_average():
+    """Eq. 3 averages over the BZ mesh, s/(Omega N_k) sum_k: listing every
+    transition of a q-point r times on a mesh of r N_k points averages r equal
+    terms, so chi0 and E_c do not change."""
+    import dataclasses
+    p = syn.small_problem(config_tag=87)
+    om, W = o.frequency_grid(3)
+    iq = 1
+    Q = syn.paw_Q(p.paw, p.cell, p.qpoints[iq].q_red, o.g_sphere(p.cell, p.qpoints[iq].q_red, p.ecut_chi))
+    qp = p.qpoints[iq]
+    ref = o.chi0(p, iq, om, Q)
+    E, _ = o.energy(p, om, W, {iq: Q}, iqs=[iq])
+    for r in (2, 3):
+        rep = syn.QPoint(qp.q_red, np.tile(qp.k_of, r), np.tile(qp.kq_of, r), np.tile(qp.G0, (r, 1)), qp.weight)
+        pr = dataclasses.replace(p, nk_bz=r * p.nk_bz, qpoints=[p.qpoints[0], rep])
+        assert np.abs(o.chi0(pr, iq, om, Q) - ref).max() <= 1e-14 * np.abs(ref).max()
+        Er, _ = o.energy(pr, om, W, {iq: Q}, iqs=[iq])
+        assert abs(Er - E) <= 1e-13 * abs(E)
+    assert np.abs(ref).max() > 1e-4
+
+
 def test_chi0_time_reversal_equals_literal_eq3():
     """Gamma point, q = 0, real orbitals (C(-Q) = conj C(Q)): the oracle's real
     pair weight over f_n > f_m equals Eq. 3 with the complex factor
@@ -235,7 +278,8 @@ def test_chi0_time_reversal_equals_literal_eq3():
     C = np.array(C)
     assert np.abs(C @ C.conj().T - np.eye(nb)).max() < 1e-12
     eps = np.sort(rng.uniform(-1, 2, nb))
-    f = np.array([1, 1, 1, 0.4, 0, 0, 0, 0.0])
+    # two partly occupied bands: the pair (0.4, 0.7) enters once, with f_n > f_m
+    f = np.array([1, 1, 0.7, 0.4, 0, 0, 0, 0.0])
     s = syn.OrbitalSet(np.zeros(3), m.astype(np.int32), C, eps, f)
     qp = syn.QPoint(np.zeros(3), np.array([0]), np.array([0]), np.zeros((1, 3), np.int32), 1.0)
     prob = syn.Problem("tr", 0, cell, (16, 16, 16), 2.5, 1.0, 2.0, 1, [s], [qp], 4)

@@ -34,8 +34,7 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.fixture(scope="module")
-def mesh_case():
+def _mesh_case():
     # two k-points along x: q = (1/2, 0, 0) maps k = 1/2 onto k' = 0 with the
     # umklapp G0 = (1, 0, 0); two PAW atoms with 4 and 5 projectors
     p = syn.small_problem(config_tag=97, nocc=3, nunocc=14, nproj=(4, 5), nw=3)
@@ -46,6 +45,11 @@ def mesh_case():
     Q, ng = _Q(p, iq)
     full = o.chi0(p, iq, om, Q)
     return p, iq, om, Q, ng, full
+
+
+@pytest.fixture(scope="module")
+def mesh_case():
+    return _mesh_case()
 
 
 def test_sampled_equals_full_on_unsorted_gaps(mesh_case):

@@ -67,6 +67,35 @@ def test_rotated_orbitals_give_the_chi0_of_the_rotated_k_point():
     assert np.abs(chi([wrong]) - b).max() > 1e-3 * np.abs(b).max()
 
 
+def _psi(s, x):
+    """Orbitals of set s at reduced positions x (npts, 3) by the plane-wave sum
+    of Eq. 8 without the Omega^-1/2 factor: (nbands, npts)."""
+    kq = np.asarray(s.k_red, float)[None, :] + np.asarray(s.miller, float)
+    return np.asarray(s.C) @ np.exp(2j * np.pi * (kq @ x.T))
+
+
+def test_rotated_set_is_the_transformed_function_in_real_space():
+    """Eq. 9 point by point.  With k' = M k on reduced reciprocal coordinates the
+    operation {T|tau} maps reduced positions by x -> M^-T x + tau, so the set
+    it produces must satisfy psi'(x) = psi(M^T (x - tau)); time reversal
+    conjugates that.  Checked on the plane-wave sums of both sets at random
+    points, for a unimodular M that is not a rotation of this cell (the
+    identity holds for any), a fractional translation and time reversal."""
+    s = syn.make_orbitals(6, 0, np.diag([5.0, 5.5, 6.0]), [0.1, 0.25, -0.2], 2.0, 2, 3)
+    M = np.array([[1, 1, 0], [0, 1, 0], [0, 1, 1]])
+    assert round(np.linalg.det(M)) == 1
+    tau = np.array([0.1, -0.35, 0.2])
+    x = np.random.default_rng(8).uniform(-1.0, 1.0, (9, 3))
+    for tr in (False, True):
+        r = o.rotate_set(s, M, time_reversal=tr, tau=tau)
+        want = _psi(s, (x - tau) @ M)
+        if tr:
+            want = np.conj(want)
+        assert np.abs(_psi(r, x) - want).max() < 1e-12 * np.abs(want).max()
+    # the inversion image psi(-x) is a different function: conjugation matters
+    assert np.abs(_psi(s, -x) - np.conj(_psi(s, x))).max() > 1e-2 * np.abs(_psi(s, x)).max()
+
+
 def test_projector_rotation_composes_and_identity_is_a_no_op():
     s = syn.make_orbitals(4, 0, np.eye(3) * 6.0, [0.1, 0.2, 0.0], 3.0, 3, 5)
     nproj = [3, 3, 2]
