@@ -48,10 +48,11 @@ def test_header_constants_match_the_binding():
 
 def test_gauss_legendre_matches_oracle(lib):
     for n in (1, 2, 8, 16, 33):
-        om, W = b.rpa_gauss_legendre(n, 1.0)
-        omr, Wr = o.frequency_grid(n, 1.0)
-        assert np.allclose(om, omr, rtol=1e-13, atol=0)
-        assert np.allclose(W, Wr, rtol=1e-12, atol=0)
+        for omega0 in (1.0, 0.4, 2.5):
+            om, W = b.rpa_gauss_legendre(n, omega0)
+            omr, Wr = o.frequency_grid(n, omega0)
+            assert np.allclose(om, omr, rtol=1e-13, atol=0)
+            assert np.allclose(W, Wr, rtol=1e-12, atol=0)
     with pytest.raises(b.RpaError) as e:
         b.rpa_gauss_legendre(0)
     assert e.value.status == b.RPA_ERR_ARG

@@ -106,6 +106,29 @@ MUTATIONS = [
     ("gradient: conjugate of Q dropped in the PAW adjoint", '"gnm,ni,ijg->mj", nbar, Pn, np.conj(Qa))',
      '"gnm,ni,ijg->mj", nbar, Pn, Qa)', 1),
     ("gradient: optical head adjoint sign", "bmat = 1j * nbar[ig0] / dlt", "bmat = -1j * nbar[ig0] / dlt", 1),
+    ("gradient: umklapp shift dropped in the adjoint", "tgt = millk + G + np.asarray(G0, dtype=np.int64)",
+     "tgt = millk + G", 2),
+    ("gradient: Q_ij transposed in the PAW adjoint", '"gnm,mj,ijg->ni", np.conj(nbar), Pm, Qa)',
+     '"gnm,mj,jig->ni", np.conj(nbar), Pm, Qa)', 1),
+    # further slips in the inputs of the method
+    ("quadrature: omega0 ignored in the nodes", "omega = omega0 * (1.0 + x) / (1.0 - x)",
+     "omega = (1.0 + x) / (1.0 - x)", 1),
+    ("quadrature: omega0 ignored in the weights", "W = wx * 2.0 * omega0 / (1.0 - x) ** 2",
+     "W = wx * 2.0 / (1.0 - x) ** 2", 1),
+    ("Coulomb: v_G = 0 at G = 0 for every q", "nz = np.any(qg != 0.0, axis=1)",
+     "nz = np.any(np.asarray(gmiller) != 0, axis=1)", 1),
+    ("sphere: q ignored", "v = (np.array([g1, g2, g3], dtype=np.float64) + q) @ B",
+     "v = np.array([g1, g2, g3], dtype=np.float64) @ B", 1),
+    ("PAW: Q block offset not advanced", "        off += ni\n        qoff += ni * ni * ng\n    return out",
+     "        off += ni\n    return out", 1),
+    ("chi0: only the first transition summed", "    for t in range(len(qp.k_of)):\n        ik, ikp, G0 = int(qp.k_of[t])",
+     "    for t in range(1):\n        ik, ikp, G0 = int(qp.k_of[t])", 1),
+    ("optical: q direction not normalised", "    qhat = qhat / np.linalg.norm(qhat)\n    B = reciprocal(cell)",
+     "    B = reciprocal(cell)", 1),
+    ("symmetry: k not rotated", "kr = M @ np.asarray(oset.k_red, dtype=np.float64)",
+     "kr = np.asarray(oset.k_red, dtype=np.float64)", 1),
+    ("symmetry: plane waves rotated by M^T", "Qr = np.asarray(oset.miller, dtype=np.int64) @ M.T",
+     "Qr = np.asarray(oset.miller, dtype=np.int64) @ M", 1),
 ]
 
 

@@ -42,6 +42,11 @@ def test_frequency_map_lorentzian_integral(delta):
     assert errs[1] < 2e-3
     om, W = o.frequency_grid(16)
     assert np.all(om > 0) and np.all(W > 0) and np.all(np.diff(om) > 0)
+    # the scale omega0 of the map is free: the rule integrates the same
+    # Lorentzian for any omega0
+    for omega0 in (0.4, 2.5):
+        om, W = o.frequency_grid(64, omega0)
+        assert abs(np.sum(W / (om ** 2 + delta ** 2)) - np.pi / (2 * delta)) < 1e-8 * np.pi / (2 * delta)
 
 
 # ---------------------------------------------------------------- G sphere
@@ -55,6 +60,24 @@ def test_gsphere_lattice_point_counts():
     g = o.g_sphere(cell, [0, 0, 0], 2.5)
     key = [tuple(r) for r in g]
     assert key == sorted(key)
+
+
+def test_gsphere_off_gamma():
+    """At q = (1/2, 0, 0) of a cell with B = identity, |q+G| = 1/2 for G = 0 and
+    G = (-1, 0, 0) only, so a cutoff just above 1/8 holds exactly those two;
+    just above 5/8 adds the eight G with |q+G|^2 = 5/4.  Moving q by a lattice
+    vector G0 moves the sphere by -G0."""
+    cell = np.eye(3) * 2 * np.pi
+    q = np.array([0.5, 0.0, 0.0])
+    g = o.g_sphere(cell, q, 0.125 * 1.001)
+    assert sorted(map(tuple, g)) == [(-1, 0, 0), (0, 0, 0)]
+    assert len(o.g_sphere(cell, q, 0.625 * 1.001)) == 10
+    tri = np.array([[7.0, 0.0, 0.0], [2.1, 6.4, 0.0], [-1.3, 1.7, 8.2]])
+    qt = np.array([0.25, -0.125, 1.0 / 3.0])
+    G0 = np.array([1, -2, 1])
+    a = o.g_sphere(tri, qt, 3.0)
+    b = o.g_sphere(tri, qt + G0, 3.0)
+    assert np.array_equal(b, a - G0)
 
 
 def test_reciprocal_lattice_is_dual_to_the_cell():
@@ -363,6 +386,10 @@ def _fd_problem():
     p = syn.small_problem(config_tag=93, a=5.0, grid=(10, 10, 10), ecut_wf=2.5, ecut_chi=1.2,
                           nocc=2, nunocc=6, mesh=(2, 1, 1), nproj=(2, 3), nw=4)
     Qs = [syn.paw_Q(p.paw, p.cell, qp.q_red, o.g_sphere(p.cell, qp.q_red, p.ecut_chi)) for qp in p.qpoints]
+    # the synthetic c_ij are symmetric (real partial waves); a general Q_ij(G)
+    # is not, and the adjoint must tell i from j
+    rng = np.random.default_rng(17)
+    Qs = [Q + 0.05 * (rng.standard_normal(Q.shape) + 1j * rng.standard_normal(Q.shape)) for Q in Qs]
     return p, Qs
 
 
