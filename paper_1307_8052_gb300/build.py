@@ -47,7 +47,8 @@ def _compile(src: str, verbose: bool) -> tuple[str, str]:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "rpa_internal.h"), os.path.join(ROOT, "include", "rpa.h")]
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    deps = srcs + headers + [os.path.join(ROOT, "include", "rpa.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) < t for d in deps):
