@@ -258,7 +258,7 @@ rpa_status rpa_energy_collect(rpa_ctx* ctx, const double* wq, const double* W,
  * When every context uses RPA_BF16X2 (RPA_TUNE_BATCH_PERSIST of ctxs[0] = 1,
  * the default), the graph is built around persistent launches: the k-blocks
  * of all contexts and q-points are packed, in order, into groups (at most
- * RPA_TUNE_BATCH_MB, 16 GiB by default, of rank-k operands and 32 blocks
+ * RPA_TUNE_BATCH_MB, 16 GiB by default, of rank-k operands and 24 blocks
  * each; a larger block alone); per group the pair densities and operand
  * preparation of its blocks run into a graph-owned buffer, one persistent
  * tensor-core launch (one CTA per SM)
