@@ -457,7 +457,7 @@ rpa_status rpa_set_tuning(rpa_ctx* ctx, int32_t param, int64_t value);
  * `stream` (a cudaStream_t; NULL = the legacy default stream) of the current
  * device, and the call returns after that stream has finished it.
  *
- * Scratch: one process-wide static device array per device (17 MiB + 2 KiB,
+ * Scratch: one process-wide static device array per device (17 MiB + 1040 B,
  * held until the process exits).  Limits: 1 <= nw <= 64 and
  * nw * ng * ng <= 1048576 (e.g. ng <= 256 at nw = 16); larger sizes, null or
  * host pointers, and device memory of a GPU other than the current device

@@ -646,7 +646,7 @@ cudaError_t run_logdet_batch(const LdMat* d, int nmat, int maxNG, cudaStream_t s
 // kNoAllocMaxElems complex elements), the inverses of the diagonal blocks (CB^2
 // per frequency), the per-frequency log-det and trace accumulators and the
 // pivot flag.  It lives for the life of the process on every device that loads
-// the library (17 MiB + 2 KiB).
+// the library (17 MiB + 1040 B).
 constexpr int64_t kNoAllocMaxElems = (int64_t)1 << 20;
 constexpr int kNoAllocMaxNw = 64;
 constexpr int64_t kNoAllocLinv = (int64_t)kNoAllocMaxNw * CB * CB;
