@@ -436,7 +436,7 @@ def run_ours(args):
                               "blocked Cholesky, FP64 throughout"),
                    "quadrature": "FP64 Gauss-Legendre, 16 nodes mapped to [0, inf)",
                    "pairs_per_q": [Kall[i] for i in iqs_all], "nw": p.nw,
-                   "l2": "inputs larger than L2 (grids 1.2 GB, pair densities + rank-k operands >= 3.5 GB per block)",
+                   "l2": "inputs larger than L2 (grids >= 1.2 GB, pair densities + rank-k operands >= 3.5 GB per block)",
                    "parallelism": (f"replicas x{world}" if args.replicas or world == 1 else
                                    f"q-points sharded over {world} ranks (no data-path collective): "
                                    + "; ".join(f"rank {r}: q {part}" for r, part in enumerate(shards)))},
