@@ -98,18 +98,51 @@ def lib() -> ct.CDLL:
 
 
 # ------------------------------------------------------------------ marshalling
+_TORCH_DTYPE = {np.dtype(np.complex128): "torch.complex128", np.dtype(np.float64): "torch.float64",
+                np.dtype(np.int32): "torch.int32"}
+
+
+def _is_tensor(x):
+    return hasattr(x, "data_ptr") and hasattr(x, "is_contiguous")
+
+
 def _ptr(x, dtype=None, keep=None):
-    """Pointer to contiguous memory of x (numpy array or torch tensor)."""
+    """Pointer to contiguous memory of an input (numpy array, sequence or torch
+    tensor).  Host arrays are converted to ``dtype`` (a copy if needed, kept
+    alive in ``keep``); a tensor, which may live on the device, is passed as
+    it is and must already be contiguous and of that dtype."""
     if x is None:
         return None
-    if hasattr(x, "data_ptr") and hasattr(x, "is_contiguous"):
+    if _is_tensor(x):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(x.dtype) != _TORCH_DTYPE[np.dtype(dtype)]:
+            raise TypeError(f"tensor of {x.dtype} where {_TORCH_DTYPE[np.dtype(dtype)]} is required")
         return ct.c_void_p(x.data_ptr())
     a = np.ascontiguousarray(x, dtype=dtype)
     if keep is not None:
         keep.append(a)
     return ct.c_void_p(a.ctypes.data)
+
+
+def _out_ptr(x, dtype, count=None):
+    """Pointer to an output buffer that the library fills in place: a writable,
+    contiguous numpy array or tensor of exactly ``dtype`` (and ``count``
+    elements when the binding knows the size).  Never a converted copy, whose
+    contents the caller would not see, nor a narrower type the library would
+    write past."""
+    dt = np.dtype(dtype)
+    if _is_tensor(x):
+        ok = x.is_contiguous() and str(x.dtype) == _TORCH_DTYPE[dt] and (count is None or x.numel() == count)
+        ptr = x.data_ptr() if ok else 0
+    else:
+        ok = (isinstance(x, np.ndarray) and x.flags.c_contiguous and x.flags.writeable and x.dtype == dt
+              and (count is None or x.size == count))
+        ptr = x.ctypes.data if ok else 0
+    if not ok:
+        size = "" if count is None else f" of {count} elements"
+        raise ValueError(f"output buffer must be a writable contiguous {dt} array or tensor{size}")
+    return ct.c_void_p(ptr)
 
 
 def _check(ctx, st):
@@ -247,11 +280,12 @@ def rpa_chi0(ctx, iq, omega, out=None):
     """chi0[nw][NG][NG] complex128; ``out`` may be a preallocated numpy array or CUDA tensor."""
     keep = []
     omega = np.ascontiguousarray(omega, dtype=np.float64)
+    ng = ct.c_int32()
+    _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
     if out is None:
-        ng = ct.c_int32()
-        _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
         out = np.zeros((len(omega), ng.value, ng.value), dtype=np.complex128)
-    _check(ctx, lib().rpa_chi0(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), _ptr(out, None, keep)))
+    dst = _out_ptr(out, np.complex128, len(omega) * ng.value * ng.value)
+    _check(ctx, lib().rpa_chi0(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), dst))
     return out
 
 
@@ -259,11 +293,12 @@ def rpa_epsilon_inv(ctx, iq, omega, out=None):
     """(1 - v^1/2 chi0 v^1/2)^-1 [nw][NG][NG] complex128; ``out`` may be a preallocated numpy array or CUDA tensor."""
     keep = []
     omega = np.ascontiguousarray(omega, dtype=np.float64)
+    ng = ct.c_int32()
+    _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
     if out is None:
-        ng = ct.c_int32()
-        _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
         out = np.zeros((len(omega), ng.value, ng.value), dtype=np.complex128)
-    _check(ctx, lib().rpa_epsilon_inv(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), _ptr(out, None, keep)))
+    dst = _out_ptr(out, np.complex128, len(omega) * ng.value * ng.value)
+    _check(ctx, lib().rpa_epsilon_inv(ctx, int(iq), len(omega), _ptr(omega, np.float64, keep), dst))
     return out
 
 
@@ -291,18 +326,31 @@ def rpa_energy_backward(ctx, iqs, wq, omega, W, dEc=1.0, sets=(), dC=None, dP=No
     omega = np.ascontiguousarray(omega, dtype=np.float64)
     sets = np.ascontiguousarray(sets, dtype=np.int32)
 
-    def ptr_array(bufs, n):
+    def ptr_array(bufs, n, counts=None):
         if bufs is None:
             return None
-        arr = (ct.c_void_p * n)(*[(_ptr(x, None, keep).value if x is not None else None) for x in bufs])
+        if len(bufs) > n:
+            raise ValueError(f"{len(bufs)} output buffers for {n} entries")
+        ptrs = [_out_ptr(x, np.complex128, None if counts is None else counts[i]).value if x is not None else None
+                for i, x in enumerate(bufs)]
+        arr = (ct.c_void_p * n)(*ptrs)
         keep.append(arr)
         return ct.cast(arr, ct.c_void_p)
+
+    chi_counts = None
+    if dchi is not None:
+        chi_counts = []
+        for iq in iqs:
+            ng = ct.c_int32()
+            _check(ctx, lib().rpa_gvectors(ctx, int(iq), ct.byref(ng), None))
+            chi_counts.append(len(omega) * ng.value * ng.value)
 
     E = ct.c_double()
     st = lib().rpa_energy_backward(ctx, len(iqs), _ptr(iqs, np.int32, keep), _ptr(wq, np.float64, keep), len(omega),
                                    _ptr(omega, np.float64, keep), _ptr(W, np.float64, keep), float(dEc),
                                    ct.byref(E), len(sets), _ptr(sets, np.int32, keep) if len(sets) else None,
-                                   ptr_array(dC, len(sets)), ptr_array(dP, len(sets)), ptr_array(dchi, len(iqs)))
+                                   ptr_array(dC, len(sets)), ptr_array(dP, len(sets)),
+                                   ptr_array(dchi, len(iqs), chi_counts))
     _check(ctx, st)
     return E.value
 
@@ -361,7 +409,8 @@ def rpa_logdet_noalloc(chi, v, terms, stream=0):
     """Allocation-free log-det terms from device tensors chi [nw][ng][ng] (complex128),
     v [ng] and terms [nw] (float64); see include/rpa.h."""
     nw, ng = int(chi.shape[0]), int(chi.shape[1])
-    _check(None, lib().rpa_logdet_noalloc(_ptr(chi), _ptr(v), nw, ng, _ptr(terms),
+    _check(None, lib().rpa_logdet_noalloc(_ptr(chi, np.complex128), _ptr(v, np.float64), nw, ng,
+                                          _out_ptr(terms, np.float64, nw),
                                           ct.c_void_p(int(stream)) if stream else None))
 
 
