@@ -125,6 +125,16 @@ def _ptr(x, dtype=None, keep=None):
     return ct.c_void_p(a.ctypes.data)
 
 
+def _host(x, dtype, shape, what):
+    """A host array argument as a contiguous array of ``dtype``, checked
+    against the shape that the other arguments imply: the library reads
+    exactly that many elements."""
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if a.shape != tuple(shape):
+        raise ValueError(f"{what} has shape {a.shape}, expected {tuple(shape)}")
+    return a
+
+
 def _out_ptr(x, dtype, count=None):
     """Pointer to an output buffer that the library fills in place: a writable,
     contiguous numpy array or tensor of exactly ``dtype`` (and ``count``
@@ -186,6 +196,10 @@ def rpa_gauss_legendre(n, omega0=1.0):
 def rpa_set_orbitals(ctx, kidx, k_red, miller, C, eps, f):
     keep = []
     nb, npw = int(C.shape[0]), int(C.shape[1])
+    k_red = _host(k_red, np.float64, (3,), "k_red")
+    miller = _host(miller, np.int32, (npw, 3), "miller")
+    eps = _host(eps, np.float64, (nb,), "eps")
+    f = _host(f, np.float64, (nb,), "f")
     st = lib().rpa_set_orbitals(ctx, int(kidx), _ptr(k_red, np.float64, keep), nb, npw,
                                 _ptr(miller, np.int32, keep), _ptr(C, np.complex128, keep),
                                 _ptr(eps, np.float64, keep), _ptr(f, np.float64, keep))
@@ -202,10 +216,13 @@ def rpa_set_paw(ctx, kidx, nproj, P):
 def rpa_set_qpoint(ctx, iq, q_red, k_of, kq_of, G0) -> int:
     keep = []
     ng = ct.c_int32()
-    k_of = np.asarray(k_of, dtype=np.int32)
-    st = lib().rpa_set_qpoint(ctx, int(iq), _ptr(q_red, np.float64, keep), len(k_of), _ptr(k_of, np.int32, keep),
-                              _ptr(kq_of, np.int32, keep), _ptr(np.asarray(G0).reshape(-1, 3), np.int32, keep),
-                              ct.byref(ng))
+    k_of = np.ascontiguousarray(k_of, dtype=np.int32).reshape(-1)
+    nk = len(k_of)
+    q_red = _host(q_red, np.float64, (3,), "q_red")
+    kq_of = _host(kq_of, np.int32, (nk,), "kq_of")
+    G0 = _host(np.asarray(G0).reshape(-1, 3), np.int32, (nk, 3), "G0")
+    st = lib().rpa_set_qpoint(ctx, int(iq), _ptr(q_red, np.float64, keep), nk, _ptr(k_of, np.int32, keep),
+                              _ptr(kq_of, np.int32, keep), _ptr(G0, np.int32, keep), ct.byref(ng))
     _check(ctx, st)
     return ng.value
 
@@ -307,6 +324,8 @@ def rpa_energy(ctx, iqs, wq, omega, W):
     keep = []
     iqs = np.ascontiguousarray(iqs, dtype=np.int32)
     omega = np.ascontiguousarray(omega, dtype=np.float64)
+    wq = _host(wq, np.float64, (len(iqs),), "wq")
+    W = _host(W, np.float64, (len(omega),), "W")
     terms = np.zeros((len(iqs), len(omega)))
     E = ct.c_double()
     st = lib().rpa_energy(ctx, len(iqs), _ptr(iqs, np.int32, keep), _ptr(wq, np.float64, keep), len(omega),
@@ -325,6 +344,8 @@ def rpa_energy_backward(ctx, iqs, wq, omega, W, dEc=1.0, sets=(), dC=None, dP=No
     iqs = np.ascontiguousarray(iqs, dtype=np.int32)
     omega = np.ascontiguousarray(omega, dtype=np.float64)
     sets = np.ascontiguousarray(sets, dtype=np.int32)
+    wq = _host(wq, np.float64, (len(iqs),), "wq")
+    W = _host(W, np.float64, (len(omega),), "W")
 
     def ptr_array(bufs, n, counts=None):
         if bufs is None:
@@ -370,6 +391,7 @@ def rpa_energy_enqueue(ctx, iqs):
 def rpa_energy_collect(ctx, wq, W, nq):
     keep = []
     W = np.ascontiguousarray(W, dtype=np.float64)
+    wq = _host(wq, np.float64, (nq,), "wq")
     terms = np.zeros((nq, len(W)))
     E = ct.c_double()
     _check(ctx, lib().rpa_energy_collect(ctx, _ptr(wq, np.float64, keep), _ptr(W, np.float64, keep), ct.byref(E),

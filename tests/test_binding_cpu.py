@@ -94,3 +94,30 @@ def test_wrappers_pass_the_caller_buffers(monkeypatch):
     with pytest.raises(ValueError):
         b.rpa_energy_backward("ctx", [0], [1.0], om, [1.0, 1.0], 1.0, [0], None, None,
                               [np.zeros((2, 2, 2), dtype=np.complex128)])
+
+
+def test_host_arrays_must_match_the_sizes_the_library_reads(monkeypatch):
+    fake = _FakeLib()
+    monkeypatch.setattr(b, "_lib", fake)
+    C = np.zeros((4, 6), dtype=np.complex128)
+    mil = np.zeros((6, 3), dtype=np.int32)
+    b.rpa_set_orbitals("ctx", 0, [0.0, 0.0, 0.0], mil, C, np.zeros(4), np.ones(4))
+    assert fake.calls[-1][0] == "rpa_set_orbitals"
+    for bad in ({"miller": mil[:5]}, {"eps": np.zeros(3)}, {"f": np.ones(5)}, {"k_red": [0.0, 0.0]}):
+        kw = dict(k_red=[0.0, 0.0, 0.0], miller=mil, eps=np.zeros(4), f=np.ones(4))
+        kw.update(bad)
+        with pytest.raises(ValueError):
+            b.rpa_set_orbitals("ctx", 0, kw["k_red"], kw["miller"], C, kw["eps"], kw["f"])
+    b.rpa_set_qpoint("ctx", 0, [0.5, 0, 0], [0, 1], [1, 0], [[0, 0, 0], [1, 0, 0]])
+    with pytest.raises(ValueError):
+        b.rpa_set_qpoint("ctx", 0, [0.5, 0, 0], [0, 1], [1], [[0, 0, 0], [1, 0, 0]])
+    with pytest.raises(ValueError):
+        b.rpa_set_qpoint("ctx", 0, [0.5, 0, 0], [0, 1], [1, 0], [[0, 0, 0]])
+    om = np.array([0.5, 1.0])
+    b.rpa_energy("ctx", [0, 1], [0.5, 0.5], om, [1.0, 1.0])
+    with pytest.raises(ValueError):
+        b.rpa_energy("ctx", [0, 1], [1.0], om, [1.0, 1.0])
+    with pytest.raises(ValueError):
+        b.rpa_energy("ctx", [0], [1.0], om, [1.0])
+    with pytest.raises(ValueError):
+        b.rpa_energy_collect("ctx", [1.0], [1.0, 1.0], 2)
