@@ -95,16 +95,21 @@ typedef struct {
   void* stream;        /* cudaStream_t to order work on; NULL: library stream */
 } rpa_params;
 
-/* Creates a context on params->device.  Validates the cell (non-singular),
+/* Creates a context on params->device holding the fixed inputs of the
+ * calculation (Table 1: the cell and real-space grid of Eqs. 8 and 10, the
+ * response cutoff of Sec. 2.1, the prefactor s / (Omega N_k) of Eq. 3).
+ * Validates the cell (non-singular),
  * grid (each N_i in [2, 768]), ecut_chi > 0, spin_factor > 0, nk_bz >= 1 and
  * the precision.  *out receives the context; RPA_ERR_ARG on bad parameters,
  * RPA_ERR_CUDA if the device cannot be used. */
 rpa_status rpa_create(const rpa_params* params, rpa_ctx** out);
 
-/* Releases every device allocation of the context.  NULL is ignored. */
+/* Releases every device allocation of the context (no counterpart in the
+ * paper).  NULL is ignored. */
 void rpa_destroy(rpa_ctx* ctx);
 
-/* Message of the last failing call on this context (never NULL). */
+/* Message of the last failing call on this context (never NULL; no
+ * counterpart in the paper). */
 const char* rpa_last_error(const rpa_ctx* ctx);
 
 /* Gauss-Legendre frequency grid (Sec. 2.1, 16 points in the paper) mapped to
@@ -294,9 +299,11 @@ rpa_status rpa_energy_backward(rpa_ctx* ctx, int32_t nq, const int32_t* iqs,
 
 /* Per-stage device timings of the most recent rpa_chi0/rpa_energy call,
  * measured with CUDA events on the context's stream when enabled by
- * rpa_set_profiling(ctx, 1).  Index: 0 wavefunctions to grid, 1 pair
- * densities (+PAW), 2 rank-k update kernel, 3 log-det, 4 other, 5 rank-k
- * operand preparation (split-bfloat16 modes).  ms[RPA_NSTAGES] total
+ * rpa_set_profiling(ctx, 1); the stages group the steps of Table 1 as the
+ * paper's per-step timings (Tables 2-3) do.  Index: 0 wavefunctions to grid
+ * (step 3), 1 pair densities (+PAW; steps 5-9), 2 rank-k update kernel
+ * (step 11), 3 log-det (step 13), 4 other, 5 rank-k operand preparation
+ * (split-bfloat16 modes).  ms[RPA_NSTAGES] total
  * milliseconds per stage, launches[RPA_NSTAGES] kernel launches per stage. */
 #define RPA_NSTAGES 6
 rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
