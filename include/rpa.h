@@ -310,7 +310,10 @@ rpa_status rpa_set_profiling(rpa_ctx* ctx, int32_t enable);
 rpa_status rpa_get_profile(const rpa_ctx* ctx, double* ms, int64_t* launches);
 
 /* Tuning knobs (they change launch shapes and rounding, never the quantity
- * computed):
+ * computed).  The paper's one knob is Nu, the number of unoccupied states
+ * grouped into one update (the multi-u approach of Sec. 3.2, Eq. 17); here
+ * every pair of a block of occupied bands enters one rank-k launch, and
+ * RPA_TUNE_OPERAND_MB and RPA_TUNE_PAIR_CHUNK set those group sizes:
  * RPA_TUNE_TC_FOLD     units of K accumulated in FP32 tensor memory before
  *                      the partial sum is added to FP32 running sums in
  *                      registers (split-bfloat16 modes), in [1, 2^20];
