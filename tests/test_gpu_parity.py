@@ -347,6 +347,35 @@ def test_not_hpd_is_reported_not_trapped():
         b.rpa_destroy(ctx)
 
 
+def test_device_allocation_failure_is_a_status_and_the_context_recovers():
+    """A chi0 that cannot fit in device memory (4096 frequencies x NG^2 x 16 B,
+    0.6 TB at NG 3042) makes the allocation fail before any kernel runs:
+    RPA_ERR_OOM, not a crash, and the same context then evaluates the q-point
+    at two frequencies exactly as a fresh context does."""
+    cell = np.eye(3) * 20.0
+    q = np.array([0.25, 0.0, 0.0])
+    sets = [syn.make_orbitals(81, i, cell, k, 0.5, 1, 2) for i, k in enumerate([np.zeros(3), q])]
+    qp = syn.QPoint(q, np.array([0]), np.array([1]), np.zeros((1, 3), np.int32), 1.0)
+    p = syn.Problem("oom", 81, cell, (24, 24, 24), 0.5, 4.0, 2.0, 1, sets, [qp], 2, None)
+    om, W = o.frequency_grid(2)
+    ctx = _ctx(p, "fp64")
+    try:
+        ng = len(b.rpa_gvectors(ctx, 0))
+        assert ng > 3000 and 4096 * ng * ng * 16 > 2 * 288e9
+        with pytest.raises(b.RpaError) as e:
+            b.rpa_energy(ctx, [0], [1.0], np.linspace(0.1, 10.0, 4096), np.ones(4096))
+        assert e.value.status == b.RPA_ERR_OOM
+        E1, t1 = b.rpa_energy(ctx, [0], [1.0], om, W)
+    finally:
+        b.rpa_destroy(ctx)
+    ctx = _ctx(p, "fp64")
+    try:
+        E2, t2 = b.rpa_energy(ctx, [0], [1.0], om, W)
+    finally:
+        b.rpa_destroy(ctx)
+    assert np.array_equal(t1, t2) and E1 == E2 and E1 < 0
+
+
 def test_state_and_argument_errors():
     p = syn.config0()
     ctx = b.rpa_create(p.cell, p.grid, p.ecut_chi, p.spin_factor, p.nk_bz, "fp64")
