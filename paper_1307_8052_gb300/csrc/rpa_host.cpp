@@ -1424,7 +1424,9 @@ rpa_status energy_backward_T(rpa_ctx* c, int nq, const int* iqs, const double* w
 extern "C" {
 
 rpa_status rpa_create(const rpa_params* p, rpa_ctx** out) {
-  if (!p || !out || !host_readable(p) || !host_readable(out)) return RPA_ERR_ARG;
+  // (no pointer-attribute query here: it would touch the current device
+  // before params->device is selected)
+  if (!p || !out) return RPA_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < 3; ++i)
     if (p->grid[i] < 2 || p->grid[i] > kMaxGrid) return RPA_ERR_ARG;
