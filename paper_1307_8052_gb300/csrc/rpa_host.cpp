@@ -295,7 +295,16 @@ bool host_readable(const void* p) {
   return a.type != cudaMemoryTypeDevice;
 }
 
+// The query runs with the context's device current, as the call's own work
+// does, so it never starts a context on another device.
+bool on_device(int device) {
+  if (cudaSetDevice(device) == cudaSuccess) return true;
+  cudaGetLastError();
+  return false;
+}
+
 rpa_status host_args(rpa_ctx* c, std::initializer_list<const void*> ps) {
+  if (!on_device(c->prm.device)) return fail(c, RPA_ERR_CUDA, "cudaSetDevice(%d) failed", c->prm.device);
   for (const void* p : ps)
     if (!host_readable(p)) return fail(c, RPA_ERR_ARG, "an argument the host reads or writes is device memory");
   return RPA_OK;
@@ -1901,7 +1910,9 @@ rpa_status rpa_set_qpoint(rpa_ctx* c, int32_t iq, const double q_red[3], int32_t
 }
 
 rpa_status rpa_gvectors(const rpa_ctx* c, int32_t iq, int32_t* ng, int32_t* miller_out) {
-  if (!c || !ng || !host_readable(ng) || !host_readable(miller_out)) return RPA_ERR_ARG;
+  if (!c || !ng) return RPA_ERR_ARG;
+  if (!on_device(c->prm.device)) return RPA_ERR_CUDA;
+  if (!host_readable(ng) || !host_readable(miller_out)) return RPA_ERR_ARG;
   auto it = c->qpts.find(iq);
   if (it == c->qpts.end() || !it->second.valid) return RPA_ERR_STATE;
   *ng = it->second.NG;
@@ -2458,7 +2469,9 @@ rpa_status batched_enqueue(rpa_graph* g, rpa_ctx* const* ctxs, int n, const int3
 
 rpa_status rpa_graph_create(rpa_ctx* const* ctxs, int32_t n, const int32_t* nq, const int32_t* iqs, rpa_graph** out) {
   if (!ctxs || n < 1 || !nq || !iqs || !out) return RPA_ERR_ARG;
-  if (!host_readable(ctxs) || !host_readable(nq) || !host_readable(iqs) || !host_readable(out)) return RPA_ERR_ARG;
+  if (!host_readable(ctxs) || !ctxs[0]) return RPA_ERR_ARG;
+  if (!on_device(ctxs[0]->prm.device)) return RPA_ERR_CUDA;
+  if (!host_readable(nq) || !host_readable(iqs) || !host_readable(out)) return RPA_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || nq[i] < 1) return RPA_ERR_ARG;
@@ -2681,7 +2694,9 @@ rpa_status rpa_set_tuning(rpa_ctx* c, int32_t param, int64_t value) {
 }
 
 rpa_status rpa_get_profile(const rpa_ctx* c, double* ms, int64_t* launches) {
-  if (!c || !host_readable(ms) || !host_readable(launches)) return RPA_ERR_ARG;
+  if (!c) return RPA_ERR_ARG;
+  if (!on_device(c->prm.device)) return RPA_ERR_CUDA;
+  if (!host_readable(ms) || !host_readable(launches)) return RPA_ERR_ARG;
   for (int i = 0; i < RPA_NSTAGES; ++i) {
     if (ms) ms[i] = c->prof_ms[i];
     if (launches) launches[i] = c->prof_launch[i];
