@@ -129,6 +129,16 @@ MUTATIONS = [
      "kr = np.asarray(oset.k_red, dtype=np.float64)", 1),
     ("symmetry: plane waves rotated by M^T", "Qr = np.asarray(oset.miller, dtype=np.int64) @ M.T",
      "Qr = np.asarray(oset.miller, dtype=np.int64) @ M", 1),
+    ("symmetry: projections not conjugated under time reversal", "            P = np.conj(P)\n",
+     "            pass\n", 1),
+    ("weight: energy difference not squared in the denominator", "om[None, None, :] ** 2 + d[:, :, None] ** 2",
+     "om[None, None, :] ** 2 + d[:, :, None]", 1),
+    ("PAW: Q block read with G slowest", "Qa = Qflat[qoff:qoff + ni * ni * ng].reshape(ni * ni, ng)",
+     "Qa = Qflat[qoff:qoff + ni * ni * ng].reshape(ng, ni * ni).T", 1),
+    ("optical: sign of the head", "return -1j * D / (np.asarray(eps_m)[None, :] - np.asarray(eps_n)[:, None])",
+     "return 1j * D / (np.asarray(eps_m)[None, :] - np.asarray(eps_n)[:, None])", 1),
+    ("gradient: Hermitian part not halved", "out[j] = (wq * omega_weights[j] / TWO_PI) * 0.5 * (G + G.conj().T)",
+     "out[j] = (wq * omega_weights[j] / TWO_PI) * (G + G.conj().T)", 1),
 ]
 
 

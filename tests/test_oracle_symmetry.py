@@ -96,6 +96,32 @@ def test_rotated_set_is_the_transformed_function_in_real_space():
     assert np.abs(_psi(s, -x) - np.conj(_psi(s, x))).max() > 1e-2 * np.abs(_psi(s, x)).max()
 
 
+def test_time_reversal_conjugates_the_pair_densities_with_paw():
+    """psi -> conj(psi) maps (k, k+q) to (-k, -k-q), and the full pair density
+    of Eqs. 4 and 6 to n'(G; -q) = conj(n(-G; q)): the plane-wave part by the
+    relabelling Q -> -Q with conjugated coefficients, the PAW part through
+    P -> conj(P) (real projector functions) and Q_ij(-k) = conj(Q_ij(k))
+    (real partial waves, as the synthetic Q has)."""
+    cell = np.diag([5.0, 5.5, 4.5])
+    k, q = np.array([0.1, 0.2, 0.0]), np.array([0.25, 0.0, -0.1])
+    nproj = [2, 3]
+    paw = syn.make_paw_setup(5, nproj)
+    sets = []
+    for i, kk in enumerate((k, k + q)):
+        s_ = syn.make_orbitals(5, i, cell, kk, 2.0, 2, 4)
+        sets.append(dataclasses.replace(s_, P=syn.make_projections(5, i, 6, sum(nproj))))
+    eye = [np.eye(n) for n in nproj]
+    trs = [o.rotate_set(s_, np.eye(3, dtype=int), True, nproj, [0, 1], eye) for s_ in sets]
+    assert np.allclose(trs[0].k_red, -k) and np.allclose(trs[1].k_red, -k - q)
+    gm = o.g_sphere(cell, q, 1.5)
+    n, _, _ = o.pair_block(sets, paw.nproj, syn.paw_Q(paw, cell, q, gm), gm, 0, 1, [0, 0, 0])
+    nt, _, _ = o.pair_block(trs, paw.nproj, syn.paw_Q(paw, cell, -q, -gm), -gm, 0, 1, [0, 0, 0])
+    assert np.abs(nt - np.conj(n)).max() <= 1e-13 * np.abs(n).max()
+    # the PAW part alone is not invariant: P -> conj(P) is what matches
+    assert np.abs(syn.paw_Q(paw, cell, -q, -gm) - np.conj(syn.paw_Q(paw, cell, q, gm))).max() < 1e-14
+    assert np.abs(np.imag(sets[0].P)).max() > 1e-3
+
+
 def test_projector_rotation_composes_and_identity_is_a_no_op():
     s = syn.make_orbitals(4, 0, np.eye(3) * 6.0, [0.1, 0.2, 0.0], 3.0, 3, 5)
     nproj = [3, 3, 2]
