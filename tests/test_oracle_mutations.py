@@ -139,6 +139,14 @@ MUTATIONS = [
      "return 1j * D / (np.asarray(eps_m)[None, :] - np.asarray(eps_n)[:, None])", 1),
     ("gradient: Hermitian part not halved", "out[j] = (wq * omega_weights[j] / TWO_PI) * 0.5 * (G + G.conj().T)",
      "out[j] = (wq * omega_weights[j] / TWO_PI) * (G + G.conj().T)", 1),
+    ("sphere: reciprocal basis transposed", "v = (np.array([g1, g2, g3], dtype=np.float64) + q) @ B",
+     "v = (np.array([g1, g2, g3], dtype=np.float64) + q) @ B.T", 1),
+    ("Coulomb: reciprocal basis transposed", "c = qg @ B", "c = qg @ B.T", 1),
+    ("optical: k dropped from the dipole", "kQ = (np.asarray(oset.k_red, dtype=np.float64)[None, :] + "
+     "np.asarray(oset.miller, dtype=np.float64)) @ B", "kQ = np.asarray(oset.miller, dtype=np.float64) @ B", 1),
+    ("gradient: Gamma transposed", 'np.einsum("gh,hab->gab", Gam[j], n)', 'np.einsum("gh,hab->gab", Gam[j].T, n)', 1),
+    ("pair density: plane waves on the box edge dropped", "inside = np.all((tgt >= lo) & (tgt <= hi), axis=1)",
+     "inside = np.all((tgt > lo) & (tgt <= hi), axis=1)", 1),
 ]
 
 

@@ -102,6 +102,20 @@ def test_reciprocal_lattice_is_dual_to_the_cell():
     assert np.allclose(np.sort(g2)[1:], b1 ** 2, rtol=1e-12)
 
 
+def test_coulomb_on_a_hexagonal_lattice():
+    """v_G = 4 pi / |G|^2 depends on |G| only: the six shortest basal G of a
+    hexagonal lattice (a = 4, c = 2.5 bohr; |b1| = 4 pi / (a sqrt 3), the
+    textbook length) share v = 4 pi / |b1|^2, and v_0 = 0 at q = 0."""
+    a = 4.0
+    hexa = np.array([[a, 0.0, 0.0], [-a / 2, a * np.sqrt(3.0) / 2, 0.0], [0.0, 0.0, 2.5]])
+    b1 = 4.0 * np.pi / (a * np.sqrt(3.0))
+    gm = o.g_sphere(hexa, [0, 0, 0], 0.5 * b1 ** 2 * 1.001)
+    v = o.coulomb(hexa, [0, 0, 0], gm)
+    zero = ~gm.any(axis=1)
+    assert zero.sum() == 1 and v[zero][0] == 0.0
+    assert np.allclose(v[~zero], 4.0 * np.pi / b1 ** 2, rtol=1e-13) and (~zero).sum() == 6
+
+
 def test_coulomb_zero_only_at_q_plus_g_zero():
     cell = np.eye(3) * 10.0
     gm = o.g_sphere(cell, [0, 0, 0], 1.0)
