@@ -147,6 +147,12 @@ MUTATIONS = [
     ("gradient: Gamma transposed", 'np.einsum("gh,hab->gab", Gam[j], n)', 'np.einsum("gh,hab->gab", Gam[j].T, n)', 1),
     ("pair density: plane waves on the box edge dropped", "inside = np.all((tgt >= lo) & (tgt <= hi), axis=1)",
      "inside = np.all((tgt > lo) & (tgt <= hi), axis=1)", 1),
+    ("gradient: optical energy difference reversed", "dlt = sk.eps[msel][None, :] - sk.eps[nsel][:, None]",
+     "dlt = sk.eps[nsel][:, None] - sk.eps[msel][None, :]", 1),
+    ("gradient: optical plane-wave adjoint sign", "gC[ik][msel] += (-1j * bmat.T @ sk.C[nsel]) * sv[None, :]",
+     "gC[ik][msel] += (1j * bmat.T @ sk.C[nsel]) * sv[None, :]", 1),
+    ("gradient: optical PAW adjoint conjugate dropped", "gP[ik][np.ix_(msel, cols)] += bmat.T @ Pn @ np.conj(Qd)",
+     "gP[ik][np.ix_(msel, cols)] += bmat.T @ Pn @ Qd", 1),
 ]
 
 
