@@ -153,6 +153,13 @@ MUTATIONS = [
      "gC[ik][msel] += (1j * bmat.T @ sk.C[nsel]) * sv[None, :]", 1),
     ("gradient: optical PAW adjoint conjugate dropped", "gP[ik][np.ix_(msel, cols)] += bmat.T @ Pn @ np.conj(Qd)",
      "gP[ik][np.ix_(msel, cols)] += bmat.T @ Pn @ Qd", 1),
+    ("PAW: projector offset of the k+q band ignored", "Pa_m = Pm[:, off:off + ni]", "Pa_m = Pm[:, :ni]", 1),
+    ("symmetry: atom map ignored", "src = atom_map[a]", "src = a", 1),
+    ("chi0 sampled: G sorted", "gm = gm_all[gidx]", "gm = gm_all[np.sort(gidx)]", 1),
+    ("chi0 sampled: Q block stride of the sample", "off += ni * ni * ng_all", "off += ni * ni * len(gidx)", 1),
+    ("E_c: Hermitian part taken with a transpose", "M = 0.5 * (M + M.conj().T)", "M = 0.5 * (M + M.T)", 1),
+    ("gradient: projections of the k set on the k+q side", "Pm = skp.P[msel, off:off + ni]",
+     "Pm = sk.P[msel, off:off + ni]", 1),
 ]
 
 
